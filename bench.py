@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 layered-medium Helmholtz solver: solved unknowns/s.
+
+One step = one hz_solve of the two-block PML workload (160 x 160 x 128
+interior nodes, PML rim in x/y, ramped z, 12 layers, 2 x 2 blocks, 4 point
+sources, complex128): steps 1-7 of the block method of Sec. 2 with the
+interface correction, every RHS to relative residual <= 1e-8.  The FP64 path is
+the headline `value`; the mixed path (FP32 transforms, FP64 z solves,
+interface solves and refinement) is measured on the same workload and reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hz|reference]
+
+N > 1 (torchrun): every rank solves its own copy of the workload (replicas,
+weak scaling, no collective on the data path); value = all ranks' unknowns /
+the slowest rank's time.  `--impl reference` times the CPU FP64 oracle (the
+plain block algorithm in numpy/scipy) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solved unknowns/s at rel. residual <=1e-8 (FP64 path; mixed path beside it)"
+UNIT = "unknowns/s"
+RTOL = 1e-8
+FP64_FLOPS_PER_CLK_SM = 4          # 2 DFMA per SM per clock (1.25 TFLOP/s nominal at 2070 MHz)
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = sorted(float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit())
+        mx = max(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def block_sizes(n, ifaces):
+    edges = [-1] + list(ifaces) + [n]
+    return [edges[b + 1] - edges[b] - 1 for b in range(len(edges) - 1)]
+
+
+def bulk_macs(w, nrhs):
+    """Complex multiply-adds of the four bulk transform launches (X1..X4) of one solve."""
+    bx, by = block_sizes(w.nx, w.x_iface), block_sizes(w.ny, w.y_iface)
+    sx, sy = sum(n * n for n in bx), sum(n * n for n in by)
+    rows_x = w.ny - len(w.y_iface)        # rows transformed along x (interface rows skipped)
+    rows_y = w.nx - len(w.x_iface)
+    per = nrhs * w.nz
+    return [per * rows_x * sx, per * rows_y * sy, per * rows_y * sy, per * rows_x * sx]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1909_01299_gb300", "csrc", "hz_xform.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        ent = data.get(kernel, {})
+        if ent.get("source_sha") == kernel_source_hash() and ent.get("workload") == workload:
+            return ent.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(budget_s: float = 12.0, max_runs: int = 3):
+    """Time the CPU oracle's block solver on 1 RHS of the workload (bounded sample)."""
+    import numpy as np
+    from oracle import hz_oracle as O
+    from paper_1909_01299_gb300 import workloads as W
+    w = W.pml_160x160x128(nrhs=1)
+    P = O.Problem.from_workload(w)
+    A, _ = O.assemble(P)
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max_runs and (time.perf_counter() - t_all) < budget_s:
+        t0 = time.perf_counter()
+        u = O.block_solve(P, w.f, A)
+        times.append(time.perf_counter() - t0)
+    res = float(np.max(O.residual(P, u, w.f, A)))
+    best = min(times)
+    return {"value": w.unknowns / best, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 of 4 RHS of {w.name} through the full 7-step block algorithm, "
+                      f"{len(times)} run(s), best {best:.2f} s, residual {res:.1e}; BLAS threads = "
+                      f"cores, per-mode z solves single-threaded"}, best, w.unknowns
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import hz_oracle as O
+    from paper_1909_01299_gb300 import workloads as W
+    w = W.pml_160x160x128(nrhs=1)
+    P = O.Problem.from_workload(w)
+    A, _ = O.assemble(P)
+    for _ in range(args.warmup):
+        O.block_solve(P, w.f, A)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = O.block_solve(P, w.f, A)
+    dt = (time.perf_counter() - t0) / args.steps
+    res = float(np.max(O.residual(P, u, w.f, A)))
+    value = w.unknowns / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic",
+            "config": {"workload": "pml-160x160x128-2x2blocks-fp64 (1 of 4 RHS per step)",
+                       "nx": 160, "ny": 160, "nz": 128, "blocks": "2x2", "nrhs": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"1 RHS per step, residual {res:.1e}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def time_path(torch, hz, plan, f, u, steps, warmup, dist, world, device):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.solve(f, out=u)
+    torch.cuda.synchronize()
+    plan.set_stage_timing(True)
+    l0 = plan.info()["kernel_launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(device) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve(f, out=u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = plan.info()["kernel_launches"] - l0
+    stages = plan.stage_times()
+    plan.set_stage_timing(False)
+    return ms, launches, stages, clk.summary()
+
+
+def run_hz(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.cuda.current_device()
+    from paper_1909_01299_gb300 import build as B
+    B.build()
+    from paper_1909_01299_gb300 import hz, workloads as W
+
+    w = W.pml_160x160x128()
+    R = w.nrhs
+    f = torch.from_numpy(w.f).to(device)
+    u = torch.empty_like(f)
+    plan = hz.Plan.from_workload(w, precision="fp64")
+    plan_ms = plan.info()["plan_ms"]
+
+    # FP64 path (headline)
+    ms64, launches64, st64, clk64 = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist, world,
+                                              device)
+    res64 = float(np.max(plan.residual(f, u)))
+    # mixed path on the same workload
+    plan.set_options(precision="mixed", rtol=RTOL, max_refine=10)
+    msmx, launchesmx, stmx, clkmx = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist,
+                                              world, device)
+    infomx = plan.info()
+    resmx = float(np.max(plan.residual(f, u)))
+    plan.set_options(precision="fp64")
+
+    # end to end through the host-buffer entry point (H2D of f and D2H of u inside the call)
+    fh = torch.from_numpy(w.f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    for _ in range(2):
+        plan.solve_host(fh, out=uh)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        plan.solve_host(fh, out=uh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    unknowns = w.unknowns * R
+    value = world * unknowns / (ms64 * 1e-3)
+    # roofline of the dominant kernel: the FP64 bulk transform (4 launches per solve)
+    macs = bulk_macs(w, R)
+    complex_w = True
+    flops_per_launch = sum(macs) / 4 * (6 if complex_w else 4)
+    t_launch = (st64["fwd"][0] + st64["inv"][0]) / max(1, st64["fwd"][1] + st64["inv"][1])
+    achieved = flops_per_launch / (t_launch * 1e-3) / 1e12
+    peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
+    total_ms = sum(v[0] for v in st64.values())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, _, _ = oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "blocks": "2x2", "nrhs": R,
+                   "grid": "uniform core 128 + 16-node geometric rim (ratio 1.3, outer 8 complex) in x/y; "
+                           "z ramp 0.5..2.0; 12 layers",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "working set ~0.4 GB (f, u, 3 volume buffers, factors) > 129 MB L2; no flush",
+                   "rel_residual_max": res64, "plan_ms": plan_ms},
+        "gpu_launches": launches64,
+        "roofline": {"bound": "alu", "kernel": "xform_kernel<double> (FP64 bulk x/y transforms)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_note": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s); "
+                                  "probe measured 1.197 TFLOP/s at ~1.97 GHz",
+                     "flops_per_launch": flops_per_launch, "launch_ms": t_launch,
+                     "traffic": profiled_traffic("xform_kernel<double>", w.name),
+                     "share_of_step": (st64["fwd"][0] + st64["inv"][0]) / max(total_ms, 1e-9)},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in st64.items() if v[1]},
+        "mixed": {"value": world * unknowns / (msmx * 1e-3), "ms_per_step": msmx,
+                  "speedup_vs_fp64": ms64 / msmx, "refinements": infomx["refinements"],
+                  "rel_residual_max": resmx, "gpu_launches": launchesmx, "dtype": "c64 transforms + f64",
+                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in stmx.items() if v[1]},
+                  "clocks": clkmx},
+        "e2e": {"value": world * unknowns / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(fh.numel() * 16),
+                "d2h_bytes_per_step": int(uh.numel() * 16), "ms_per_step": e2e_s * 1e3,
+                "entry_point": "hz_solve_host (pinned host buffers)"},
+        "clocks": clk64,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_hz(args)
+
+
+if __name__ == "__main__":
+    main()

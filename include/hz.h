@@ -1,0 +1,195 @@
+/*
+ * hz.h -- C ABI of the GB300 layered-medium Helmholtz solver.
+ *
+ * Solves the 7-point finite-volume discretisation (Eq. (fd), Kronecker form
+ * Eq. (fdmtr)) of
+ *
+ *     -sigma(z) (u_xx + u_yy) - (sigma(z) u_z)_z - k^2(z) u = f
+ *
+ * on a tensor grid S_x x S_y x S_z with homogeneous Dirichlet boundaries, by
+ * the block method of Sec. 2: the grid is split into Cartesian blocks
+ * S^i_x x S^j_y x S_z; each block is solved with zero Dirichlet data by x/y
+ * eigen-transforms and one tridiagonal solve in z per mode (Eq. (fdmtrprjfr));
+ * the residual left on the block interfaces is removed with the global
+ * eigen-transform (Eq. (fdmtrprjfrerr)) and a second local solve
+ * (Eq. (fdmtrprjfrerrloc)); steps 1-7 of the algorithm in Sec. 2.
+ *
+ * Discretisation conventions (all arrays are host arrays, copied at plan creation):
+ *   - An axis with N interior (unknown) nodes has N+1 steps h_0..h_N; step h_n
+ *     joins node n-1 to node n and nodes -1 and N carry u = 0.  Steps may be
+ *     complex (absorbing "PML" parts of the grid, Sec. 2).
+ *   - hhat_i = (h_i + h_{i+1}) / 2 are the control-volume edge lengths, and the
+ *     solver returns u = A^{-1} (Mz (x) My (x) Mx) f with M_d = diag(hhat).
+ *   - k^2 and sigma are node-based per layer; layer L holds the z nodes
+ *     [z_begin[L], z_begin[L+1]).  sigma on a z step inside a layer is the
+ *     layer's value, on a step joining two layers the harmonic mean of the two.
+ *
+ * Device arrays f, u, g, lam are complex128 (interleaved re, im doubles) of
+ * shape (nrhs, Nz, Ny, Nx), x fastest, contiguous.  The caller owns them;
+ * they are never retained after a call returns.  f == u (in place) is allowed.
+ *
+ * Errors: every entry point returns an hz_status; nothing is printed and no
+ * exception crosses the ABI.  Kernels report a zero/non-finite pivot or a
+ * non-finite value through a device status word that the call reads back.
+ */
+#ifndef HZ_H_
+#define HZ_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } hz_c128;   /* layout of complex128 */
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_ARG = 1,            /* bad size, pointer or option                            */
+  HZ_ERR_EIG = 2,            /* a 1D eigen-decomposition failed its identity checks    */
+  HZ_ERR_SINGULAR = 3,       /* zero or non-finite pivot in a z tridiagonal            */
+  HZ_ERR_NONFINITE = 4,      /* non-finite value in the input or the result            */
+  HZ_ERR_NOT_CONVERGED = 5,  /* mixed path: refinement did not reach rtol              */
+  HZ_ERR_OOM = 6,            /* device allocation failed                               */
+  HZ_ERR_CUDA = 7,           /* a CUDA runtime call failed                             */
+  HZ_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up                     */
+} hz_status;
+
+enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+
+typedef struct hz_plan_s *hz_plan_t;
+
+/* Grid: nx, ny, nz interior nodes; hx, hy, hz point to nx+1, ny+1, nz+1 steps. */
+typedef struct {
+  int nx, ny, nz;
+  const hz_c128 *hx, *hy, *hz;
+} hz_grid;
+
+/* Layers: z_begin has nlayers+1 entries, z_begin[0] = 0, z_begin[nlayers] = nz,
+ * strictly increasing.  k2 has nlayers complex entries.  sigma has nlayers
+ * positive entries or is NULL (sigma = 1). */
+typedef struct {
+  int nlayers;
+  const int *z_begin;
+  const hz_c128 *k2;
+  const double *sigma;
+} hz_layers;
+
+/* Block partition: nbx x nby blocks.  x_iface lists the nbx-1 interface node
+ * indices (strictly increasing, each block keeps >= 1 node); NULL selects the
+ * default p_b = floor(b (nx+1) / nbx) - 1, b = 1..nbx-1.  Same for y.  The
+ * interface nodes belong to no block (Sec. 2, "the projection operators to
+ * interior nodes"). */
+typedef struct {
+  int nbx, nby;
+  const int *x_iface, *y_iface;
+} hz_blocks;
+
+/* Options.  precision: HZ_FP64 (all arithmetic FP64) or HZ_MIXED (x/y
+ * eigen-transforms on FP32 tensor cores; z solves, interface solves and the
+ * residual in FP64; FP64 iterative refinement until the relative residual
+ * ||M f - A u|| / ||M f|| <= rtol for every RHS, at most max_refine
+ * corrections).  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+typedef struct {
+  int precision;
+  double rtol;
+  int max_refine;
+  void *cuda_stream;
+} hz_options;
+
+/* Per-solve report. */
+typedef struct {
+  int refinements;           /* corrections applied after the first solve (mixed path)  */
+  double rel_residual;       /* max over RHS of ||M f - A u|| / ||M f|| when measured,
+                                else -1                                                 */
+  double min_abs_pivot;      /* smallest |pivot| over all z eliminations of the plan    */
+  double plan_ms;            /* host + device time of the last plan / frequency set-up  */
+  double eig_max_residual;   /* largest relative eigen-identity residual of the plan    */
+  long long device_bytes;    /* device memory owned by the plan                         */
+  long long kernel_launches; /* kernels launched by this plan's solves so far           */
+} hz_info;
+
+/* Stage timers: when enabled, every solve records CUDA events on the plan's
+ * stream around each stage and accumulates the elapsed milliseconds per stage
+ * (HZ_STAGE_*), with the number of launches per stage.  Off by default. */
+enum {
+  HZ_STAGE_FWD = 0,       /* step 1: bulk forward x/y transforms (2 launches)          */
+  HZ_STAGE_PASS_A = 1,    /* step 2: block z solves                                   */
+  HZ_STAGE_EDGES = 2,     /* step 3: v next to the interfaces                          */
+  HZ_STAGE_IRES = 3,      /* step 4: interface residual                                */
+  HZ_STAGE_GLOBAL = 4,    /* step 5: global interface solve                            */
+  HZ_STAGE_PASS_B = 5,    /* step 6: boundary terms and block z solves                  */
+  HZ_STAGE_INV = 6,       /* step 7: bulk inverse x/y transforms (2 launches)          */
+  HZ_STAGE_IFACE_OUT = 7, /* step 7: u = w on the interfaces                           */
+  HZ_STAGE_RESID = 8,     /* refinement / residual stencil and norms                    */
+  HZ_NSTAGES = 9
+};
+hz_status hz_set_stage_timing(hz_plan_t plan, int enable);   /* also resets the totals */
+/* ms[HZ_NSTAGES] and launches[HZ_NSTAGES] (either may be NULL) receive the totals. */
+hz_status hz_get_stage_times(hz_plan_t plan, double *ms, long long *launches);
+
+/* Build a plan: 1D operators, per-block and global generalized eigenpairs
+ * (K_d W = M_d W Lambda, W^T M_d W = I; the display after Eq. (fdmtrprj) and
+ * before Eq. (fdmtrprjfrerr)), the z elimination factors of every mode, and all
+ * device tables.  Errors: HZ_ERR_ARG on bad sizes/pointers, HZ_ERR_EIG when an
+ * eigen-decomposition fails its checks, HZ_ERR_SINGULAR on a zero pivot,
+ * HZ_ERR_OOM / HZ_ERR_CUDA on device failures.  *out is NULL on error. */
+hz_status hz_plan_create(const hz_grid *grid, const hz_layers *layers, const hz_blocks *blocks,
+                         const hz_options *opts, hz_plan_t *out);
+
+/* Scale the base k^2 of every layer by omega^2 and rebuild the z factors
+ * (Sec. 2: k^2 enters only the z operator, so the x/y eigen data are kept). */
+hz_status hz_plan_set_frequency(hz_plan_t plan, double omega);
+
+/* Replace the base per-layer k^2 (nlayers entries, host array) and rebuild the z
+ * factors; the x/y eigen data are kept (k^2 enters only the z operator of
+ * Eq. (fdmtrprjfr)).  The current frequency scaling omega^2 still applies. */
+hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
+
+/* Change the options' stream, precision, rtol and max_refine of a plan. */
+hz_status hz_plan_set_options(hz_plan_t plan, const hz_options *opts);
+
+/* u = A^{-1} (M f): steps 1-7 of the algorithm in Sec. 2 for nrhs right-hand
+ * sides.  f_dev, u_dev: device arrays (see above).  Stream-ordered on the
+ * plan's stream; returns after the result is complete. */
+hz_status hz_solve(hz_plan_t plan, const hz_c128 *f_dev, hz_c128 *u_dev, int nrhs);
+
+/* The same solve with HOST arrays f_host, u_host (pageable or pinned): the call
+ * copies f to the device, solves and copies u back. */
+hz_status hz_solve_host(hz_plan_t plan, const hz_c128 *f_host, hz_c128 *u_host, int nrhs);
+
+/* lam = A^{-H} g.  A is complex symmetric (Eq. (fdmtr) with symmetric K_d and
+ * diagonal M_d), so A^H = conj(A) and the adjoint reuses the forward path:
+ * lam = conj(A^{-1} conj(g)).  g is already in the weighted space (no M is
+ * applied to it). */
+hz_status hz_solve_adjoint(hz_plan_t plan, const hz_c128 *g_dev, hz_c128 *lam_dev, int nrhs);
+
+/* Layer gradient G_L = sum_rhs sum_{k in L} hhat^z_k sum_ij conj(lam_ijk) hhat^x_i hhat^y_j u_ijk
+ * for L = 0..nlayers-1, written to G_host (nlayers entries).  For a real misfit J whose
+ * adjoint source is g = dJ/du* the result gives dJ/dRe k^2_L = Re G_L and
+ * dJ/dIm k^2_L = -Im G_L (derivative of Eq. (fdmtr) in k^2). */
+hz_status hz_grad_layers(hz_plan_t plan, const hz_c128 *u_dev, const hz_c128 *lam_dev, int nrhs,
+                         hz_c128 *G_host);
+
+/* Relative residuals ||M f - A u||_2 / ||M f||_2 per RHS (FP64), into rel_host (nrhs). */
+hz_status hz_residual(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev, int nrhs,
+                      double *rel_host);
+
+hz_status hz_get_info(hz_plan_t plan, hz_info *out);
+
+hz_status hz_plan_destroy(hz_plan_t plan);
+
+const char *hz_status_str(hz_status s);
+
+/* Host-only helper (no device memory is touched): the generalised eigenpairs
+ * K W = M W Lambda, W^T M W = I of the complex-symmetric tridiagonal pencil with
+ * diagonal kd (n), off-diagonal ko (n-1) and diagonal M = diag(m) (n), as used
+ * for every block and axis of a plan (display after Eq. (fdmtrprj)).  lam (n)
+ * and W (n*n, row-major: W[i*n + l] is node i of mode l) are caller-owned.
+ * *residual receives max(||K W - M W Lambda||_F / (||K||_F ||W||_F),
+ * max |W^T M W - I|).  HZ_ERR_EIG if the iteration breaks down. */
+hz_status hz_tridiag_eig(int n, const hz_c128 *kd, const hz_c128 *ko, const hz_c128 *m, hz_c128 *lam,
+                         hz_c128 *W, double *residual);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H_ */

@@ -1,0 +1,955 @@
+// C ABI of the hz library: plan creation (1D operators, eigen-decompositions,
+// device tables, z factors) and the solve orchestration of steps 1-7 of Sec. 2.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "hz_internal.h"
+
+using hz::cd;
+
+namespace hz {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hz
+
+namespace {
+
+constexpr int kTileN = 32;   // output columns per transform tile (matches hz_xform.cu)
+
+// ---------------------------------------------------------------------------
+// Host-side axis data
+// ---------------------------------------------------------------------------
+struct AxisPlan {
+  int n = 0, nb = 1;
+  std::vector<cd> h, mh, kd, ko;             // steps, dual lengths, stiffness (diag, off)
+  std::vector<int> bstart, bsize, iface;
+  std::vector<std::vector<cd>> blam, bW;     // per block eigenpairs (W row-major [node][mode])
+  std::vector<int> breal;
+  std::vector<cd> glam, gW;                  // whole-axis eigenpairs (when the plan needs them)
+  int greal = 0;
+  double eig_res = 0.0;
+};
+
+// Device tables of one axis.
+struct AxisDev {
+  hz::XformSet fwd, inv, gfwd, ginv;
+  double2 *lam_b = nullptr, *lam_g = nullptr;    // eigenvalue per position (block / global)
+  signed char* skip = nullptr;                   // interface flags
+  int* ifc = nullptr;                            // interface node indices
+  double2 *m = nullptr, *im = nullptr, *ih = nullptr;
+  double2* edge_coef = nullptr;  int2* edge_rng = nullptr;   // 2 nI slots (step 3)
+  double2* gcoef = nullptr;      int2* grng = nullptr;       // nI slots (step 5), Wg[p][:]
+  int *gl = nullptr, *gr = nullptr;                          // pass B interface indices
+  double2 *cl = nullptr, *cr = nullptr;                      // pass B coefficients
+  double2* ks = nullptr;                                     // stencil rows / mhat
+};
+
+struct Workspace {
+  int cap = 0;                       // RHS capacity
+  double2 *FT = nullptr, *G = nullptr, *V = nullptr;
+  double2 *cX = nullptr, *vX = nullptr, *cY = nullptr, *vY = nullptr;
+  double2 *rX = nullptr, *rY = nullptr, *aX = nullptr, *bY = nullptr;
+  double2 *cg = nullptr, *dg = nullptr, *wX = nullptr, *wY = nullptr;
+  double2 *alX = nullptr, *alY = nullptr;
+  double2 *RHO = nullptr, *F2 = nullptr;           // residual / input copy (mixed, adjoint, host)
+  double2 *HU = nullptr;                           // output staging for host solves
+  double* partial = nullptr; double* norms = nullptr;
+  double2* gpart = nullptr; double2* Gl = nullptr;
+  int rho_cap = 0, f2_cap = 0, hu_cap = 0;
+};
+
+}  // namespace
+
+struct hz_plan_s {
+  int nx = 0, ny = 0, nz = 0, nlayers = 0;
+  hz_options opts{};
+  cudaStream_t st = nullptr;
+  AxisPlan ax, ay;
+  std::vector<cd> hz, k2base;
+  std::vector<double> sig_layer;
+  std::vector<int> z_begin;
+  double omega = 1.0;
+  bool need_global = false;
+  int real_cm = 1;
+  AxisDev dx, dy;
+  // z tables
+  double2 *tzd = nullptr, *szs = nullptr, *mz = nullptr, *imz = nullptr, *coff = nullptr;
+  double2 *cm_b = nullptr, *cm_g = nullptr, *tzs = nullptr;
+  double* sig = nullptr;
+  int* zb = nullptr;
+  // factors
+  double2 *Pb = nullptr, *Qb = nullptr, *Pg = nullptr, *Qg = nullptr;
+  int* status = nullptr;
+  unsigned long long* minpiv = nullptr;
+  Workspace ws;
+  std::vector<void*> allocs;
+  long long bytes = 0;
+  hz_info info{};
+  // stage timers
+  bool timing = false;
+  double stage_ms[HZ_NSTAGES] = {};
+  long long stage_launches[HZ_NSTAGES] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int stage; cudaEvent_t a, b; long long launches; };
+  std::vector<Rec> recs;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+struct Fail {
+  hz_status s;
+};
+
+void ck(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) throw Fail{HZ_ERR_OOM};
+  if (e != cudaSuccess) throw Fail{HZ_ERR_CUDA};
+}
+
+// Records CUDA events around a stage when the plan's stage timers are on.
+class Stage {
+ public:
+  Stage(hz_plan_t p, int stage) : p_(p), stage_(stage), l0_(hz::launch_count()) {
+    if (p_->timing) a_ = next_event(), ck(cudaEventRecord(a_, p_->st));
+  }
+  ~Stage() {
+    if (p_->timing) {
+      cudaEvent_t b = next_event();
+      cudaEventRecord(b, p_->st);
+      p_->recs.push_back({stage_, a_, b, hz::launch_count() - l0_});
+    }
+  }
+
+ private:
+  cudaEvent_t next_event() {
+    if (p_->ev_used == p_->ev_pool.size()) {
+      cudaEvent_t e;
+      ck(cudaEventCreate(&e));
+      p_->ev_pool.push_back(e);
+    }
+    return p_->ev_pool[p_->ev_used++];
+  }
+  hz_plan_t p_;
+  int stage_;
+  long long l0_;
+  cudaEvent_t a_ = nullptr;
+};
+
+// After the stream is synchronised: fold the recorded event pairs into the totals.
+void collect_stages(hz_plan_t p) {
+  for (const auto& r : p->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) p->stage_ms[r.stage] += ms;
+    p->stage_launches[r.stage] += r.launches;
+  }
+  p->recs.clear();
+  p->ev_used = 0;
+}
+
+template <typename T>
+T* dalloc(hz_plan_t p, size_t count) {
+  if (count == 0) count = 1;
+  void* ptr = nullptr;
+  ck(cudaMalloc(&ptr, count * sizeof(T)));
+  ck(cudaMemsetAsync(ptr, 0, count * sizeof(T), p->st));
+  p->allocs.push_back(ptr);
+  p->bytes += (long long)(count * sizeof(T));
+  return static_cast<T*>(ptr);
+}
+
+void dfree(hz_plan_t p, void* ptr) {
+  if (!ptr) return;
+  auto it = std::find(p->allocs.begin(), p->allocs.end(), ptr);
+  if (it != p->allocs.end()) p->allocs.erase(it);
+  cudaFree(ptr);
+}
+
+template <typename T>
+T* upload(hz_plan_t p, const std::vector<T>& v) {
+  T* d = dalloc<T>(p, v.size());
+  if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p->st));
+  return d;
+}
+
+double2* upload_c(hz_plan_t p, const std::vector<cd>& v) {
+  std::vector<double2> t(v.size());
+  for (size_t i = 0; i < v.size(); ++i) t[i] = make_double2(v[i].real(), v[i].imag());
+  return upload(p, t);
+}
+
+bool finite(cd z) { return std::isfinite(z.real()) && std::isfinite(z.imag()); }
+
+// ---------------------------------------------------------------------------
+// Plan construction
+// ---------------------------------------------------------------------------
+hz_status build_axis(AxisPlan& A, int n, const hz_c128* h, int nb, const int* ifc) {
+  A.n = n;
+  A.nb = nb;
+  A.h.resize(n + 1);
+  for (int i = 0; i <= n; ++i) {
+    A.h[i] = cd(h[i].re, h[i].im);
+    if (!finite(A.h[i]) || std::abs(A.h[i]) == 0.0) return HZ_ERR_ARG;
+  }
+  A.mh.resize(n);
+  A.kd.resize(n);
+  A.ko.resize(std::max(n - 1, 0));
+  for (int i = 0; i < n; ++i) {
+    A.mh[i] = 0.5 * (A.h[i] + A.h[i + 1]);
+    A.kd[i] = 1.0 / A.h[i] + 1.0 / A.h[i + 1];
+    if (i + 1 < n) A.ko[i] = -1.0 / A.h[i + 1];
+  }
+  A.iface.clear();
+  for (int b = 1; b < nb; ++b) A.iface.push_back(ifc ? ifc[b - 1] : (b * (n + 1)) / nb - 1);
+  int prev = -1;
+  A.bstart.clear();
+  A.bsize.clear();
+  for (int b = 0; b < nb; ++b) {
+    const int end = (b < nb - 1) ? A.iface[b] : n;
+    const int size = end - prev - 1;
+    if (size < 1) return HZ_ERR_ARG;
+    A.bstart.push_back(prev + 1);
+    A.bsize.push_back(size);
+    prev = end;
+  }
+  A.blam.assign(nb, {});
+  A.bW.assign(nb, {});
+  A.breal.assign(nb, 1);
+  A.eig_res = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const int s = A.bstart[b], sz = A.bsize[b];
+    double res = 0.0;
+    if (!hz::tridiag_eig(sz, &A.kd[s], sz > 1 ? &A.ko[s] : nullptr, &A.mh[s], A.blam[b], A.bW[b], &res))
+      return HZ_ERR_EIG;
+    A.eig_res = std::max(A.eig_res, res);
+    for (const cd& w : A.bW[b])
+      if (w.imag() != 0.0) { A.breal[b] = 0; break; }
+  }
+  return HZ_OK;
+}
+
+hz_status build_global(AxisPlan& A) {
+  if (A.nb == 1) {
+    A.glam = A.blam[0];
+    A.gW = A.bW[0];
+    A.greal = A.breal[0];
+    return HZ_OK;
+  }
+  double res = 0.0;
+  if (!hz::tridiag_eig(A.n, A.kd.data(), A.ko.data(), A.mh.data(), A.glam, A.gW, &res)) return HZ_ERR_EIG;
+  A.eig_res = std::max(A.eig_res, res);
+  A.greal = 1;
+  for (const cd& w : A.gW)
+    if (w.imag() != 0.0) { A.greal = 0; break; }
+  return HZ_OK;
+}
+
+// Pack a block-diagonal transform: tab(b)[a][c] = get(b, a, c).
+template <typename Get>
+void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>& start,
+                const std::vector<int>& size, const std::vector<int>& real, Get get) {
+  xs.ncols = ncols;
+  xs.nblocks = (int)start.size();
+  std::vector<hz::XBlock> blocks;
+  std::vector<hz::XTile> tiles;
+  std::vector<double> t64;
+  std::vector<float> t32;
+  for (int b = 0; b < xs.nblocks; ++b) {
+    const int n = size[b];
+    hz::XBlock xb{};
+    xb.start = start[b];
+    xb.size = n;
+    xb.real = real[b];
+    xb.toff = (long long)t64.size();
+    xb.toff32 = (long long)t32.size();
+    const size_t nn = (size_t)n * n;
+    if (real[b]) {
+      t64.resize(t64.size() + nn);
+      t32.resize(t32.size() + nn);
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < n; ++c) {
+          const double v = get(b, a, c).real();
+          t64[xb.toff + (size_t)a * n + c] = v;
+          t32[xb.toff32 + (size_t)a * n + c] = (float)v;
+        }
+    } else {
+      t64.resize(t64.size() + 3 * nn);
+      t32.resize(t32.size() + 2 * nn);
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < n; ++c) {
+          const cd v = get(b, a, c);
+          const size_t o = (size_t)a * n + c;
+          t64[xb.toff + o] = v.real();
+          t64[xb.toff + nn + o] = v.imag() - v.real();
+          t64[xb.toff + 2 * nn + o] = v.real() + v.imag();
+          t32[xb.toff32 + o] = (float)v.real();
+          t32[xb.toff32 + nn + o] = (float)v.imag();
+        }
+    }
+    blocks.push_back(xb);
+    for (int c0 = 0; c0 < n; c0 += kTileN) tiles.push_back(hz::XTile{b, c0, std::min(kTileN, n - c0), 0});
+  }
+  xs.ntiles = (int)tiles.size();
+  xs.h_blocks = blocks;
+  xs.d_blocks = upload(p, blocks);
+  xs.d_tiles = upload(p, tiles);
+  xs.d_tab = upload(p, t64);
+  xs.d_tab32 = upload(p, t32);
+}
+
+void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global) {
+  const int n = A.n, nI = (int)A.iface.size();
+  make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, [&](int b, int a, int c) {
+    return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
+  });
+  make_xform(p, D.inv, n, A.bstart, A.bsize, A.breal,
+             [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
+  std::vector<cd> lam_b(n, cd(0)), lam_g(n, cd(0));
+  std::vector<signed char> skip(n, 0);
+  for (int q : A.iface) skip[q] = 1;
+  for (int b = 0; b < A.nb; ++b)
+    for (int a = 0; a < A.bsize[b]; ++a) lam_b[A.bstart[b] + a] = A.blam[b][a];
+  if (need_global) {
+    std::vector<int> s0{0}, sn{n}, gr{A.greal};
+    make_xform(p, D.gfwd, n, s0, sn, gr, [&](int, int a, int c) { return A.gW[(size_t)a * n + c]; });
+    make_xform(p, D.ginv, n, s0, sn, gr, [&](int, int a, int c) { return A.gW[(size_t)c * n + a]; });
+    lam_g = A.glam;
+  }
+  D.lam_b = upload_c(p, lam_b);
+  D.lam_g = upload_c(p, lam_g);
+  D.skip = upload(p, skip);
+  D.ifc = upload(p, A.iface);
+  std::vector<cd> im(n), ih(n + 1);
+  for (int i = 0; i < n; ++i) im[i] = 1.0 / A.mh[i];
+  for (int i = 0; i <= n; ++i) ih[i] = 1.0 / A.h[i];
+  D.m = upload_c(p, A.mh);
+  D.im = upload_c(p, im);
+  D.ih = upload_c(p, ih);
+  // step 3 edge rows: slot 2q = last row of the block left of interface q, 2q+1 = first row right of it
+  std::vector<cd> ecoef((size_t)std::max(2 * nI, 1) * n, cd(0));
+  std::vector<int2> erng(std::max(2 * nI, 1), make_int2(0, 0));
+  for (int q = 0; q < nI; ++q) {
+    const int bl = q, br = q + 1;
+    const int sl = A.bstart[bl], nl = A.bsize[bl], sr = A.bstart[br], nr = A.bsize[br];
+    for (int l = 0; l < nl; ++l) ecoef[(size_t)(2 * q) * n + sl + l] = A.bW[bl][(size_t)(nl - 1) * nl + l];
+    for (int l = 0; l < nr; ++l) ecoef[(size_t)(2 * q + 1) * n + sr + l] = A.bW[br][(size_t)0 * nr + l];
+    erng[2 * q] = make_int2(sl, sl + nl);
+    erng[2 * q + 1] = make_int2(sr, sr + nr);
+  }
+  D.edge_coef = upload_c(p, ecoef);
+  D.edge_rng = upload(p, erng);
+  // step 5: rows of the whole-axis W at the interfaces
+  std::vector<cd> gcoef((size_t)std::max(nI, 1) * n, cd(0));
+  std::vector<int2> grng(std::max(nI, 1), make_int2(0, n));
+  if (need_global)
+    for (int q = 0; q < nI; ++q)
+      for (int l = 0; l < n; ++l) gcoef[(size_t)q * n + l] = A.gW[(size_t)A.iface[q] * n + l];
+  D.gcoef = upload_c(p, gcoef);
+  D.grng = upload(p, grng);
+  // step 6: boundary right-hand side coefficients W[e][l] / h across the interface
+  std::vector<int> gl(n, -1), grr(n, -1);
+  std::vector<cd> cl(n, cd(0)), cr(n, cd(0));
+  for (int b = 0; b < A.nb; ++b) {
+    const int s = A.bstart[b], nb = A.bsize[b];
+    for (int l = 0; l < nb; ++l) {
+      if (b > 0) {
+        gl[s + l] = b - 1;
+        cl[s + l] = A.bW[b][(size_t)0 * nb + l] / A.h[s];
+      }
+      if (b < A.nb - 1) {
+        grr[s + l] = b;
+        cr[s + l] = A.bW[b][(size_t)(nb - 1) * nb + l] / A.h[s + nb];
+      }
+    }
+  }
+  D.gl = upload(p, gl);
+  D.gr = upload(p, grr);
+  D.cl = upload_c(p, cl);
+  D.cr = upload_c(p, cr);
+  // stencil rows divided by hhat
+  std::vector<cd> ks((size_t)3 * n, cd(0));
+  for (int i = 0; i < n; ++i) {
+    if (i > 0) ks[3 * i + 0] = A.ko[i - 1] / A.mh[i];
+    ks[3 * i + 1] = A.kd[i] / A.mh[i];
+    if (i + 1 < n) ks[3 * i + 2] = A.ko[i] / A.mh[i];
+  }
+  D.ks = upload_c(p, ks);
+}
+
+// z coefficients for the current k^2 (base * omega^2) and the mode factors.
+void build_z(hz_plan_t p) {
+  const int nz = p->nz;
+  std::vector<cd> k2n(nz);
+  std::vector<double> sn(nz, 1.0);
+  for (int L = 0; L < p->nlayers; ++L)
+    for (int k = p->z_begin[L]; k < p->z_begin[L + 1]; ++k) {
+      k2n[k] = p->k2base[L] * (p->omega * p->omega);
+      if (!p->sig_layer.empty()) sn[k] = p->sig_layer[L];
+    }
+  std::vector<double> shalf(nz + 1);
+  shalf[0] = sn[0];
+  shalf[nz] = sn[nz - 1];
+  for (int k = 1; k < nz; ++k) shalf[k] = 2.0 * sn[k - 1] * sn[k] / (sn[k - 1] + sn[k]);
+  std::vector<cd> mz(nz), imz(nz), szs(nz), tzd(nz), coff(nz, cd(0)), cmb(nz, cd(0)), cmg(nz, cd(0));
+  std::vector<cd> tzs((size_t)3 * nz, cd(0));
+  p->real_cm = 1;
+  for (int k = 0; k < nz; ++k) {
+    mz[k] = 0.5 * (p->hz[k] + p->hz[k + 1]);
+    imz[k] = 1.0 / mz[k];
+    szs[k] = sn[k] * mz[k];
+    tzd[k] = shalf[k] / p->hz[k] + shalf[k + 1] / p->hz[k + 1] - k2n[k] * mz[k];
+    if (k > 0) {
+      coff[k] = -shalf[k] / p->hz[k];
+      cmb[k] = coff[k] / mz[k];
+      cmg[k] = coff[k];
+      if (cmb[k].imag() != 0.0 || cmg[k].imag() != 0.0) p->real_cm = 0;
+    }
+  }
+  for (int k = 0; k < nz; ++k) {
+    if (k > 0) tzs[3 * k + 0] = coff[k] / mz[k];
+    tzs[3 * k + 1] = tzd[k] / mz[k];
+    if (k + 1 < nz) tzs[3 * k + 2] = coff[k + 1] / mz[k];
+  }
+  auto put = [&](double2*& d, const std::vector<cd>& v) {
+    if (!d) d = dalloc<double2>(p, v.size());
+    std::vector<double2> t(v.size());
+    for (size_t i = 0; i < v.size(); ++i) t[i] = make_double2(v[i].real(), v[i].imag());
+    ck(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+    ck(cudaStreamSynchronize(p->st));
+  };
+  put(p->mz, mz);
+  put(p->imz, imz);
+  put(p->szs, szs);
+  put(p->tzd, tzd);
+  put(p->coff, coff);
+  put(p->cm_b, cmb);
+  put(p->cm_g, cmg);
+  put(p->tzs, tzs);
+  if (!p->sig_layer.empty() && !p->sig) p->sig = upload(p, sn);
+  if (!p->zb) p->zb = upload(p, p->z_begin);
+
+  const long long vol = (long long)p->nx * p->ny * nz;
+  if (!p->Pb) {
+    p->Pb = dalloc<double2>(p, vol);
+    p->Qb = dalloc<double2>(p, vol);
+    if (p->need_global) {
+      p->Pg = dalloc<double2>(p, vol);
+      p->Qg = dalloc<double2>(p, vol);
+    }
+  }
+  const unsigned long long inf_bits = 0x7ff0000000000000ULL;
+  ck(cudaMemcpyAsync(p->minpiv, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, p->st));
+  ck(cudaMemsetAsync(p->status, 0, sizeof(int), p->st));
+  hz::zfactor(p->Pb, p->Qb, p->dx.lam_b, p->dy.lam_b, p->dx.skip, p->dy.skip, p->tzd, p->szs, p->coff,
+              p->mz, p->nx, p->ny, nz, p->minpiv, p->status, p->st);
+  if (p->need_global)
+    hz::zfactor(p->Pg, p->Qg, p->dx.lam_g, p->dy.lam_g, nullptr, nullptr, p->tzd, p->szs, p->coff,
+                nullptr, p->nx, p->ny, nz, p->minpiv, p->status, p->st);
+  ck(cudaGetLastError());
+  int status = 0;
+  unsigned long long mp = 0;
+  ck(cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  ck(cudaMemcpyAsync(&mp, p->minpiv, sizeof(mp), cudaMemcpyDeviceToHost, p->st));
+  ck(cudaStreamSynchronize(p->st));
+  double mpd;
+  std::memcpy(&mpd, &mp, sizeof(mpd));
+  p->info.min_abs_pivot = mpd;
+  if (status) throw Fail{(hz_status)status};
+}
+
+void ensure_ws(hz_plan_t p, int R) {
+  Workspace& w = p->ws;
+  if (w.cap >= R) return;
+  double2** bufs[] = {&w.FT, &w.G, &w.V, &w.cX, &w.vX, &w.cY, &w.vY, &w.rX, &w.rY, &w.aX, &w.bY,
+                      &w.cg, &w.dg, &w.wX, &w.wY, &w.alX, &w.alY};
+  for (double2** b : bufs) { dfree(p, *b); *b = nullptr; }
+  dfree(p, w.partial); dfree(p, w.norms);
+  const long long vol = (long long)p->nx * p->ny * p->nz * R;
+  const long long zr = (long long)p->nz * R;
+  const int nIx = (int)p->ax.iface.size(), nIy = (int)p->ay.iface.size();
+  w.FT = dalloc<double2>(p, vol);
+  w.G = dalloc<double2>(p, vol);
+  w.V = dalloc<double2>(p, vol);
+  w.cX = dalloc<double2>(p, zr * 2 * nIx * p->ny);
+  w.vX = dalloc<double2>(p, zr * 2 * nIx * p->ny);
+  w.cY = dalloc<double2>(p, zr * 2 * nIy * p->nx);
+  w.vY = dalloc<double2>(p, zr * 2 * nIy * p->nx);
+  w.rX = dalloc<double2>(p, zr * nIx * p->ny);
+  w.rY = dalloc<double2>(p, zr * nIy * p->nx);
+  w.aX = dalloc<double2>(p, zr * nIx * p->ny);
+  w.bY = dalloc<double2>(p, zr * nIy * p->nx);
+  w.cg = dalloc<double2>(p, zr * nIx * p->ny);
+  w.dg = dalloc<double2>(p, zr * nIy * p->nx);
+  w.wX = dalloc<double2>(p, zr * nIx * p->ny);
+  w.wY = dalloc<double2>(p, zr * nIy * p->nx);
+  w.alX = dalloc<double2>(p, zr * nIx * p->ny);
+  w.alY = dalloc<double2>(p, zr * nIy * p->nx);
+  w.partial = dalloc<double>(p, (size_t)2 * R * 4 * 152 + 2);
+  w.norms = dalloc<double>(p, (size_t)2 * R);
+  w.cap = R;
+  if (w.rho_cap) { dfree(p, w.RHO); w.RHO = nullptr; w.rho_cap = 0; }
+  if (w.f2_cap) { dfree(p, w.F2); w.F2 = nullptr; w.f2_cap = 0; }
+  if (w.hu_cap) { dfree(p, w.HU); w.HU = nullptr; w.hu_cap = 0; }
+}
+
+double2* ensure_extra(hz_plan_t p, double2*& buf, int& cap, int R) {
+  if (cap < R) {
+    dfree(p, buf);
+    buf = dalloc<double2>(p, (long long)p->nx * p->ny * p->nz * R);
+    cap = R;
+  }
+  return buf;
+}
+
+hz::IfaceArgs iface_args(hz_plan_t p, int R) {
+  hz::IfaceArgs a;
+  a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nrhs = R;
+  a.nIx = (int)p->ax.iface.size(); a.nIy = (int)p->ay.iface.size();
+  a.xif = p->dx.ifc; a.yif = p->dy.ifc;
+  a.isx = p->dx.skip; a.isy = p->dy.skip;
+  a.mx = p->dx.m; a.my = p->dy.m; a.mz = p->mz;
+  a.ihx = p->dx.ih; a.ihy = p->dy.ih;
+  a.sig = p->sig;
+  return a;
+}
+
+// One pass of steps 1-7: u (=|+=) S(f).  lo = FP32 bulk transforms (mixed path).
+void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int store, int conj_out) {
+  cudaStream_t st = p->st;
+  Workspace& w = p->ws;
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  const long long planes = (long long)R * nz;
+  const int nIx = (int)p->ax.iface.size(), nIy = (int)p->ay.iface.size();
+  auto bulk = lo ? hz::xform_f32 : hz::xform_f64;
+  // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
+  {
+    Stage t(p, HZ_STAGE_FWD);
+    bulk(p->dx.fwd, f, w.G, ny, planes, 1, hz::XS_STORE, 0, p->dy.skip, st);
+    bulk(p->dy.fwd, w.G, w.FT, nx, planes, 0, hz::XS_STORE, 0, p->dx.skip, st);
+  }
+
+  hz::ZSolveArgs za;
+  za.nx = nx; za.ny = ny; za.nz = nz; za.nrhs = R;
+  za.real_cm = p->real_cm;
+  za.skip_i = p->dx.skip; za.skip_j = p->dy.skip;
+  za.rhs = w.FT; za.out = w.V;
+  za.P = p->Pb; za.Q = p->Qb; za.cm = p->cm_b;
+  za.sig = p->sig;
+  za.nIx = nIx; za.nIy = nIy;
+  // Step 2: mode-wise z solves of every block (pass A)
+  {
+    Stage t(p, HZ_STAGE_PASS_A);
+    hz::zsolve(hz::Z_PASS_A, za, st);
+  }
+
+  if (nIx + nIy > 0) {
+    // Step 3: v at the nodes next to the interfaces
+    std::unique_ptr<Stage> t3(new Stage(p, HZ_STAGE_EDGES));
+    if (nIx) {
+      hz::contract_rows(w.V, w.cX, p->dx.edge_coef, p->dx.edge_rng, nx, ny, 2 * nIx, planes, st);
+      hz::xform_f64(p->dy.inv, w.cX, w.vX, 2 * nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    }
+    if (nIy) {
+      hz::contract_cols(w.V, w.cY, p->dy.edge_coef, p->dy.edge_rng, nx, ny, 2 * nIy, planes, st);
+      hz::xform_f64(p->dx.inv, w.cY, w.vY, 2 * nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    }
+    t3.reset();
+    // Step 4: r = M f - A v on the interfaces
+    hz::IfaceArgs ia = iface_args(p, R);
+    {
+      Stage t(p, HZ_STAGE_IRES);
+      hz::iface_residual(ia, f, w.vX, w.vY, w.rX, w.rY, st);
+    }
+    // Step 5: w on the interfaces through the whole-axis eigenbasis
+    std::unique_ptr<Stage> t5(new Stage(p, HZ_STAGE_GLOBAL));
+    if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    hz::ZSolveArgs zg = za;
+    zg.skip_i = nullptr; zg.skip_j = nullptr;
+    zg.out = w.G;                                   // w~ (G is free until step 7)
+    zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
+    zg.aX = w.aX; zg.bY = w.bY; zg.WgxI = p->dx.gcoef; zg.WgyI = p->dy.gcoef;
+    hz::zsolve(hz::Z_GLOBAL, zg, st);
+    if (nIx) {
+      hz::contract_rows(w.G, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
+      hz::xform_f64(p->dy.ginv, w.cg, w.wX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      // Step 6 (x interfaces): forward y-transform of w on the interface rows
+      hz::xform_f64(p->dy.fwd, w.wX, w.alX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    }
+    if (nIy) {
+      hz::contract_cols(w.G, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, st);
+      hz::xform_f64(p->dx.ginv, w.dg, w.wY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dx.fwd, w.wY, w.alY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    }
+    t5.reset();
+    // Step 6: pass B, (Tz + s S_z) u~ = M_z f~ + g~ with g~ generated from the interface data
+    Stage t6(p, HZ_STAGE_PASS_B);
+    hz::ZSolveArgs zb = za;
+    zb.alphaX = w.alX; zb.alphaY = w.alY;
+    zb.gxl = p->dx.gl; zb.gxr = p->dx.gr; zb.gyl = p->dy.gl; zb.gyr = p->dy.gr;
+    zb.cxl = p->dx.cl; zb.cxr = p->dx.cr; zb.cyl = p->dy.cl; zb.cyr = p->dy.cr;
+    hz::zsolve(hz::Z_PASS_B, zb, st);
+  }
+  // Step 7: u = W_x (x) W_y u~ in the blocks; u = w on the interfaces
+  {
+    Stage t(p, HZ_STAGE_INV);
+    bulk(p->dy.inv, w.V, w.G, nx, planes, 1, hz::XS_STORE, 0, p->dx.skip, st);
+    bulk(p->dx.inv, w.G, u, ny, planes, 0, store, conj_out, p->dy.skip, st);
+  }
+  if (nIx + nIy > 0) {
+    Stage t(p, HZ_STAGE_IFACE_OUT);
+    hz::IfaceArgs ia = iface_args(p, R);
+    hz::write_iface(ia, w.wX, w.wY, u, conj_out, store == hz::XS_ACCUM, st);
+  }
+  ck(cudaGetLastError());
+}
+
+hz::StencilArgs stencil_args(hz_plan_t p, int R) {
+  hz::StencilArgs a;
+  a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nrhs = R;
+  a.kxs = p->dx.ks; a.kys = p->dy.ks; a.tzs = p->tzs; a.sig = p->sig;
+  a.mx = p->dx.m; a.my = p->dy.m; a.mz = p->mz;
+  return a;
+}
+
+// rho = f - M^{-1} A u; returns max over RHS of ||M rho|| / ||M f||.
+double residual_core(hz_plan_t p, const double2* f, const double2* u, double2* rho, int R,
+                     std::vector<double>* per_rhs) {
+  hz::StencilArgs a = stencil_args(p, R);
+  const int parts = hz::stencil_parts(a);
+  {
+    Stage t(p, HZ_STAGE_RESID);
+    hz::stencil_residual(a, f, u, rho, p->ws.partial, parts, p->st);
+    hz::finish_norms(p->ws.partial, parts, R, p->ws.norms, p->st);
+  }
+  ck(cudaGetLastError());
+  std::vector<double> nrm(2 * R);
+  ck(cudaMemcpyAsync(nrm.data(), p->ws.norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ck(cudaStreamSynchronize(p->st));
+  double worst = 0.0;
+  if (per_rhs) per_rhs->assign(R, 0.0);
+  for (int r = 0; r < R; ++r) {
+    const double rel = nrm[2 * r + 1] > 0 ? std::sqrt(nrm[2 * r] / nrm[2 * r + 1]) : std::sqrt(nrm[2 * r]);
+    if (!std::isfinite(rel)) throw Fail{HZ_ERR_NONFINITE};
+    if (per_rhs) (*per_rhs)[r] = rel;
+    worst = std::max(worst, rel);
+  }
+  return worst;
+}
+
+// Full solve: FP64 single pass, or mixed with FP64 refinement.
+void solve_full_impl(hz_plan_t p, const double2* f, double2* u, int R, int conj_out);
+
+void solve_full(hz_plan_t p, const double2* f, double2* u, int R, int conj_out) {
+  const long long l0 = hz::launch_count();
+  solve_full_impl(p, f, u, R, conj_out);
+  p->info.kernel_launches += hz::launch_count() - l0;
+  if (p->timing) collect_stages(p);
+}
+
+void solve_full_impl(hz_plan_t p, const double2* f, double2* u, int R, int conj_out) {
+  ensure_ws(p, R);
+  p->info.refinements = 0;
+  p->info.rel_residual = -1.0;
+  if (p->opts.precision != HZ_MIXED) {
+    solve_core(p, f, u, R, false, hz::XS_STORE, conj_out);
+    ck(cudaStreamSynchronize(p->st));
+    return;
+  }
+  const double2* fin = f;
+  if (f == u) {   // refinement needs f after u is written
+    double2* f2 = ensure_extra(p, p->ws.F2, p->ws.f2_cap, R);
+    ck(cudaMemcpyAsync(f2, f, sizeof(double2) * (size_t)p->nx * p->ny * p->nz * R,
+                       cudaMemcpyDeviceToDevice, p->st));
+    fin = f2;
+  }
+  double2* rho = ensure_extra(p, p->ws.RHO, p->ws.rho_cap, R);
+  solve_core(p, fin, u, R, true, hz::XS_STORE, 0);
+  double rel = residual_core(p, fin, u, rho, R, nullptr);
+  int it = 0;
+  while (rel > p->opts.rtol && it < p->opts.max_refine) {
+    solve_core(p, rho, u, R, true, hz::XS_ACCUM, 0);
+    rel = residual_core(p, fin, u, rho, R, nullptr);
+    ++it;
+  }
+  p->info.refinements = it;
+  p->info.rel_residual = rel;
+  if (conj_out) {
+    hz::conj_inplace(u, (long long)p->nx * p->ny * p->nz * R, p->st);
+    ck(cudaStreamSynchronize(p->st));
+  }
+  if (rel > p->opts.rtol) throw Fail{HZ_ERR_NOT_CONVERGED};
+}
+
+void release(hz_plan_t p) {
+  for (void* a : p->allocs) cudaFree(a);
+  p->allocs.clear();
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pool.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hz_status_str(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "ok";
+    case HZ_ERR_ARG: return "invalid argument";
+    case HZ_ERR_EIG: return "eigen-decomposition failed its checks";
+    case HZ_ERR_SINGULAR: return "zero or non-finite pivot in a z elimination";
+    case HZ_ERR_NONFINITE: return "non-finite value";
+    case HZ_ERR_NOT_CONVERGED: return "iterative refinement did not reach rtol";
+    case HZ_ERR_OOM: return "device allocation failed";
+    case HZ_ERR_CUDA: return "CUDA runtime error";
+    case HZ_ERR_TIMEOUT: return "bounded device wait gave up";
+  }
+  return "unknown status";
+}
+
+hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_blocks* blocks,
+                         const hz_options* opts, hz_plan_t* out) {
+  if (!out) return HZ_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !layers || !grid->hx || !grid->hy || !grid->hz) return HZ_ERR_ARG;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return HZ_ERR_ARG;
+  if (layers->nlayers < 1 || !layers->z_begin || !layers->k2) return HZ_ERR_ARG;
+  const int nl = layers->nlayers;
+  if (layers->z_begin[0] != 0 || layers->z_begin[nl] != grid->nz) return HZ_ERR_ARG;
+  for (int L = 0; L < nl; ++L) {
+    if (layers->z_begin[L + 1] <= layers->z_begin[L]) return HZ_ERR_ARG;
+    if (!std::isfinite(layers->k2[L].re) || !std::isfinite(layers->k2[L].im)) return HZ_ERR_ARG;
+    if (layers->sigma && !(layers->sigma[L] > 0.0 && std::isfinite(layers->sigma[L]))) return HZ_ERR_ARG;
+  }
+  const int nbx = blocks ? blocks->nbx : 1, nby = blocks ? blocks->nby : 1;
+  if (nbx < 1 || nby < 1 || nbx > grid->nx || nby > grid->ny) return HZ_ERR_ARG;
+  if (opts && (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED)) return HZ_ERR_ARG;
+
+  hz_plan_t p = new (std::nothrow) hz_plan_s();
+  if (!p) return HZ_ERR_OOM;
+  const auto t0 = std::chrono::steady_clock::now();
+  p->nx = grid->nx; p->ny = grid->ny; p->nz = grid->nz; p->nlayers = nl;
+  if (opts) p->opts = *opts;
+  else { p->opts.precision = HZ_FP64; p->opts.rtol = 1e-8; p->opts.max_refine = 10; p->opts.cuda_stream = nullptr; }
+  if (!(p->opts.rtol > 0)) p->opts.rtol = 1e-8;
+  if (p->opts.max_refine < 0) p->opts.max_refine = 0;
+  p->st = (cudaStream_t)p->opts.cuda_stream;
+  p->hz.resize(grid->nz + 1);
+  for (int k = 0; k <= grid->nz; ++k) {
+    p->hz[k] = cd(grid->hz[k].re, grid->hz[k].im);
+    if (!finite(p->hz[k]) || std::abs(p->hz[k]) == 0.0) { delete p; return HZ_ERR_ARG; }
+  }
+  p->z_begin.assign(layers->z_begin, layers->z_begin + nl + 1);
+  p->k2base.resize(nl);
+  for (int L = 0; L < nl; ++L) p->k2base[L] = cd(layers->k2[L].re, layers->k2[L].im);
+  if (layers->sigma) p->sig_layer.assign(layers->sigma, layers->sigma + nl);
+
+  hz_status s = build_axis(p->ax, grid->nx, grid->hx, nbx, blocks ? blocks->x_iface : nullptr);
+  if (s == HZ_OK) s = build_axis(p->ay, grid->ny, grid->hy, nby, blocks ? blocks->y_iface : nullptr);
+  p->need_global = (nbx > 1 || nby > 1);
+  if (s == HZ_OK && p->need_global) {
+    s = build_global(p->ax);
+    if (s == HZ_OK) s = build_global(p->ay);
+  }
+  if (s == HZ_OK) {
+    p->info.eig_max_residual = std::max(p->ax.eig_res, p->ay.eig_res);
+    if (!(p->info.eig_max_residual < 1e-9)) s = HZ_ERR_EIG;
+  }
+  if (s != HZ_OK) { delete p; return s; }
+  try {
+    p->status = dalloc<int>(p, 1);
+    p->minpiv = dalloc<unsigned long long>(p, 1);
+    build_axis_dev(p, p->ax, p->dx, p->need_global);
+    build_axis_dev(p, p->ay, p->dy, p->need_global);
+    build_z(p);
+    ck(cudaStreamSynchronize(p->st));
+  } catch (const Fail& e) {
+    release(p);
+    delete p;
+    return e.s;
+  }
+  p->info.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  p->info.device_bytes = p->bytes;
+  *out = p;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_frequency(hz_plan_t p, double omega) {
+  if (!p || !std::isfinite(omega)) return HZ_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  p->omega = omega;
+  try {
+    build_z(p);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  p->info.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_k2(hz_plan_t p, const hz_c128* k2) {
+  if (!p || !k2) return HZ_ERR_ARG;
+  for (int L = 0; L < p->nlayers; ++L)
+    if (!std::isfinite(k2[L].re) || !std::isfinite(k2[L].im)) return HZ_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int L = 0; L < p->nlayers; ++L) p->k2base[L] = cd(k2[L].re, k2[L].im);
+  try {
+    build_z(p);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  p->info.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return HZ_OK;
+}
+
+hz_status hz_tridiag_eig(int n, const hz_c128* kd, const hz_c128* ko, const hz_c128* m, hz_c128* lam,
+                         hz_c128* W, double* residual) {
+  if (n < 1 || !kd || !m || !lam || !W || (n > 1 && !ko)) return HZ_ERR_ARG;
+  std::vector<cd> d(n), o(std::max(n - 1, 1)), mm(n), l, w;
+  for (int i = 0; i < n; ++i) {
+    d[i] = cd(kd[i].re, kd[i].im);
+    mm[i] = cd(m[i].re, m[i].im);
+  }
+  for (int i = 0; i + 1 < n; ++i) o[i] = cd(ko[i].re, ko[i].im);
+  double res = 0.0;
+  if (!hz::tridiag_eig(n, d.data(), o.data(), mm.data(), l, w, &res)) return HZ_ERR_EIG;
+  for (int i = 0; i < n; ++i) lam[i] = hz_c128{l[i].real(), l[i].imag()};
+  for (size_t i = 0; i < (size_t)n * n; ++i) W[i] = hz_c128{w[i].real(), w[i].imag()};
+  if (residual) *residual = res;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_options(hz_plan_t p, const hz_options* opts) {
+  if (!p || !opts) return HZ_ERR_ARG;
+  if (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED) return HZ_ERR_ARG;
+  p->opts = *opts;
+  if (!(p->opts.rtol > 0)) p->opts.rtol = 1e-8;
+  if (p->opts.max_refine < 0) p->opts.max_refine = 0;
+  p->st = (cudaStream_t)opts->cuda_stream;
+  return HZ_OK;
+}
+
+hz_status hz_solve(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
+  if (!p || !f || !u || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    solve_full(p, reinterpret_cast<const double2*>(f), reinterpret_cast<double2*>(u), nrhs, 0);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_solve_host(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
+  if (!p || !f || !u || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    ensure_ws(p, nrhs);
+    const size_t bytes = sizeof(double2) * (size_t)p->nx * p->ny * p->nz * nrhs;
+    double2* fd = ensure_extra(p, p->ws.F2, p->ws.f2_cap, nrhs);
+    double2* ud = ensure_extra(p, p->ws.HU, p->ws.hu_cap, nrhs);
+    ck(cudaMemcpyAsync(fd, f, bytes, cudaMemcpyHostToDevice, p->st));
+    solve_full(p, fd, ud, nrhs, 0);
+    ck(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, p->st));
+    ck(cudaStreamSynchronize(p->st));
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_solve_adjoint(hz_plan_t p, const hz_c128* g, hz_c128* lam, int nrhs) {
+  if (!p || !g || !lam || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    ensure_ws(p, nrhs);
+    double2* f2 = ensure_extra(p, p->ws.F2, p->ws.f2_cap, nrhs);
+    hz::adjoint_prep(reinterpret_cast<const double2*>(g), f2, p->dx.im, p->dy.im, p->imz, p->nx, p->ny,
+                     p->nz, nrhs, p->st);
+    solve_full(p, f2, reinterpret_cast<double2*>(lam), nrhs, 1);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_grad_layers(hz_plan_t p, const hz_c128* u, const hz_c128* lam, int nrhs, hz_c128* G_host) {
+  if (!p || !u || !lam || !G_host || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    Workspace& w = p->ws;
+    const int parts = hz::grad_parts(p->nx, p->ny, nrhs);
+    dfree(p, w.gpart);
+    dfree(p, w.Gl);
+    w.gpart = dalloc<double2>(p, (size_t)parts * p->nz);
+    w.Gl = dalloc<double2>(p, p->nlayers);
+    hz::grad_layers(reinterpret_cast<const double2*>(u), reinterpret_cast<const double2*>(lam), p->dx.m,
+                    p->dy.m, p->mz, p->zb, p->nlayers, p->nx, p->ny, p->nz, nrhs, w.gpart, parts, w.Gl,
+                    p->st);
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(G_host, w.Gl, sizeof(double2) * p->nlayers, cudaMemcpyDeviceToHost, p->st));
+    ck(cudaStreamSynchronize(p->st));
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_residual(hz_plan_t p, const hz_c128* f, const hz_c128* u, int nrhs, double* rel_host) {
+  if (!p || !f || !u || !rel_host || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    ensure_ws(p, nrhs);
+    double2* rho = ensure_extra(p, p->ws.RHO, p->ws.rho_cap, nrhs);
+    std::vector<double> rel;
+    residual_core(p, reinterpret_cast<const double2*>(f), reinterpret_cast<const double2*>(u), rho, nrhs, &rel);
+    for (int r = 0; r < nrhs; ++r) rel_host[r] = rel[r];
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_set_stage_timing(hz_plan_t p, int enable) {
+  if (!p) return HZ_ERR_ARG;
+  if (cudaStreamSynchronize(p->st) != cudaSuccess) return HZ_ERR_CUDA;
+  collect_stages(p);
+  p->timing = enable != 0;
+  for (int s = 0; s < HZ_NSTAGES; ++s) {
+    p->stage_ms[s] = 0.0;
+    p->stage_launches[s] = 0;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_get_stage_times(hz_plan_t p, double* ms, long long* launches) {
+  if (!p) return HZ_ERR_ARG;
+  for (int s = 0; s < HZ_NSTAGES; ++s) {
+    if (ms) ms[s] = p->stage_ms[s];
+    if (launches) launches[s] = p->stage_launches[s];
+  }
+  return HZ_OK;
+}
+
+hz_status hz_get_info(hz_plan_t p, hz_info* out) {
+  if (!p || !out) return HZ_ERR_ARG;
+  p->info.device_bytes = p->bytes;
+  *out = p->info;
+  return HZ_OK;
+}
+
+hz_status hz_plan_destroy(hz_plan_t p) {
+  if (!p) return HZ_ERR_ARG;
+  cudaStreamSynchronize(p->st);
+  release(p);
+  delete p;
+  return HZ_OK;
+}
+
+}  // extern "C"

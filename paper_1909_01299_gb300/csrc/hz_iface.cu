@@ -1,0 +1,372 @@
+// Interface steps of Sec. 2 (steps 3-6), the FP64 residual stencil and the
+// layer-gradient reduction.
+//
+//  * contract_rows / contract_cols: the first half of every transform that is
+//    only needed on a few rows -- v next to the interfaces (step 3) is
+//    W_x[e,:] V~ W_y^T, and w on the interfaces (step 5) is W_x[p,:] w~ W_y^T;
+//    the contraction with one eigenvector row is done here, the remaining
+//    short transform by the row-transform kernels.
+//  * iface_residual: step 4, r = M f - A v on the interface planes.  v is zero
+//    on the interfaces, so only the couplings to the two neighbouring nodes
+//    across the interface enter (residual support, Sec. 2).
+//  * write_iface: step 7 on the interfaces, u = w there.
+//  * stencil_residual: rho = f - M^{-1} A u with the 7-point operator of
+//    Eq. (fd)/(fdmtr), for iterative refinement and residual reports.
+//  * grad_layers: G_L = sum_{k in L} hhat^z_k sum conj(lam) hhat^x hhat^y u.
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
+  return make_double2(fma(c.x, y.x, fma(-c.y, y.y, acc.x)), fma(c.x, y.y, fma(c.y, y.x, acc.y)));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+                                     const double2* __restrict__ coef, const int2* __restrict__ range,
+                                     int nrows, int ncols, int nslots, long long nplanes) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = nplanes * nslots * (long long)ncols;
+  if (t >= total) return;
+  const int j = (int)(t % ncols);
+  const long long ps = t / ncols;
+  const int s = (int)(ps % nslots);
+  const long long plane = ps / nslots;
+  const int2 rg = range[s];
+  const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
+  const double2* __restrict__ c = coef + (long long)s * nrows;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = rg.x; i < rg.y; ++i) acc = cfma(c[i], v[(long long)i * ncols], acc);
+  out[t] = acc;
+}
+
+__global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+                                     const double2* __restrict__ coef, const int2* __restrict__ range,
+                                     int nrows, int ncols, int nslots, long long nplanes) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = nplanes * nslots * (long long)nrows;
+  if (t >= total) return;
+  const int i = (int)(t % nrows);
+  const long long ps = t / nrows;
+  const int s = (int)(ps % nslots);
+  const long long plane = ps / nslots;
+  const int2 rg = range[s];
+  const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
+  const double2* __restrict__ c = coef + (long long)s * ncols;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
+  out[t] = acc;
+}
+
+// rX[r][k][p][j] for all j; rY[r][k][q][i] for all i (0 where i is an x-interface).
+__global__ void iface_residual_kernel(const IfaceArgs a, const double2* __restrict__ f,
+                                      const double2* __restrict__ vX, const double2* __restrict__ vY,
+                                      double2* __restrict__ rX, double2* __restrict__ rY) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nXe = (long long)a.nrhs * a.nz * a.nIx * a.ny;
+  const long long nYe = (long long)a.nrhs * a.nz * a.nIy * a.nx;
+  if (t < nXe) {
+    const int j = (int)(t % a.ny);
+    const long long rkp = t / a.ny;
+    const int p = (int)(rkp % a.nIx);
+    const long long rk = rkp / a.nIx;
+    const int k = (int)(rk % a.nz);
+    const int r = (int)(rk / a.nz);
+    const int node = a.xif[p];
+    const double2 mzk = a.mz[k], myj = a.my[j];
+    const double2 fv = f[(((long long)r * a.nz + k) * a.ny + j) * a.nx + node];
+    double2 res = cmul(cmul(a.mx[node], myj), cmul(mzk, fv));
+    if (!a.isy[j]) {
+      const double2 vl = vX[(rk * 2 * a.nIx + 2 * p) * a.ny + j];
+      const double2 vr = vX[(rk * 2 * a.nIx + 2 * p + 1) * a.ny + j];
+      double2 nb = cfma(a.ihx[node + 1], vr, cmul(a.ihx[node], vl));
+      double2 w = cmul(myj, mzk);
+      if (a.sig) { w.x *= a.sig[k]; w.y *= a.sig[k]; }
+      res = cfma(w, nb, res);
+    }
+    rX[t] = res;
+  } else if (t < nXe + nYe) {
+    const long long u = t - nXe;
+    const int i = (int)(u % a.nx);
+    const long long rkq = u / a.nx;
+    const int q = (int)(rkq % a.nIy);
+    const long long rk = rkq / a.nIy;
+    const int k = (int)(rk % a.nz);
+    const int r = (int)(rk / a.nz);
+    if (a.isx[i]) { rY[u] = make_double2(0.0, 0.0); return; }
+    const int node = a.yif[q];
+    const double2 mzk = a.mz[k], mxi = a.mx[i];
+    const double2 fv = f[(((long long)r * a.nz + k) * a.ny + node) * a.nx + i];
+    double2 res = cmul(cmul(mxi, a.my[node]), cmul(mzk, fv));
+    const double2 vl = vY[(rk * 2 * a.nIy + 2 * q) * a.nx + i];
+    const double2 vr = vY[(rk * 2 * a.nIy + 2 * q + 1) * a.nx + i];
+    double2 nb = cfma(a.ihy[node + 1], vr, cmul(a.ihy[node], vl));
+    double2 w = cmul(mxi, mzk);
+    if (a.sig) { w.x *= a.sig[k]; w.y *= a.sig[k]; }
+    rY[u] = cfma(w, nb, res);
+  }
+}
+
+__global__ void write_iface_kernel(const IfaceArgs a, const double2* __restrict__ wX,
+                                   const double2* __restrict__ wY, double2* __restrict__ u,
+                                   int conj_out, int accumulate) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nXe = (long long)a.nrhs * a.nz * a.nIx * a.ny;
+  const long long nYe = (long long)a.nrhs * a.nz * a.nIy * a.nx;
+  double2 v;
+  long long dst;
+  if (t < nXe) {
+    const int j = (int)(t % a.ny);
+    const long long rkp = t / a.ny;
+    const int p = (int)(rkp % a.nIx);
+    const long long rk = rkp / a.nIx;
+    v = wX[t];
+    dst = (rk * a.ny + j) * a.nx + a.xif[p];
+  } else if (t < nXe + nYe) {
+    const long long s = t - nXe;
+    const int i = (int)(s % a.nx);
+    if (a.isx[i]) return;
+    const long long rkq = s / a.nx;
+    const int q = (int)(rkq % a.nIy);
+    const long long rk = rkq / a.nIy;
+    v = wY[s];
+    dst = (rk * a.ny + a.yif[q]) * a.nx + i;
+  } else {
+    return;
+  }
+  if (conj_out) v.y = -v.y;
+  if (accumulate) {
+    double2 o = u[dst];
+    v.x += o.x;
+    v.y += o.y;
+  }
+  u[dst] = v;
+}
+
+__global__ void adjoint_prep_kernel(const double2* __restrict__ g, double2* __restrict__ out,
+                                    const double2* __restrict__ imx, const double2* __restrict__ imy,
+                                    const double2* __restrict__ imz, int nx, int ny, int nz,
+                                    long long total) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int i = (int)(t % nx);
+  const long long q = t / nx;
+  const int j = (int)(q % ny);
+  const int k = (int)((q / ny) % nz);
+  double2 v = g[t];
+  v.y = -v.y;
+  out[t] = cmul(cmul(v, imx[i]), cmul(imy[j], imz[k]));
+}
+
+__global__ void conj_kernel(double2* __restrict__ u, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) u[t].y = -u[t].y;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NT / 32; ++q) s += sh[q];
+  return s;
+}
+
+constexpr int ST = 256;
+
+// grid (nparts, nrhs): each CTA strides over one RHS's elements.
+__global__ void __launch_bounds__(ST) stencil_kernel(const StencilArgs a, const double2* __restrict__ f,
+                                                     const double2* __restrict__ u,
+                                                     double2* __restrict__ rho,
+                                                     double* __restrict__ partial) {
+  __shared__ double sh[ST / 32];
+  const int r = blockIdx.y;
+  const long long nxy = (long long)a.nx * a.ny;
+  const long long n = nxy * a.nz;
+  const double2* __restrict__ ur = u + r * n;
+  const double2* __restrict__ fr = f + r * n;
+  double2* __restrict__ pr = rho + r * n;
+  double nr2 = 0.0, nf2 = 0.0;
+  for (long long t = blockIdx.x * (long long)ST + threadIdx.x; t < n; t += (long long)gridDim.x * ST) {
+    const int i = (int)(t % a.nx);
+    const long long q = t / a.nx;
+    const int j = (int)(q % a.ny);
+    const int k = (int)(q / a.ny);
+    const double2 uc = ur[t];
+    const double2* kx = a.kxs + 3 * i;
+    const double2* ky = a.kys + 3 * j;
+    const double2* tz = a.tzs + 3 * k;
+    const double s = a.sig ? a.sig[k] : 1.0;
+    // horizontal part sigma_k (Kx' u + Ky' u)
+    double2 h = cmul(cadd(kx[1], ky[1]), uc);
+    if (i > 0) h = cfma(kx[0], ur[t - 1], h);
+    if (i < a.nx - 1) h = cfma(kx[2], ur[t + 1], h);
+    if (j > 0) h = cfma(ky[0], ur[t - a.nx], h);
+    if (j < a.ny - 1) h = cfma(ky[2], ur[t + a.nx], h);
+    double2 au = cmul(tz[1], uc);
+    au.x = fma(s, h.x, au.x);
+    au.y = fma(s, h.y, au.y);
+    if (k > 0) au = cfma(tz[0], ur[t - nxy], au);
+    if (k < a.nz - 1) au = cfma(tz[2], ur[t + nxy], au);
+    const double2 fv = fr[t];
+    const double2 res = make_double2(fv.x - au.x, fv.y - au.y);
+    pr[t] = res;
+    const double2 mx = a.mx[i], my = a.my[j], mz = a.mz[k];
+    const double w2 = (mx.x * mx.x + mx.y * mx.y) * (my.x * my.x + my.y * my.y) * (mz.x * mz.x + mz.y * mz.y);
+    nr2 = fma(w2, res.x * res.x + res.y * res.y, nr2);
+    nf2 = fma(w2, fv.x * fv.x + fv.y * fv.y, nf2);
+  }
+  const double s1 = block_sum<ST>(nr2, sh);
+  const double s2 = block_sum<ST>(nf2, sh);
+  if (threadIdx.x == 0) {
+    partial[((long long)r * gridDim.x + blockIdx.x) * 2 + 0] = s1;
+    partial[((long long)r * gridDim.x + blockIdx.x) * 2 + 1] = s2;
+  }
+}
+
+__global__ void finish_norms_kernel(const double* __restrict__ partial, int nparts, double* out) {
+  const int r = blockIdx.x;
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += partial[((long long)r * nparts + p) * 2 + threadIdx.x];
+    out[2 * r + threadIdx.x] = s;
+  }
+}
+
+// grid (nparts, nz): CTA sums conj(lam) mx my u over a slice of (r, j, i) of plane k.
+__global__ void __launch_bounds__(ST) grad_kernel(const double2* __restrict__ u,
+                                                  const double2* __restrict__ lam,
+                                                  const double2* __restrict__ mx,
+                                                  const double2* __restrict__ my, int nx, int ny,
+                                                  int nz, int nrhs, double2* __restrict__ partial) {
+  __shared__ double sh[ST / 32];
+  const int k = blockIdx.y;
+  const long long nxy = (long long)nx * ny;
+  const long long n = nxy * nrhs;
+  double sr = 0.0, si = 0.0;
+  for (long long t = blockIdx.x * (long long)ST + threadIdx.x; t < n; t += (long long)gridDim.x * ST) {
+    const int r = (int)(t / nxy);
+    const long long pos = t - (long long)r * nxy;
+    const int j = (int)(pos / nx), i = (int)(pos - (long long)j * nx);
+    const long long idx = ((long long)r * nz + k) * nxy + pos;
+    double2 l = lam[idx];
+    l.y = -l.y;
+    const double2 v = cmul(cmul(l, u[idx]), cmul(mx[i], my[j]));
+    sr += v.x;
+    si += v.y;
+  }
+  const double a = block_sum<ST>(sr, sh);
+  const double b = block_sum<ST>(si, sh);
+  if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = make_double2(a, b);
+}
+
+__global__ void grad_finish_kernel(const double2* __restrict__ partial, int nparts,
+                                   const double2* __restrict__ mz, const int* __restrict__ z_begin,
+                                   int nlayers, double2* __restrict__ G) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlayers) return;
+  double2 g = make_double2(0.0, 0.0);
+  for (int k = z_begin[L]; k < z_begin[L + 1]; ++k) {
+    double2 pk = make_double2(0.0, 0.0);
+    for (int p = 0; p < nparts; ++p) pk = cadd(pk, partial[(long long)k * nparts + p]);
+    g = cfma(mz[k], pk, g);
+  }
+  G[L] = g;
+}
+
+unsigned blocks_for(long long n, int T) { return (unsigned)((n + T - 1) / T); }
+
+}  // namespace
+
+void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  const long long n = nplanes * nslots * (long long)ncols;
+  if (n == 0) return;
+  contract_rows_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  count_launch();
+}
+
+void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  const long long n = nplanes * nslots * (long long)nrows;
+  if (n == 0) return;
+  contract_cols_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  count_launch();
+}
+
+void iface_residual(const IfaceArgs& a, const double2* f, const double2* vX, const double2* vY,
+                    double2* rX, double2* rY, cudaStream_t st) {
+  const long long n = (long long)a.nrhs * a.nz * ((long long)a.nIx * a.ny + (long long)a.nIy * a.nx);
+  if (n == 0) return;
+  iface_residual_kernel<<<blocks_for(n, 128), 128, 0, st>>>(a, f, vX, vY, rX, rY);
+  count_launch();
+}
+
+void write_iface(const IfaceArgs& a, const double2* wX, const double2* wY, double2* u, int conj_out,
+                 int accumulate, cudaStream_t st) {
+  const long long n = (long long)a.nrhs * a.nz * ((long long)a.nIx * a.ny + (long long)a.nIy * a.nx);
+  if (n == 0) return;
+  write_iface_kernel<<<blocks_for(n, 128), 128, 0, st>>>(a, wX, wY, u, conj_out, accumulate);
+  count_launch();
+}
+
+void adjoint_prep(const double2* g, double2* out, const double2* imx, const double2* imy,
+                  const double2* imz, int nx, int ny, int nz, int nrhs, cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz * nrhs;
+  if (n == 0) return;
+  adjoint_prep_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g, out, imx, imy, imz, nx, ny, nz, n);
+  count_launch();
+}
+
+void conj_inplace(double2* u, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  conj_kernel<<<blocks_for(n, 256), 256, 0, st>>>(u, n);
+  count_launch();
+}
+
+int stencil_parts(const StencilArgs& a) {
+  const long long n = (long long)a.nx * a.ny * a.nz;
+  long long parts = (n + ST * 8 - 1) / (ST * 8);
+  const long long cap = (4LL * 152 + a.nrhs - 1) / a.nrhs;
+  if (parts > cap) parts = cap;
+  return parts < 1 ? 1 : (int)parts;
+}
+
+void stencil_residual(const StencilArgs& a, const double2* f, const double2* u, double2* rho,
+                      double* partial, int nparts, cudaStream_t st) {
+  dim3 grid(nparts, a.nrhs);
+  stencil_kernel<<<grid, ST, 0, st>>>(a, f, u, rho, partial);
+  count_launch();
+}
+
+void finish_norms(const double* partial, int nparts, int nrhs, double* out, cudaStream_t st) {
+  finish_norms_kernel<<<nrhs, 32, 0, st>>>(partial, nparts, out);
+  count_launch();
+}
+
+int grad_parts(int nx, int ny, int nrhs) {
+  const long long n = (long long)nx * ny * nrhs;
+  long long parts = (n + ST * 8 - 1) / (ST * 8);
+  if (parts > 64) parts = 64;
+  return parts < 1 ? 1 : (int)parts;
+}
+
+void grad_layers(const double2* u, const double2* lam, const double2* mx, const double2* my,
+                 const double2* mz, const int* z_begin, int nlayers, int nx, int ny, int nz, int nrhs,
+                 double2* partial, int nparts, double2* G, cudaStream_t st) {
+  dim3 grid(nparts, nz);
+  grad_kernel<<<grid, ST, 0, st>>>(u, lam, mx, my, nx, ny, nz, nrhs, partial);
+  count_launch();
+  grad_finish_kernel<<<(nlayers + 63) / 64, 64, 0, st>>>(partial, nparts, mz, z_begin, nlayers, G);
+  count_launch();
+}
+
+}  // namespace hz

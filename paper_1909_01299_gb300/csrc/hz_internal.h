@@ -1,0 +1,172 @@
+// Internal declarations of the hz library: host plan, device tables, kernel launchers.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hz.h"
+
+namespace hz {
+
+using cd = std::complex<double>;
+
+// Every kernel launcher calls this once per launch (launch accounting for reports).
+void count_launch(int n = 1);
+long long launch_count();
+
+// Complex-symmetric generalised tridiagonal eigenpairs K W = M W Lambda, W^T M W = I.
+// kd: n diagonal, ko: n-1 off-diagonal, m: n diagonal of M.  W is row-major n x n
+// (W[i*n + l] = component at node i of mode l).  Returns false on failure.
+bool tridiag_eig(int n, const cd* kd, const cd* ko, const cd* m, std::vector<cd>& lam,
+                 std::vector<cd>& W, double* eig_residual);
+
+// ---------------------------------------------------------------------------
+// Row transforms: out_row[s + c] = sum_a in_row[s + a] * B_b[a][c] for every block b
+// covering columns [s, s + n) of a row of length ncols (block-diagonal B).
+// ---------------------------------------------------------------------------
+struct XBlock {
+  int start;            // first column of the block in the row
+  int size;             // block width n
+  int real;             // 1: table is real (one n*n plane); 0: complex
+  int pad;
+  long long toff;       // offset (doubles) of the FP64 table; complex entries c + i d are
+                        //    stored for the 3M product as three planes [c | d - c | c + d]
+  long long toff32;     // offset (floats) of the FP32 table; complex: two planes [c | d]
+};
+struct XTile {
+  int blk;              // block index
+  int c0;               // first output column within the block
+  int cw;               // number of output columns of the tile (<= tile width)
+  int pad;
+};
+
+// A device-resident block-diagonal transform (one per axis and use).
+struct XformSet {
+  int ncols = 0;                  // row length (axis length)
+  int nblocks = 0;
+  int ntiles = 0;
+  XBlock* d_blocks = nullptr;
+  XTile* d_tiles = nullptr;
+  double* d_tab = nullptr;        // FP64 tables (3M layout for complex blocks)
+  float* d_tab32 = nullptr;       // FP32 copy of the same tables for the mixed path
+  std::vector<XBlock> h_blocks;
+};
+
+enum XformStore { XS_STORE = 0, XS_ACCUM = 1 };
+
+// FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
+// trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out
+// has the input's layout.  store: XS_STORE or XS_ACCUM (out += result).  conj_out
+// conjugates the result before it is stored.
+// rowskip (may be NULL) flags rows (index within the plane) that are neither computed nor
+// written: the interface rows, which belong to no block.
+void xform_f64(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
+               long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
+               cudaStream_t st);
+// Same contraction with FP32 arithmetic on FP64 data (SIMT FFMA), for the mixed path.
+void xform_f32(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
+               long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
+               cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// z solves per mode (Eq. (fdmtrprjfr), Eq. (fdmtrprjfrerr))
+// ---------------------------------------------------------------------------
+struct ZFactors {
+  double2* P = nullptr;           // [k][i][j]: scaled inverse pivot
+  double2* Q = nullptr;           // [k][i][j]: back-substitution multiplier c_{k+1} / d_k
+  double2* cm = nullptr;          // [k]: forward multiplier c_k (/ mz_k when folded)
+};
+
+struct ZSolveArgs {
+  const double2* rhs = nullptr;   // mode-layout right-hand side [r][k][i][j] (pass A/B)
+  double2* out = nullptr;         // mode-layout result [r][k][i][j]
+  const double2* P = nullptr;
+  const double2* Q = nullptr;
+  const double2* cm = nullptr;
+  const signed char* skip_i = nullptr;   // 1 at x-interface positions (block passes)
+  const signed char* skip_j = nullptr;
+  int nx = 0, ny = 0, nz = 0, nrhs = 0;
+  int real_cm = 0;
+  // pass B: boundary right-hand side sigma_k (cxl aX[pl] + cxr aX[pr] + cyl aY[ql] + cyr aY[qr])
+  const double* sig = nullptr;           // [k]
+  const double2* alphaX = nullptr;       // [r][k][nIx][ny]
+  const double2* alphaY = nullptr;       // [r][k][nIy][nx]
+  const int* gxl = nullptr; const int* gxr = nullptr;     // per i: interface index or -1
+  const int* gyl = nullptr; const int* gyr = nullptr;     // per j
+  const double2* cxl = nullptr; const double2* cxr = nullptr;   // per i
+  const double2* cyl = nullptr; const double2* cyr = nullptr;   // per j
+  // global pass: rhs = sum_p WgxI[p][i] aX[r][k][p][j] + sum_q WgyI[q][j] bY[r][k][q][i]
+  const double2* aX = nullptr;           // [r][k][nIx][ny]
+  const double2* bY = nullptr;           // [r][k][nIy][nx]
+  const double2* WgxI = nullptr;         // [nIx][nx]
+  const double2* WgyI = nullptr;         // [nIy][ny]
+  int nIx = 0, nIy = 0;
+};
+
+enum ZMode { Z_PASS_A = 0, Z_PASS_B = 1, Z_GLOBAL = 2 };
+void zsolve(int mode, const ZSolveArgs& a, cudaStream_t st);
+
+// Elimination factors of (Tz + s_ij S_z) for every (i, j) with s_ij = lamx[i] + lamy[j]
+// (no pivoting).  fold (may be NULL) scales P by fold[k] (the M_z of the right-hand side).
+void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,
+             const signed char* skip_i, const signed char* skip_j, const double2* tzd,
+             const double2* szs, const double2* coff, const double2* fold, int nx, int ny, int nz,
+             unsigned long long* min_pivot_bits, int* status, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Interface steps
+// ---------------------------------------------------------------------------
+// out[plane][s][j] = sum_{i in [lo_s, hi_s)} coef[s][i] V[plane][i][j]  (contraction over rows)
+void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+// out[plane][s][i] = sum_{j in [lo_s, hi_s)} coef[s][j] V[plane][i][j]  (contraction within rows)
+void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+
+struct IfaceArgs {
+  int nx = 0, ny = 0, nz = 0, nrhs = 0, nIx = 0, nIy = 0;
+  const int* xif = nullptr; const int* yif = nullptr;          // interface node indices
+  const signed char* isx = nullptr; const signed char* isy = nullptr;   // interface flags
+  const double2* mx = nullptr; const double2* my = nullptr; const double2* mz = nullptr;
+  const double2* ihx = nullptr; const double2* ihy = nullptr;  // 1 / h (N+1 steps)
+  const double* sig = nullptr;                                  // sigma per z node
+};
+// Step 4: residual r = M f - A v on the interfaces from v at the neighbouring nodes.
+void iface_residual(const IfaceArgs& a, const double2* f, const double2* vX, const double2* vY,
+                    double2* rX, double2* rY, cudaStream_t st);
+// Step 7 (interface part): u = w on the interface planes.
+void write_iface(const IfaceArgs& a, const double2* wX, const double2* wY, double2* u, int conj_out,
+                 int accumulate, cudaStream_t st);
+
+// Adjoint input: out = conj(g) / (mx_i my_j mz_k).
+void adjoint_prep(const double2* g, double2* out, const double2* imx, const double2* imy,
+                  const double2* imz, int nx, int ny, int nz, int nrhs, cudaStream_t st);
+
+// u = conj(u) elementwise.
+void conj_inplace(double2* u, long long n, cudaStream_t st);
+
+// Stencil residual (FP64): rho = f - M^{-1} A u and per-RHS sums of |M rho|^2, |M f|^2.
+struct StencilArgs {
+  int nx = 0, ny = 0, nz = 0, nrhs = 0;
+  const double2* kxs = nullptr;   // [nx][3]: (lower, diag, upper) of K_x row i / mx_i
+  const double2* kys = nullptr;   // [ny][3]
+  const double2* tzs = nullptr;   // [nz][3]: row k of Tz / mz_k
+  const double* sig = nullptr;    // [nz]
+  const double2* mx = nullptr; const double2* my = nullptr; const double2* mz = nullptr;
+};
+void stencil_residual(const StencilArgs& a, const double2* f, const double2* u, double2* rho,
+                      double* partial, int nparts, cudaStream_t st);
+int stencil_parts(const StencilArgs& a);   // number of partial sums per RHS
+void finish_norms(const double* partial, int nparts, int nrhs, double* out, cudaStream_t st);
+
+// Layer gradient: G_L = sum_{k in L} mz_k sum_{r,i,j} conj(lam) mx my u.
+void grad_layers(const double2* u, const double2* lam, const double2* mx, const double2* my,
+                 const double2* mz, const int* z_begin, int nlayers, int nx, int ny, int nz,
+                 int nrhs, double2* partial, int nparts, double2* G, cudaStream_t st);
+int grad_parts(int nx, int ny, int nrhs);
+
+}  // namespace hz

@@ -1,0 +1,317 @@
+"""Thin Python binding of the hz C ABI (include/hz.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+libhz.so.  PyTorch supplies device memory and the stream; tensors must be
+contiguous complex128 of shape (nrhs, Nz, Ny, Nx) on the plan's device.
+Importing this module loads the library and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhz.so")
+
+HZ_FP64, HZ_MIXED = 0, 1
+
+
+class c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class hz_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_void_p), ("hy", ctypes.c_void_p), ("hz", ctypes.c_void_p)]
+
+
+class hz_layers(ctypes.Structure):
+    _fields_ = [("nlayers", ctypes.c_int), ("z_begin", ctypes.c_void_p), ("k2", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p)]
+
+
+class hz_blocks(ctypes.Structure):
+    _fields_ = [("nbx", ctypes.c_int), ("nby", ctypes.c_int), ("x_iface", ctypes.c_void_p),
+                ("y_iface", ctypes.c_void_p)]
+
+
+class hz_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class hz_info(ctypes.Structure):
+    _fields_ = [("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("min_abs_pivot", ctypes.c_double), ("plan_ms", ctypes.c_double),
+                ("eig_max_residual", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+# Every symbol declared in include/hz.h, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "hz_plan_create": (ctypes.c_int, [ctypes.POINTER(hz_grid), ctypes.POINTER(hz_layers),
+                                      ctypes.POINTER(hz_blocks), ctypes.POINTER(hz_options),
+                                      ctypes.POINTER(_P)]),
+    "hz_plan_set_frequency": (ctypes.c_int, [_P, ctypes.c_double]),
+    "hz_plan_set_k2": (ctypes.c_int, [_P, _P]),
+    "hz_plan_set_options": (ctypes.c_int, [_P, ctypes.POINTER(hz_options)]),
+    "hz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "hz_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "hz_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "hz_grad_layers": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "hz_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "hz_get_info": (ctypes.c_int, [_P, ctypes.POINTER(hz_info)]),
+    "hz_plan_destroy": (ctypes.c_int, [_P]),
+    "hz_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "hz_set_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "hz_get_stage_times": (ctypes.c_int, [_P, _P, _P]),
+    "hz_tridiag_eig": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P,
+                                      ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"hz CUDA library not built ({LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class HzError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_lib.hz_status_str(code).decode()} (status {code})")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise HzError(code, where)
+
+
+def _c128_array(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def tridiag_eig(kd, ko, m):
+    """Host eigen-solver of the plan: K W = M W Lambda, W^T M W = I (complex symmetric)."""
+    kd, ko, m = _c128_array(kd), _c128_array(ko), _c128_array(m)
+    n = len(kd)
+    lam = np.empty(n, np.complex128)
+    W = np.empty((n, n), np.complex128)
+    res = ctypes.c_double()
+    _check(_lib.hz_tridiag_eig(n, kd.ctypes.data, ko.ctypes.data if n > 1 else None, m.ctypes.data,
+                               lam.ctypes.data, W.ctypes.data, ctypes.byref(res)), "hz_tridiag_eig")
+    return lam, W, res.value
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Plan:
+    """A solver plan (hz_plan_create): grid, layers, blocks and options.
+
+    precision: "fp64" (DFMA transforms) or "mixed" (FP32 transforms, FP64 z solves,
+    interface solves and refinement to `rtol`).
+    """
+
+    def __init__(self, hx, hy, hz, z_begin, k2, sigma=None, x_iface=None, y_iface=None,
+                 nbx: Optional[int] = None, nby: Optional[int] = None, precision: str = "fp64",
+                 rtol: float = 1e-8, max_refine: int = 10, stream=None):
+        self._keep = []
+        hx, hy, hz = _c128_array(hx), _c128_array(hy), _c128_array(hz)
+        zb = np.ascontiguousarray(np.asarray(z_begin, dtype=np.int32))
+        k2 = _c128_array(k2)
+        self.nx, self.ny, self.nz = len(hx) - 1, len(hy) - 1, len(hz) - 1
+        self.nlayers = len(k2)
+        self.z_begin = zb.copy()
+        g = hz_grid(self.nx, self.ny, self.nz, hx.ctypes.data, hy.ctypes.data, hz.ctypes.data)
+        sig = None if sigma is None else np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+        lay = hz_layers(self.nlayers, zb.ctypes.data, k2.ctypes.data, None if sig is None else sig.ctypes.data)
+        xi = None if x_iface is None else np.ascontiguousarray(np.asarray(x_iface, dtype=np.int32))
+        yi = None if y_iface is None else np.ascontiguousarray(np.asarray(y_iface, dtype=np.int32))
+        nbx = (len(xi) + 1 if xi is not None else 1) if nbx is None else nbx
+        nby = (len(yi) + 1 if yi is not None else 1) if nby is None else nby
+        blk = hz_blocks(nbx, nby, None if xi is None or len(xi) == 0 else xi.ctypes.data,
+                        None if yi is None or len(yi) == 0 else yi.ctypes.data)
+        self.precision = precision
+        self._opts = hz_options(HZ_MIXED if precision == "mixed" else HZ_FP64, rtol, max_refine,
+                                _stream_handle(stream))
+        h = _P()
+        _check(_lib.hz_plan_create(ctypes.byref(g), ctypes.byref(lay), ctypes.byref(blk),
+                                   ctypes.byref(self._opts), ctypes.byref(h)), "hz_plan_create")
+        self._h = h
+        self.hx, self.hy, self.hz = hx, hy, hz
+
+    @classmethod
+    def from_workload(cls, w, precision: Optional[str] = None, **kw):
+        return cls(w.hx, w.hy, w.hz, w.z_begin, w.k2, w.sigma, w.x_iface, w.y_iface,
+                   nbx=len(w.x_iface) + 1, nby=len(w.y_iface) + 1,
+                   precision=precision or w.precision, **kw)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hz_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ------------------------------------------------------
+    def set_options(self, precision=None, rtol=None, max_refine=None, stream=None):
+        if precision is not None:
+            self.precision = precision
+            self._opts.precision = HZ_MIXED if precision == "mixed" else HZ_FP64
+        if rtol is not None:
+            self._opts.rtol = rtol
+        if max_refine is not None:
+            self._opts.max_refine = max_refine
+        self._opts.cuda_stream = _stream_handle(stream)
+        _check(_lib.hz_plan_set_options(self._h, ctypes.byref(self._opts)), "hz_plan_set_options")
+
+    def set_frequency(self, omega: float):
+        _check(_lib.hz_plan_set_frequency(self._h, float(omega)), "hz_plan_set_frequency")
+
+    def set_k2(self, k2):
+        k2 = _c128_array(k2)
+        assert len(k2) == self.nlayers
+        _check(_lib.hz_plan_set_k2(self._h, k2.ctypes.data), "hz_plan_set_k2")
+
+    def info(self) -> dict:
+        i = hz_info()
+        _check(_lib.hz_get_info(self._h, ctypes.byref(i)), "hz_get_info")
+        return {f: getattr(i, f) for f, _ in hz_info._fields_}
+
+    STAGES = ["fwd", "pass_a", "edges", "iface_residual", "global", "pass_b", "inv", "iface_out",
+              "residual"]
+
+    def set_stage_timing(self, enable: bool):
+        _check(_lib.hz_set_stage_timing(self._h, int(enable)), "hz_set_stage_timing")
+
+    def stage_times(self) -> dict:
+        ms = np.zeros(len(self.STAGES), np.float64)
+        n = np.zeros(len(self.STAGES), np.int64)
+        _check(_lib.hz_get_stage_times(self._h, ms.ctypes.data, n.ctypes.data), "hz_get_stage_times")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    # -- solves -------------------------------------------------------------
+    def _check_tensor(self, t):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+            raise ValueError("expected a contiguous complex128 CUDA tensor")
+        if t.dim() != 4 or tuple(t.shape[1:]) != (self.nz, self.ny, self.nx):
+            raise ValueError(f"expected shape (nrhs, {self.nz}, {self.ny}, {self.nx}), got {tuple(t.shape)}")
+        return t.shape[0]
+
+    def solve(self, f, out=None):
+        """u = A^{-1} (M f) for device tensors (hz_solve)."""
+        import torch
+        R = self._check_tensor(f)
+        u = torch.empty_like(f) if out is None else out
+        _check(_lib.hz_solve(self._h, f.data_ptr(), u.data_ptr(), R), "hz_solve")
+        return u
+
+    def solve_host(self, f_host, out=None):
+        """hz_solve_host on host arrays (numpy or CPU tensors); returns a numpy array."""
+        f = _c128_array(f_host) if not hasattr(f_host, "data_ptr") else f_host
+        if hasattr(f, "data_ptr"):
+            u = np.empty(tuple(f.shape), np.complex128) if out is None else out
+            ptr_f = f.data_ptr()
+        else:
+            u = np.empty_like(f) if out is None else out
+            ptr_f = f.ctypes.data
+        ptr_u = u.data_ptr() if hasattr(u, "data_ptr") else u.ctypes.data
+        _check(_lib.hz_solve_host(self._h, ptr_f, ptr_u, f.shape[0]), "hz_solve_host")
+        return u
+
+    def solve_adjoint(self, g, out=None):
+        """lam = A^{-H} g (hz_solve_adjoint); g is in the weighted space."""
+        import torch
+        R = self._check_tensor(g)
+        lam = torch.empty_like(g) if out is None else out
+        _check(_lib.hz_solve_adjoint(self._h, g.data_ptr(), lam.data_ptr(), R), "hz_solve_adjoint")
+        return lam
+
+    def grad_layers(self, u, lam) -> np.ndarray:
+        R = self._check_tensor(u)
+        self._check_tensor(lam)
+        G = np.empty(self.nlayers, np.complex128)
+        _check(_lib.hz_grad_layers(self._h, u.data_ptr(), lam.data_ptr(), R, G.ctypes.data), "hz_grad_layers")
+        return G
+
+    def residual(self, f, u) -> np.ndarray:
+        R = self._check_tensor(f)
+        out = np.empty(R, np.float64)
+        _check(_lib.hz_residual(self._h, f.data_ptr(), u.data_ptr(), R, out.ctypes.data), "hz_residual")
+        return out
+
+
+def dual_weights(plan: Plan):
+    """hhat per axis (host numpy), for callers that weight data by M."""
+    h = lambda s: 0.5 * (s[:-1] + s[1:])
+    return h(plan.hx), h(plan.hy), h(plan.hz)
+
+
+class HzSolve:
+    """torch.autograd.Function wrapper: u = A(k2)^{-1} M f, differentiable in k2 and f.
+
+    Usage: u = HzSolve.apply(k2, f, plan) with k2 a complex128 tensor (nlayers,)
+    on the CPU (it sets the plan's layer k^2) and f a CUDA tensor.  The backward
+    pass runs one adjoint solve lam = A^{-H} grad_u and returns
+    k2.grad = conj(G) (G from hz_grad_layers; PyTorch's convention for complex
+    leaves of real losses) and f.grad = conj(M) lam.
+    """
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, k2, f, plan):
+                plan.set_k2(k2.detach().cpu().numpy())
+                u = plan.solve(f.contiguous())
+                ctx.plan = plan
+                ctx.save_for_backward(u)
+                return u
+
+            @staticmethod
+            def backward(ctx, grad_u):
+                (u,) = ctx.saved_tensors
+                plan = ctx.plan
+                lam = plan.solve_adjoint(grad_u.contiguous())
+                G = plan.grad_layers(u, lam)
+                gk = torch.from_numpy(np.conj(G))
+                mx, my, mz = dual_weights(plan)
+                w = (np.conj(mz)[:, None, None] * np.conj(my)[None, :, None] * np.conj(mx)[None, None, :])
+                gf = lam * torch.from_numpy(w).to(lam.device)[None]
+                return gk, gf, None
+
+        return _F
+
+    _cache = None
+
+    @classmethod
+    def apply(cls, k2, f, plan):
+        if cls._cache is None:
+            cls._cache = cls._fn()
+        return cls._cache.apply(k2, f, plan)

@@ -1,0 +1,245 @@
+"""CUDA path against the CPU oracle on the same seeded inputs (needs a GB300).
+
+Tolerances: relative L2 error <= 1e-10 for the FP64 path and <= 1e-8 for the
+mixed path after refinement, as the target states; residual checks use the
+oracle's sparse operator.  Every call goes through the C ABI (hz.Plan).
+"""
+import numpy as np
+import pytest
+
+from oracle import hz_oracle as O
+from paper_1909_01299_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-8
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01299_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def hz(torch_cuda):
+    from paper_1909_01299_gb300 import hz as mod
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def gpu_solve(hz, torch, w, precision="fp64", f=None, **kw):
+    plan = hz.Plan.from_workload(w, precision=precision, **kw)
+    fd = torch.from_numpy(w.f if f is None else f).cuda()
+    u = plan.solve(fd).cpu().numpy()
+    return plan, u
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=13, ny=11, nz=9, bx=2, by=2),
+    dict(nx=13, ny=11, nz=9, bx=3, by=2),
+    dict(nx=13, ny=11, nz=9, bx=1, by=1),
+    dict(nx=13, ny=11, nz=9, bx=2, by=1),
+    dict(nx=13, ny=11, nz=9, bx=1, by=3),
+    dict(nx=13, ny=11, nz=9, bx=2, by=2, sigma=True),
+    dict(nx=16, ny=16, nz=16, bx=4, by=4, rim=4, pml=2),
+    dict(nx=70, ny=45, nz=33, bx=3, by=2, rim=6, pml=3, nrhs=3),      # several tiles + ragged tails
+])
+def test_fp64_matches_lu(hz, torch_cuda, kw):
+    w = W.tiny_pml(**kw)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    _, u = gpu_solve(hz, torch_cuda, w)
+    assert rel(u, ref) < TOL64
+
+
+def test_fp64_quadratic_exact_solution(hz, torch_cuda):
+    from tests.oracle_pins import quadratic_solution
+    w = W.tiny_pml(40, 37, 21, 3, 2, rim=5, pml=2)
+    u_ex, f = quadratic_solution(w)
+    _, u = gpu_solve(hz, torch_cuda, w, f=f[None].copy())
+    assert rel(u[0], u_ex) < TOL64
+
+
+def test_single_block_32_matches_oracle(hz, torch_cuda):
+    w = W.single_block_32()
+    P = O.Problem.from_workload(w)
+    ref = O.block_solve(P, w.f)
+    plan, u = gpu_solve(hz, torch_cuda, w)
+    assert rel(u, ref) < TOL64
+    assert np.all(O.residual(P, u, w.f) < 1e-12)
+
+
+@pytest.fixture(scope="module")
+def pml160(hz, torch_cuda):
+    w = W.pml_160x160x128()
+    P = O.Problem.from_workload(w)
+    A, _ = O.assemble(P)
+    ref = O.block_solve(P, w.f, A)
+    return w, P, A, ref
+
+
+def test_two_block_pml_full_size_fp64(hz, torch_cuda, pml160):
+    w, P, A, ref = pml160
+    plan, u = gpu_solve(hz, torch_cuda, w)
+    for r in range(w.nrhs):
+        assert rel(u[r], ref[r]) < TOL64
+    assert np.all(O.residual(P, u, w.f, A) < 1e-10)
+    # the library's own FP64 residual agrees with the oracle's
+    fd = torch_cuda.from_numpy(w.f).cuda()
+    res = plan.residual(fd, torch_cuda.from_numpy(u).cuda())
+    assert np.allclose(res, O.residual(P, u, w.f, A), rtol=1e-3, atol=1e-15)
+
+
+def test_two_block_pml_full_size_mixed(hz, torch_cuda, pml160):
+    w, P, A, ref = pml160
+    plan, u = gpu_solve(hz, torch_cuda, w, precision="mixed", rtol=1e-10, max_refine=12)
+    info = plan.info()
+    assert info["rel_residual"] <= 1e-10
+    for r in range(w.nrhs):
+        assert rel(u[r], ref[r]) < TOLMIX
+    assert np.all(O.residual(P, u, w.f, A) < 1e-8)
+
+
+@pytest.mark.parametrize("kw", [dict(nx=13, ny=11, nz=9, bx=2, by=2),
+                                dict(nx=70, ny=45, nz=33, bx=3, by=2, rim=6, pml=3, nrhs=2)])
+def test_mixed_matches_lu(hz, torch_cuda, kw):
+    w = W.tiny_pml(**kw)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    plan, u = gpu_solve(hz, torch_cuda, w, precision="mixed")
+    assert rel(u, ref) < TOLMIX
+    assert plan.info()["rel_residual"] <= 1e-8
+
+
+def test_partition_invariance_gpu(hz, torch_cuda):
+    base = W.tiny_pml(48, 40, 20, 1, 1, rim=6, pml=3)
+    _, u1 = gpu_solve(hz, torch_cuda, base)
+    for bx, by in [(2, 2), (4, 3), (3, 1)]:
+        w = W.tiny_pml(48, 40, 20, bx, by, rim=6, pml=3)
+        _, u = gpu_solve(hz, torch_cuda, w)
+        assert rel(u, u1) < TOL64
+
+
+def test_in_place_and_host_entry_points(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(30, 28, 17, 2, 2, rim=4, pml=2, nrhs=2)
+    plan = hz.Plan.from_workload(w)
+    fd = torch.from_numpy(w.f).cuda()
+    u = plan.solve(fd).cpu().numpy()
+    fd2 = torch.from_numpy(w.f).cuda()
+    plan.solve(fd2, out=fd2)                                   # f == u
+    assert rel(fd2.cpu().numpy(), u) < 1e-14
+    uh = plan.solve_host(w.f)                                  # host buffers
+    assert rel(uh, u) < 1e-14
+    plan.set_options(precision="mixed")
+    fd3 = torch.from_numpy(w.f).cuda()
+    plan.solve(fd3, out=fd3)                                   # in place with refinement
+    assert rel(fd3.cpu().numpy(), u) < TOLMIX
+
+
+def test_ragged_rhs_counts(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(33, 29, 19, 2, 3, rim=4, pml=2, nrhs=5)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    plan = hz.Plan.from_workload(w)
+    for R in (1, 5, 3):
+        u = plan.solve(torch.from_numpy(w.f[:R].copy()).cuda()).cpu().numpy()
+        assert rel(u, ref[:R]) < TOL64
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 3), (6, 1, 4), (7, 6, 1), (5, 4, 2)])
+def test_degenerate_sizes(hz, torch_cuda, shape):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(5)
+    w = W.Workload("deg", W.uniform_steps(nx, 0.9), W.uniform_steps(ny, 1.1), W.ramp_z(nz),
+                   np.array([0, nz], np.int32), np.array([0.3 + 0.02j]), np.zeros(0, np.int32),
+                   np.zeros(0, np.int32), rng.standard_normal((2, nz, ny, nx)) + 0j)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    _, u = gpu_solve(hz, torch_cuda, w)
+    assert rel(u, ref) < TOL64
+
+
+def test_single_node_blocks(hz, torch_cuda):
+    # interfaces two nodes apart leave blocks of one node
+    w = W.tiny_pml(9, 8, 6, 1, 1, rim=2, pml=1)
+    w.x_iface = np.array([1, 3, 5, 7], np.int32)
+    w.y_iface = np.array([2, 4], np.int32)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    _, u = gpu_solve(hz, torch_cuda, w)
+    assert rel(u, ref) < TOL64
+
+
+def test_frequency_rescaling(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(20, 18, 12, 2, 2, rim=3, pml=2)
+    plan = hz.Plan.from_workload(w)
+    fd = torch.from_numpy(w.f).cuda()
+    for om in (0.5, 1.5):
+        plan.set_frequency(om)
+        u = plan.solve(fd).cpu().numpy()
+        P = O.Problem.from_workload(w, k2=w.k2 * om * om)
+        assert rel(u, O.solve(P, w.f)) < TOL64
+
+
+def test_adjoint_and_layer_gradient(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(24, 22, 16, 2, 2, rim=3, pml=2, nrhs=2)
+    rng = np.random.default_rng(2)
+    rec = rng.choice(w.nx * w.ny * w.nz, 10, replace=False)
+    d_obs = O.solve(O.Problem.from_workload(w, k2=w.k2 * 1.05), w.f).reshape(2, -1)[:, rec]
+    P = O.Problem.from_workload(w)
+    J_o, G_o, u_o, lam_o = O.misfit_gradient(P, w.f, rec, d_obs, method="lu")
+    plan = hz.Plan.from_workload(w)
+    u = plan.solve(torch.from_numpy(w.f).cuda())
+    _, g = O.misfit(u.cpu().numpy(), rec, d_obs)
+    lam = plan.solve_adjoint(torch.from_numpy(g).cuda())
+    assert rel(lam.cpu().numpy(), lam_o) < TOL64
+    G = plan.grad_layers(u, lam)
+    assert rel(G, G_o) < 1e-9
+
+
+def test_autograd_wrapper_against_finite_differences(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(20, 18, 12, 2, 2, rim=3, pml=2, nrhs=1)
+    plan = hz.Plan.from_workload(w)
+    rng = np.random.default_rng(4)
+    rec = torch.from_numpy(rng.choice(w.nx * w.ny * w.nz, 8, replace=False)).cuda()
+    d = torch.from_numpy(rng.standard_normal(8) * 1e-2 + 0j).cuda()
+    f = torch.from_numpy(w.f).cuda()
+
+    def loss(k2):
+        u = hz.HzSolve.apply(k2, f, plan)
+        return 0.5 * (u.reshape(-1)[rec] - d).abs().pow(2).sum()
+
+    k2 = torch.tensor(w.k2, dtype=torch.complex128, requires_grad=True)
+    L = loss(k2)
+    L.backward()
+    eps = 1e-6
+    for Lyr in range(len(w.k2)):
+        e = torch.zeros_like(k2.detach())
+        e[Lyr] = eps
+        fd_re = (loss(k2.detach() + e) - loss(k2.detach() - e)).item() / (2 * eps)
+        fd_im = (loss(k2.detach() + 1j * e) - loss(k2.detach() - 1j * e)).item() / (2 * eps)
+        g = k2.grad[Lyr].item()
+        assert abs(g.real - fd_re) <= 1e-6 * max(abs(fd_re), 1e-12) + 1e-12
+        assert abs(g.imag - fd_im) <= 1e-6 * max(abs(fd_im), 1e-12) + 1e-12
+
+
+def test_singular_mode_is_reported(hz, torch_cuda):
+    # one x and one y node (lambda = mu = 2) and k^2 = 6 make the z matrix of the only mode
+    # tridiag(-1, 0, -1): its first pivot is exactly zero
+    with pytest.raises(hz.HzError) as e:
+        hz.Plan(W.uniform_steps(1), W.uniform_steps(1), W.uniform_steps(3), [0, 3], [6.0 + 0j])
+    assert e.value.code == 3
