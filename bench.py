@@ -111,13 +111,14 @@ def dist_env():
 
 
 def block_sizes(n, ifaces):
-    edges = [-1] + list(ifaces) + [n]
+    edges = [-1] + [int(p) for p in ifaces] + [int(n)]
     return [edges[b + 1] - edges[b] - 1 for b in range(len(edges) - 1)]
 
 
 def bulk_macs(w, nrhs):
     """Complex multiply-adds of the four bulk transform launches (X1..X4) of one solve."""
-    bx, by = block_sizes(w.nx, w.x_iface), block_sizes(w.ny, w.y_iface)
+    bx = [int(n) for n in block_sizes(w.nx, w.x_iface)]
+    by = [int(n) for n in block_sizes(w.ny, w.y_iface)]
     sx, sy = sum(n * n for n in bx), sum(n * n for n in by)
     rows_x = w.ny - len(w.y_iface)        # rows transformed along x (interface rows skipped)
     rows_y = w.nx - len(w.x_iface)

@@ -23,7 +23,7 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int kTileN = 32;   // output columns per transform tile (matches hz_xform.cu)
+constexpr int kTileN = 16;   // output columns per transform tile (matches hz_xform.cu)
 
 // ---------------------------------------------------------------------------
 // Host-side axis data
@@ -532,6 +532,8 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
   const long long planes = (long long)R * nz;
   const int nIx = (int)p->ax.iface.size(), nIy = (int)p->ay.iface.size();
   auto bulk = lo ? hz::xform_f32 : hz::xform_f64;
+  // The interface-row transforms below are non-transposed, so their rows are
+  // flattened across planes (one launch row tile covers 32 rows of any planes).
   // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
   {
     Stage t(p, HZ_STAGE_FWD);
@@ -558,11 +560,11 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
     std::unique_ptr<Stage> t3(new Stage(p, HZ_STAGE_EDGES));
     if (nIx) {
       hz::contract_rows(w.V, w.cX, p->dx.edge_coef, p->dx.edge_rng, nx, ny, 2 * nIx, planes, st);
-      hz::xform_f64(p->dy.inv, w.cX, w.vX, 2 * nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dy.inv, w.cX, w.vX, (int)(2 * nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     if (nIy) {
       hz::contract_cols(w.V, w.cY, p->dy.edge_coef, p->dy.edge_rng, nx, ny, 2 * nIy, planes, st);
-      hz::xform_f64(p->dx.inv, w.cY, w.vY, 2 * nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dx.inv, w.cY, w.vY, (int)(2 * nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     t3.reset();
     // Step 4: r = M f - A v on the interfaces
@@ -573,8 +575,8 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
     }
     // Step 5: w on the interfaces through the whole-axis eigenbasis
     std::unique_ptr<Stage> t5(new Stage(p, HZ_STAGE_GLOBAL));
-    if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
-    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+    if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     hz::ZSolveArgs zg = za;
     zg.skip_i = nullptr; zg.skip_j = nullptr;
     zg.out = w.G;                                   // w~ (G is free until step 7)
@@ -583,14 +585,14 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
     hz::zsolve(hz::Z_GLOBAL, zg, st);
     if (nIx) {
       hz::contract_rows(w.G, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
-      hz::xform_f64(p->dy.ginv, w.cg, w.wX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dy.ginv, w.cg, w.wX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
       // Step 6 (x interfaces): forward y-transform of w on the interface rows
-      hz::xform_f64(p->dy.fwd, w.wX, w.alX, nIx, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dy.fwd, w.wX, w.alX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     if (nIy) {
       hz::contract_cols(w.G, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, st);
-      hz::xform_f64(p->dx.ginv, w.dg, w.wY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
-      hz::xform_f64(p->dx.fwd, w.wY, w.alY, nIy, planes, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dx.ginv, w.dg, w.wY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::xform_f64(p->dx.fwd, w.wY, w.alY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     t5.reset();
     // Step 6: pass B, (Tz + s S_z) u~ = M_z f~ + g~ with g~ generated from the interface data

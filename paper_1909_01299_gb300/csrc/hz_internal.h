@@ -58,6 +58,39 @@ struct XformSet {
 
 enum XformStore { XS_STORE = 0, XS_ACCUM = 1 };
 
+// Tensor-core (tcgen05 kind::tf32, 3xTF32) version of the bulk transforms.  Per block the
+// complex table B (n x n) is stored as the real interleaved matrix B' (2n x 2n) transposed
+// to K-major, padded to npad (multiple of 16) rows and kpad (multiple of 32) columns, as
+// TF32 hi (npad x kpad floats at toff) followed by TF32 lo (same size).
+struct TCBlock {
+  int start;            // first complex column of the block
+  int size;             // complex width n
+  int npad, kpad;
+  long long toff;       // float offset of the hi table
+};
+struct TCTile {
+  int blk;
+  int n0;               // first real output column (multiple of 16)
+  int nt;               // real output columns (multiple of 16, <= 256)
+  int pad;
+};
+struct TCSet {
+  int ncols = 0;
+  int ntiles = 0;
+  int nt_max = 16;
+  TCBlock* d_blocks = nullptr;
+  TCTile* d_tiles = nullptr;
+  float* d_tab = nullptr;
+};
+size_t xform_tc_smem(int nt_max);
+// Host: append the TF32 hi/lo K-major tables of one block (complex table B, n x n row-major,
+// B[a][c]) and its output tiles.
+void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
+                   std::vector<TCTile>& tiles, int blk_index);
+// err: device status word (set to HZ_ERR_TIMEOUT if a bounded wait gives up).
+void xform_tc(const TCSet& ts, const double2* in, double2* out, int rows_per_plane, long long nplanes,
+              int trans, int store, const signed char* rowskip, int* err, cudaStream_t st);
+
 // FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
 // trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out
 // has the input's layout.  store: XS_STORE or XS_ACCUM (out += result).  conj_out

@@ -1,0 +1,341 @@
+// Bulk x/y eigen-transforms of the mixed path on the 5th-generation tensor cores.
+//
+// The transform of steps 1 and 7 of Sec. 2 is, per block, a complex product
+// C[rows x n] = A[rows x n] B[n x n] with the block's eigenvector table B
+// (forward W^T M or inverse W).  Written over the reals with interleaved
+// (re, im) pairs it is one real GEMM of K = N = 2n:
+//   A'[row][2a+u] = (Re, Im) of A[row][a],
+//   B'[2a][2c] = Re B, B'[2a][2c+1] = Im B, B'[2a+1][2c] = -Im B, B'[2a+1][2c+1] = Re B,
+// whose result C' = A' B' is again interleaved complex.  The GEMM runs as
+// tcgen05.mma kind::tf32 with FP32 accumulators in tensor memory, in the
+// 3xTF32 form A_hi B_hi + A_hi B_lo + A_lo B_hi (x = hi + lo, hi = tf32(x),
+// lo = tf32(x - hi)), which keeps the result at FP32 accuracy; FP64 iterative
+// refinement of the solve removes the rest.
+//
+// One CTA (4 warps) computes a 128-row x Nt-column tile (Nt <= 256, a multiple of
+// 16) of one block.  The contraction runs in chunks of 32 real K (128 bytes per
+// operand row): all threads convert the FP64 data rows to TF32 hi/lo and store
+// them, with the tables' hi/lo rows, in shared memory in the K-major
+// 128-byte-swizzled layout; one thread issues the 12 MMAs of the chunk and
+// commits them to the chunk's mbarrier; two chunk buffers alternate, so the
+// conversion of chunk c+1 overlaps the MMAs of chunk c.  The epilogue reads
+// the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile
+// rows), converts to FP64 and stores (transposed or not, optionally adding).
+// Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
+// waits (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 128;
+constexpr int KCH = 32;                  // real K per chunk (128 bytes of tf32 per row)
+constexpr int ROWB = 128;                // bytes per operand row in a chunk
+constexpr int A_BYTES = TC_M * ROWB;     // one A plane (hi or lo) of a chunk
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_NS = 2000000000LL;   // 2 s bound on any wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  // clock64 counts SM cycles; 2e9 ns at <= 2.1 GHz is < 4.2e9 cycles
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > 2 * WAIT_NS) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 46;                          // descriptor version
+  d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const float* __restrict__ tabs,
+                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, long long nrows,
+                int rows_per_plane, int ncols, int trans, int store, const signed char* __restrict__ rowskip,
+                int* __restrict__ err) {
+  extern __shared__ uint8_t smem_dyn[];
+  // 1024-byte alignment for the swizzled operand buffers
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  const TCTile t = tiles[blockIdx.y];
+  const TCBlock b = blocks[t.blk];
+  const int nt = t.nt;                                     // tile width in real columns
+  const int B_BYTES = nt * ROWB;
+  const int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long row0 = (long long)blockIdx.x * TC_M;
+  const int n = b.size;                                    // complex width of the block
+  const int nk = b.kpad / KCH;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_tf32(nt);
+  const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
+  const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
+  bool ok = true;
+  int issued = 0;                                          // chunks whose MMAs were committed
+
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    uint8_t* st = smem + s * STAGE;
+    if (kc >= 2) {                                         // MMAs of chunk kc-2 done with this buffer
+      const int w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+    }
+    // A: 128 rows x 8 chunks of 16 bytes (two complex values), hi and lo planes
+    const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_BYTES;
+#pragma unroll 2
+    for (int q = 0; q < 8; ++q) {
+      const int task = tid + TC_THREADS * q;
+      const int r = task >> 3, c = task & 7;
+      const long long grow = row0 + r;
+      const int col = kc * (KCH / 2) + 2 * c;              // complex column within the block
+      double2 v0 = make_double2(0.0, 0.0), v1 = v0;
+      if (grow < nrows) {
+        const double2* src = in + grow * (long long)ncols + b.start + col;
+        if (col < n) v0 = src[0];
+        if (col + 1 < n) v1 = src[1];
+      }
+      const float f[4] = {(float)v0.x, (float)v0.y, (float)v1.x, (float)v1.y};
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        h[e] = to_tf32(f[e]);
+        l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
+      }
+      const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
+      st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
+      st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+    }
+    // B: nt rows x 8 chunks, hi and lo tables (already tf32 in global memory)
+    const uint32_t b_hi = a_lo + A_BYTES, b_lo = b_hi + B_BYTES;
+    for (int task = tid; task < nt * 8; task += TC_THREADS) {
+      const int r = task >> 3, c = task & 7;
+      const long long go = (long long)r * b.kpad + kc * KCH + 4 * c;
+      const float4 vh = *reinterpret_cast<const float4*>(thi + go);
+      const float4 vl = *reinterpret_cast<const float4*>(tlo + go);
+      const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
+      st_shared_v4(b_hi + off, __float_as_uint(vh.x), __float_as_uint(vh.y), __float_as_uint(vh.z),
+                   __float_as_uint(vh.w));
+      st_shared_v4(b_lo + off, __float_as_uint(vl.x), __float_as_uint(vl.y), __float_as_uint(vl.z),
+                   __float_as_uint(vl.w));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < KCH / 8; ++ks) {                 // 8 tf32 = 32 bytes per MMA
+        const uint32_t koff = ks * 32;
+        const uint64_t dah = smem_desc_sw128(a_hi + koff), dal = smem_desc_sw128(a_lo + koff);
+        const uint64_t dbh = smem_desc_sw128(b_hi + koff), dbl = smem_desc_sw128(b_lo + koff);
+        const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+        mma_tf32(tmem, dah, dbh, idesc, first);
+        mma_tf32(tmem, dah, dbl, idesc, 1u);
+        mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(&bars[s]);
+    }
+    issued = kc + 1;
+  }
+  // The last commit covers every earlier MMA of this thread; wait for it (bounded) even
+  // after a failed wait, so no MMA is in flight when the tensor memory is freed.
+  if (issued > 0) {
+    const int last = issued - 1;
+    if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) ok = false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int all_ok = __syncthreads_and(ok ? 1 : 0);
+  if (all_ok) {
+    const int r = warp * 32 + lane;
+    const long long grow = row0 + r;
+    long long plane = 0;
+    int rip = 0;
+    bool row_ok = grow < nrows;
+    if (row_ok) {
+      plane = grow / rows_per_plane;
+      rip = (int)(grow - plane * rows_per_plane);
+      if (rowskip && rowskip[rip]) row_ok = false;
+    }
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c16 = 0; c16 < nt; c16 += 16) {
+      float v[16];
+      tmem_ld16(tl + c16, v);
+      if (!row_ok) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int ccol = (t.n0 + c16) / 2 + e;               // complex column within the block
+        if (ccol >= n) continue;
+        double2 val = make_double2((double)v[2 * e], (double)v[2 * e + 1]);
+        double2* p = trans ? out + plane * (long long)ncols * rows_per_plane +
+                                 (long long)(b.start + ccol) * rows_per_plane + rip
+                           : out + grow * (long long)ncols + b.start + ccol;
+        if (store == XS_ACCUM) {
+          const double2 o = *p;
+          val.x += o.x;
+          val.y += o.y;
+        }
+        *p = val;
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, (int)HZ_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+float tf32_round_host(double x) {
+  // round an FP32 value to TF32 (10 explicit mantissa bits), nearest, ties away from zero
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+
+void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
+                   std::vector<TCTile>& tiles, int blk_index) {
+  blk.start = start;
+  blk.size = n;
+  blk.npad = ((2 * n + 15) / 16) * 16;
+  blk.kpad = ((2 * n + 31) / 32) * 32;
+  blk.toff = (long long)tab.size();
+  const size_t plane = (size_t)blk.npad * blk.kpad;
+  tab.resize(tab.size() + 2 * plane, 0.0f);
+  float* hi = tab.data() + blk.toff;
+  float* lo = hi + plane;
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) {
+      const cd v = B[(size_t)a * n + c];
+      // B'[2a+u][2c+v]: (0,0) Re, (0,1) Im, (1,0) -Im, (1,1) Re; stored K-major T[2c+v][2a+u]
+      const double e[2][2] = {{v.real(), v.imag()}, {-v.imag(), v.real()}};
+      for (int u = 0; u < 2; ++u)
+        for (int w = 0; w < 2; ++w) {
+          const size_t o = (size_t)(2 * c + w) * blk.kpad + (2 * a + u);
+          const float h = tf32_round_host(e[u][w]);
+          hi[o] = h;
+          lo[o] = tf32_round_host(e[u][w] - (double)h);
+        }
+    }
+  for (int n0 = 0; n0 < blk.npad; n0 += 256) tiles.push_back(TCTile{blk_index, n0, std::min(256, blk.npad - n0), 0});
+}
+
+size_t xform_tc_smem(int nt_max) { return 1024 + 2 * (2 * A_BYTES + 2 * nt_max * ROWB) + 64; }
+
+uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }
+
+void xform_tc(const TCSet& ts, const double2* in, double2* out, int rows_per_plane, long long nplanes,
+              int trans, int store, const signed char* rowskip, int* err, cudaStream_t st) {
+  const long long nrows = nplanes * (long long)rows_per_plane;
+  if (nrows <= 0 || ts.ntiles == 0) return;
+  const size_t smem = xform_tc_smem(ts.nt_max);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool attr_set[64] = {};
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  dim3 grid((unsigned)((nrows + TC_M - 1) / TC_M), ts.ntiles);
+  xform_tc_kernel<<<grid, TC_THREADS, smem, st>>>(in, out, ts.d_tab, ts.d_blocks, ts.d_tiles, nrows,
+                                                  rows_per_plane, ts.ncols, trans, store, rowskip, err);
+  count_launch();
+}
+
+}  // namespace hz
