@@ -703,6 +703,12 @@ void release(hz_plan_t p) {
 
 }  // namespace
 
+namespace hz {
+// Read-only views of a plan for the allocation-free residual (hz_noalloc.cu).
+StencilArgs plan_stencil_args(hz_plan_t p, int nrhs) { return stencil_args(p, nrhs); }
+cudaStream_t plan_stream(hz_plan_t p) { return p->st; }
+}  // namespace hz
+
 extern "C" {
 
 const char* hz_status_str(hz_status s) {

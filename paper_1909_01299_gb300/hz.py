@@ -64,6 +64,7 @@ SIGNATURES = {
     "hz_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_grad_layers": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "hz_residual_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_get_info": (ctypes.c_int, [_P, ctypes.POINTER(hz_info)]),
     "hz_plan_destroy": (ctypes.c_int, [_P]),
     "hz_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -263,6 +264,21 @@ class Plan:
         out = np.empty(R, np.float64)
         _check(_lib.hz_residual(self._h, f.data_ptr(), u.data_ptr(), R, out.ctypes.data), "hz_residual")
         return out
+
+
+def residual_noalloc(plan: Plan, f, u) -> np.ndarray:
+    """hz_residual_noalloc: the residual check that allocates no device memory.
+
+    For callers that cannot allocate at the time of the check (inside a CUDA
+    graph capture, allocation-free serving loops); nrhs <= 64; concurrent calls on
+    one device must be serialised (they share one fixed scratch array).
+    """
+    R = plan._check_tensor(f)
+    plan._check_tensor(u)
+    out = np.empty(R, np.float64)
+    _check(_lib.hz_residual_noalloc(plan._h, f.data_ptr(), u.data_ptr(), R, out.ctypes.data),
+           "hz_residual_noalloc")
+    return out
 
 
 def dual_weights(plan: Plan):
