@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="pml160",
+                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48"],
+                    help="pml160 is the benchmark workload; the others are extra measurements")
     return ap.parse_args()
 
 
@@ -340,10 +343,85 @@ def run_hz(args):
         dist.destroy_process_group()
 
 
+def run_extra(args):
+    """Single-GPU measurements of the other named workloads (not the benchmark line)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1909_01299_gb300 import build as B
+    B.build()
+    from paper_1909_01299_gb300 import hz, workloads as W
+    out = {"workload": args.workload}
+    if args.workload == "batch48":
+        items = W.batched_models(48)
+        plans, fs, us, nrhs = [], [], [], []
+        t0 = time.perf_counter()
+        for w, omegas in items:
+            f = torch.from_numpy(w.f).cuda()
+            for om in omegas:
+                p = hz.Plan.from_workload(w, precision="mixed", rtol=RTOL)
+                p.set_frequency(float(om))
+                plans.append(p)
+                fs.append(f)
+                us.append(torch.empty_like(f))
+                nrhs.append(w.nrhs)
+        plan_s = time.perf_counter() - t0
+        batch = hz.Batch(plans, nrhs)
+        lanes = batch.autotune(fs, us)
+        for _ in range(args.warmup):
+            batch.solve(fs, us)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rel = None
+        for _ in range(args.steps):
+            rel = batch.solve(fs, us)
+        dt = (time.perf_counter() - t0) / args.steps
+        unknowns = sum(p.nx * p.ny * p.nz * r for p, r in zip(plans, nrhs))
+        out.update({"items": len(plans), "unknowns_x_rhs": unknowns, "lanes": lanes,
+                    "s_per_batch": dt, "value": unknowns / dt, "unit": UNIT,
+                    "graph_replay_ms": batch.info()["last_ms"], "launches_per_replay":
+                    batch.info()["launches_per_replay"], "rel_residual_max": float(np.max(rel)),
+                    "plan_seconds": plan_s})
+    else:
+        w = {"uniform320": W.uniform_320x320x200, "adjoint192": W.adjoint_192x192x128,
+             "uniform32": W.single_block_32, "pml160": W.pml_160x160x128}[args.workload]()
+        f = torch.from_numpy(w.f).cuda()
+        u = torch.empty_like(f)
+        plan = hz.Plan.from_workload(w, precision="fp64")
+        for prec in ("fp64", "mixed"):
+            plan.set_options(precision=prec, rtol=RTOL)
+            ms, launches, st, clk = time_path(torch, hz, plan, f, u, args.steps, args.warmup, None, 1, 0)
+            res = float(np.max(plan.residual(f, u)))
+            out[prec] = {"value": w.unknowns * w.nrhs / (ms * 1e-3), "ms_per_step": ms,
+                         "rel_residual_max": res, "refinements": plan.info()["refinements"],
+                         "stages_ms_per_step": {k: v[0] / args.steps for k, v in st.items() if v[1]},
+                         "clocks": clk}
+        if args.workload == "adjoint192":
+            rec = torch.from_numpy(w.extra["rec_flat"]).cuda()
+            plan.set_options(precision="fp64")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                uu = plan.solve(f)
+                flat = uu.reshape(w.nrhs, -1)
+                g = torch.zeros_like(flat)
+                g[:, rec] = flat[:, rec]
+                lam = plan.solve_adjoint(g.reshape(uu.shape))
+                G = plan.grad_layers(uu, lam)
+            e1.record()
+            torch.cuda.synchronize()
+            out["gradient_ms"] = e0.elapsed_time(e1) / args.steps
+        out["unit"] = UNIT
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "pml160":
+        run_extra(args)
     else:
         run_hz(args)
 

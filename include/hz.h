@@ -188,6 +188,30 @@ hz_status hz_residual(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev
 hz_status hz_residual_noalloc(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev, int nrhs,
                               double *rel_host);
 
+/* Batches (many independent solves replayed as one CUDA graph).  A batch holds nitems
+ * (plan, nrhs) items -- different grids, layers and frequencies (one plan per model and
+ * frequency) -- and nlanes concurrent streams (0 = 4), each with one workspace sized for
+ * the largest item it runs.  hz_batch_solve captures, on the first call with a given set
+ * of pointers, every item's solve into one graph: FP64 plans run steps 1-7 once; mixed
+ * plans run the first solve, its FP64 residual, one correction and the final residual
+ * (Sec. 2's algorithm per solve; the refinement is the mixed path's).  Later calls with
+ * the same pointers replay the graph.  After the replay every item's residual is checked
+ * on the host; a mixed item above its rtol gets further corrections eagerly on its plan's
+ * own stream.  rel_host (nitems, may be NULL) receives each item's max relative residual.
+ * f_dev[i], u_dev[i]: device arrays of item i (must differ).  A plan may appear in one
+ * item only.  The batch does not own the plans (destroy the batch first). */
+typedef struct hz_batch_s *hz_batch_t;
+hz_status hz_batch_create(int nitems, const hz_plan_t *plans, const int *nrhs, int nlanes, hz_batch_t *out);
+hz_status hz_batch_solve(hz_batch_t batch, const hz_c128 *const *f_dev, hz_c128 *const *u_dev,
+                         double *rel_host);
+/* Autotuner: times graph replays with 1, 2, 4 and 8 lanes on the given inputs and keeps
+ * the fastest (written to *lanes_out). */
+hz_status hz_batch_autotune(hz_batch_t batch, const hz_c128 *const *f_dev, hz_c128 *const *u_dev,
+                            int *lanes_out);
+/* Last replay's CUDA-event time (ms), kernels per replay, lanes in use. */
+hz_status hz_batch_info(hz_batch_t batch, double *last_ms, long long *launches_per_replay, int *lanes);
+hz_status hz_batch_destroy(hz_batch_t batch);
+
 hz_status hz_get_info(hz_plan_t plan, hz_info *out);
 
 hz_status hz_plan_destroy(hz_plan_t plan);

@@ -42,6 +42,7 @@ struct AxisPlan {
 // Device tables of one axis.
 struct AxisDev {
   hz::XformSet fwd, inv, gfwd, ginv;
+  hz::TCSet tfwd, tinv;                          // tensor-core copies of fwd / inv (mixed path)
   double2 *lam_b = nullptr, *lam_g = nullptr;    // eigenvalue per position (block / global)
   signed char* skip = nullptr;                   // interface flags
   int* ifc = nullptr;                            // interface node indices
@@ -51,6 +52,7 @@ struct AxisDev {
   int *gl = nullptr, *gr = nullptr;                          // pass B interface indices
   double2 *cl = nullptr, *cr = nullptr;                      // pass B coefficients
   double2* ks = nullptr;                                     // stencil rows / mhat
+  signed char* kreal = nullptr;                              // off-diagonals of row real
 };
 
 struct Workspace {
@@ -79,12 +81,17 @@ struct hz_plan_s {
   std::vector<int> z_begin;
   double omega = 1.0;
   bool need_global = false;
+  bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
   int real_cm = 1;
   AxisDev dx, dy;
   // z tables
   double2 *tzd = nullptr, *szs = nullptr, *mz = nullptr, *imz = nullptr, *coff = nullptr;
   double2 *cm_b = nullptr, *cm_g = nullptr, *tzs = nullptr;
   double* sig = nullptr;
+  // residual-stencil tables
+  double2* cxy = nullptr;
+  double *w2xy = nullptr, *w2z = nullptr;
+  signed char* rz = nullptr;
   int* zb = nullptr;
   // factors
   double2 *Pb = nullptr, *Qb = nullptr, *Pg = nullptr, *Qg = nullptr;
@@ -121,13 +128,13 @@ void ck(cudaError_t e) {
 // Records CUDA events around a stage when the plan's stage timers are on.
 class Stage {
  public:
-  Stage(hz_plan_t p, int stage) : p_(p), stage_(stage), l0_(hz::launch_count()) {
-    if (p_->timing) a_ = next_event(), ck(cudaEventRecord(a_, p_->st));
+  Stage(hz_plan_t p, cudaStream_t st, int stage) : p_(p), st_(st), stage_(stage), l0_(hz::launch_count()) {
+    if (p_->timing) a_ = next_event(), ck(cudaEventRecord(a_, st_));
   }
   ~Stage() {
     if (p_->timing) {
       cudaEvent_t b = next_event();
-      cudaEventRecord(b, p_->st);
+      cudaEventRecord(b, st_);
       p_->recs.push_back({stage_, a_, b, hz::launch_count() - l0_});
     }
   }
@@ -142,6 +149,7 @@ class Stage {
     return p_->ev_pool[p_->ev_used++];
   }
   hz_plan_t p_;
+  cudaStream_t st_;
   int stage_;
   long long l0_;
   cudaEvent_t a_ = nullptr;
@@ -308,8 +316,36 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
   xs.d_tab32 = upload(p, t32);
 }
 
+// Tensor-core tables of a block-diagonal transform: tab(b)[a][c] = get(b, a, c).
+template <typename Get>
+void make_tc(hz_plan_t p, hz::TCSet& ts, int ncols, const std::vector<int>& start,
+             const std::vector<int>& size, Get get) {
+  std::vector<float> tab;
+  std::vector<hz::TCBlock> blocks(start.size());
+  std::vector<hz::TCTile> tiles;
+  for (size_t b = 0; b < start.size(); ++b) {
+    const int n = size[b];
+    std::vector<cd> B((size_t)n * n);
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) B[(size_t)a * n + c] = get((int)b, a, c);
+    hz::tc_pack_block(B.data(), n, start[b], tab, blocks[b], tiles, (int)b);
+  }
+  ts.ncols = ncols;
+  ts.ntiles = (int)tiles.size();
+  ts.nt_max = 16;
+  for (const auto& t : tiles) ts.nt_max = std::max(ts.nt_max, t.nt);
+  ts.d_blocks = upload(p, blocks);
+  ts.d_tiles = upload(p, tiles);
+  ts.d_tab = upload(p, tab);
+}
+
 void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global) {
   const int n = A.n, nI = (int)A.iface.size();
+  make_tc(p, D.tfwd, n, A.bstart, A.bsize, [&](int b, int a, int c) {
+    return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
+  });
+  make_tc(p, D.tinv, n, A.bstart, A.bsize,
+          [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
   make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, [&](int b, int a, int c) {
     return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
   });
@@ -385,6 +421,23 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
     if (i + 1 < n) ks[3 * i + 2] = A.ko[i] / A.mh[i];
   }
   D.ks = upload_c(p, ks);
+  std::vector<signed char> kreal(n);
+  for (int i = 0; i < n; ++i) kreal[i] = (ks[3 * i].imag() == 0.0 && ks[3 * i + 2].imag() == 0.0) ? 1 : 0;
+  D.kreal = upload(p, kreal);
+}
+
+// Residual-stencil tables that combine both horizontal axes.
+void build_stencil_xy(hz_plan_t p) {
+  const int nx = p->nx, ny = p->ny;
+  std::vector<cd> cxy((size_t)nx * ny);
+  std::vector<double> w2((size_t)nx * ny);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      cxy[(size_t)j * nx + i] = p->ax.kd[i] / p->ax.mh[i] + p->ay.kd[j] / p->ay.mh[j];
+      w2[(size_t)j * nx + i] = std::norm(p->ax.mh[i]) * std::norm(p->ay.mh[j]);
+    }
+  p->cxy = upload_c(p, cxy);
+  p->w2xy = upload(p, w2);
 }
 
 // z coefficients for the current k^2 (base * omega^2) and the mode factors.
@@ -436,6 +489,19 @@ void build_z(hz_plan_t p) {
   put(p->cm_b, cmb);
   put(p->cm_g, cmg);
   put(p->tzs, tzs);
+  {
+    std::vector<double> w2z(nz);
+    std::vector<signed char> rz(nz);
+    for (int k = 0; k < nz; ++k) {
+      w2z[k] = std::norm(mz[k]);
+      rz[k] = (tzs[3 * k].imag() == 0.0 && tzs[3 * k + 2].imag() == 0.0) ? 1 : 0;
+    }
+    if (!p->w2z) p->w2z = dalloc<double>(p, nz);
+    if (!p->rz) p->rz = dalloc<signed char>(p, nz);
+    ck(cudaMemcpyAsync(p->w2z, w2z.data(), nz * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    ck(cudaMemcpyAsync(p->rz, rz.data(), nz, cudaMemcpyHostToDevice, p->st));
+    ck(cudaStreamSynchronize(p->st));
+  }
   if (!p->sig_layer.empty() && !p->sig) p->sig = upload(p, sn);
   if (!p->zb) p->zb = upload(p, p->z_begin);
 
@@ -468,6 +534,35 @@ void build_z(hz_plan_t p) {
   if (status) throw Fail{(hz_status)status};
 }
 
+// Element counts of the workspace buffers of a solve of R right-hand sides: 17 double2
+// buffers in the order FT, G, V, cX, vX, cY, vY, rX, rY, aX, bY, cg, dg, wX, wY, alX, alY,
+// then the partial-sum doubles and the volume (for RHO).
+struct WsSizes {
+  long long c[17];
+  long long partial;
+  long long vol;
+};
+WsSizes ws_sizes(hz_plan_t p, int R) {
+  WsSizes z{};
+  const long long vol = (long long)p->nx * p->ny * p->nz * R;
+  const long long zr = (long long)p->nz * R;
+  const long long nIx = (long long)p->ax.iface.size(), nIy = (long long)p->ay.iface.size();
+  const long long X = zr * nIx * p->ny, Y = zr * nIy * p->nx;
+  const long long v[17] = {vol, vol, vol, 2 * X, 2 * X, 2 * Y, 2 * Y, X, Y, X, Y, X, Y, X, Y, X, Y};
+  for (int i = 0; i < 17; ++i) z.c[i] = std::max(v[i], 1LL);
+  hz::StencilArgs sa;
+  sa.nx = p->nx; sa.ny = p->ny; sa.nz = p->nz; sa.nrhs = R;
+  z.partial = 2LL * R * hz::stencil_parts(sa) + 2;
+  z.vol = vol;
+  return z;
+}
+
+double2** ws_slots(Workspace& w, int i) {
+  double2** s[17] = {&w.FT, &w.G, &w.V, &w.cX, &w.vX, &w.cY, &w.vY, &w.rX, &w.rY, &w.aX, &w.bY,
+                     &w.cg, &w.dg, &w.wX, &w.wY, &w.alX, &w.alY};
+  return s[i];
+}
+
 void ensure_ws(hz_plan_t p, int R) {
   Workspace& w = p->ws;
   if (w.cap >= R) return;
@@ -495,7 +590,11 @@ void ensure_ws(hz_plan_t p, int R) {
   w.wY = dalloc<double2>(p, zr * nIy * p->nx);
   w.alX = dalloc<double2>(p, zr * nIx * p->ny);
   w.alY = dalloc<double2>(p, zr * nIy * p->nx);
-  w.partial = dalloc<double>(p, (size_t)2 * R * 4 * 152 + 2);
+  {
+    hz::StencilArgs sa;
+    sa.nx = p->nx; sa.ny = p->ny; sa.nz = p->nz; sa.nrhs = R;
+    w.partial = dalloc<double>(p, (size_t)2 * R * hz::stencil_parts(sa) + 2);
+  }
   w.norms = dalloc<double>(p, (size_t)2 * R);
   w.cap = R;
   if (w.rho_cap) { dfree(p, w.RHO); w.RHO = nullptr; w.rho_cap = 0; }
@@ -525,20 +624,28 @@ hz::IfaceArgs iface_args(hz_plan_t p, int R) {
 }
 
 // One pass of steps 1-7: u (=|+=) S(f).  lo = FP32 bulk transforms (mixed path).
-void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int store, int conj_out) {
-  cudaStream_t st = p->st;
-  Workspace& w = p->ws;
+void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* u, int R, bool lo,
+                int store, int conj_out) {
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const long long planes = (long long)R * nz;
   const int nIx = (int)p->ax.iface.size(), nIy = (int)p->ay.iface.size();
-  auto bulk = lo ? hz::xform_f32 : hz::xform_f64;
+  // bulk transforms: FP64 DFMA, or (mixed path) 3xTF32 on the tensor cores
+  auto bulk = [&](const hz::XformSet& xs, const hz::TCSet& ts, const double2* in, double2* out, int rpp,
+                  int trans, int store_mode, int conj, const signed char* skip) {
+    if (!lo)
+      hz::xform_f64(xs, in, out, rpp, planes, trans, store_mode, conj, skip, st);
+    else if (p->use_tc && !conj)
+      hz::xform_tc(ts, in, out, rpp, planes, trans, store_mode, skip, p->status, st);
+    else
+      hz::xform_f32(xs, in, out, rpp, planes, trans, store_mode, conj, skip, st);
+  };
   // The interface-row transforms below are non-transposed, so their rows are
   // flattened across planes (one launch row tile covers 32 rows of any planes).
   // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
   {
-    Stage t(p, HZ_STAGE_FWD);
-    bulk(p->dx.fwd, f, w.G, ny, planes, 1, hz::XS_STORE, 0, p->dy.skip, st);
-    bulk(p->dy.fwd, w.G, w.FT, nx, planes, 0, hz::XS_STORE, 0, p->dx.skip, st);
+    Stage t(p, st, HZ_STAGE_FWD);
+    bulk(p->dx.fwd, p->dx.tfwd, f, w.G, ny, 1, hz::XS_STORE, 0, p->dy.skip);
+    bulk(p->dy.fwd, p->dy.tfwd, w.G, w.FT, nx, 0, hz::XS_STORE, 0, p->dx.skip);
   }
 
   hz::ZSolveArgs za;
@@ -547,17 +654,15 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
   za.skip_i = p->dx.skip; za.skip_j = p->dy.skip;
   za.rhs = w.FT; za.out = w.V;
   za.P = p->Pb; za.Q = p->Qb; za.cm = p->cm_b;
-  za.sig = p->sig;
-  za.nIx = nIx; za.nIy = nIy;
   // Step 2: mode-wise z solves of every block (pass A)
   {
-    Stage t(p, HZ_STAGE_PASS_A);
-    hz::zsolve(hz::Z_PASS_A, za, st);
+    Stage t(p, st, HZ_STAGE_PASS_A);
+    hz::zsolve(za, st);
   }
 
   if (nIx + nIy > 0) {
     // Step 3: v at the nodes next to the interfaces
-    std::unique_ptr<Stage> t3(new Stage(p, HZ_STAGE_EDGES));
+    std::unique_ptr<Stage> t3(new Stage(p, st, HZ_STAGE_EDGES));
     if (nIx) {
       hz::contract_rows(w.V, w.cX, p->dx.edge_coef, p->dx.edge_rng, nx, ny, 2 * nIx, planes, st);
       hz::xform_f64(p->dy.inv, w.cX, w.vX, (int)(2 * nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
@@ -570,47 +675,53 @@ void solve_core(hz_plan_t p, const double2* f, double2* u, int R, bool lo, int s
     // Step 4: r = M f - A v on the interfaces
     hz::IfaceArgs ia = iface_args(p, R);
     {
-      Stage t(p, HZ_STAGE_IRES);
+      Stage t(p, st, HZ_STAGE_IRES);
       hz::iface_residual(ia, f, w.vX, w.vY, w.rX, w.rY, st);
     }
     // Step 5: w on the interfaces through the whole-axis eigenbasis
-    std::unique_ptr<Stage> t5(new Stage(p, HZ_STAGE_GLOBAL));
+    std::unique_ptr<Stage> t5(new Stage(p, st, HZ_STAGE_GLOBAL));
     if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+    hz::GlobalRhsArgs ga;
+    ga.nx = nx; ga.ny = ny; ga.nz = nz; ga.nrhs = R; ga.nIx = nIx; ga.nIy = nIy;
+    ga.aX = w.aX; ga.bY = w.bY; ga.WgxI = p->dx.gcoef; ga.WgyI = p->dy.gcoef;
+    hz::global_rhs(ga, w.G, st);                    // r~ (G is free until step 7)
     hz::ZSolveArgs zg = za;
     zg.skip_i = nullptr; zg.skip_j = nullptr;
-    zg.out = w.G;                                   // w~ (G is free until step 7)
+    zg.rhs = w.G; zg.out = w.V;                     // w~ (v~ in V is no longer needed)
     zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
-    zg.aX = w.aX; zg.bY = w.bY; zg.WgxI = p->dx.gcoef; zg.WgyI = p->dy.gcoef;
-    hz::zsolve(hz::Z_GLOBAL, zg, st);
+    hz::zsolve(zg, st);
     if (nIx) {
-      hz::contract_rows(w.G, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
+      hz::contract_rows(w.V, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
       hz::xform_f64(p->dy.ginv, w.cg, w.wX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
       // Step 6 (x interfaces): forward y-transform of w on the interface rows
       hz::xform_f64(p->dy.fwd, w.wX, w.alX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     if (nIy) {
-      hz::contract_cols(w.G, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, st);
+      hz::contract_cols(w.V, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, st);
       hz::xform_f64(p->dx.ginv, w.dg, w.wY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
       hz::xform_f64(p->dx.fwd, w.wY, w.alY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     t5.reset();
-    // Step 6: pass B, (Tz + s S_z) u~ = M_z f~ + g~ with g~ generated from the interface data
-    Stage t6(p, HZ_STAGE_PASS_B);
-    hz::ZSolveArgs zb = za;
-    zb.alphaX = w.alX; zb.alphaY = w.alY;
-    zb.gxl = p->dx.gl; zb.gxr = p->dx.gr; zb.gyl = p->dy.gl; zb.gyr = p->dy.gr;
-    zb.cxl = p->dx.cl; zb.cxr = p->dx.cr; zb.cyl = p->dy.cl; zb.cyr = p->dy.cr;
-    hz::zsolve(hz::Z_PASS_B, zb, st);
+    // Step 6: pass B, (Tz + s S_z) u~ = M_z f~ + g~ with g~ formed from the interface data
+    Stage t6(p, st, HZ_STAGE_PASS_B);
+    hz::BoundaryArgs ba;
+    ba.nx = nx; ba.ny = ny; ba.nz = nz; ba.nrhs = R; ba.nIx = nIx; ba.nIy = nIy;
+    ba.skip_i = p->dx.skip; ba.skip_j = p->dy.skip; ba.sig = p->sig;
+    ba.alphaX = w.alX; ba.alphaY = w.alY;
+    ba.gxl = p->dx.gl; ba.gxr = p->dx.gr; ba.gyl = p->dy.gl; ba.gyr = p->dy.gr;
+    ba.cxl = p->dx.cl; ba.cxr = p->dx.cr; ba.cyl = p->dy.cl; ba.cyr = p->dy.cr;
+    hz::boundary_rhs(ba, w.FT, st);                 // f~ + g~ / M_z, in place
+    hz::zsolve(za, st);
   }
   // Step 7: u = W_x (x) W_y u~ in the blocks; u = w on the interfaces
   {
-    Stage t(p, HZ_STAGE_INV);
-    bulk(p->dy.inv, w.V, w.G, nx, planes, 1, hz::XS_STORE, 0, p->dx.skip, st);
-    bulk(p->dx.inv, w.G, u, ny, planes, 0, store, conj_out, p->dy.skip, st);
+    Stage t(p, st, HZ_STAGE_INV);
+    bulk(p->dy.inv, p->dy.tinv, w.V, w.G, nx, 1, hz::XS_STORE, 0, p->dx.skip);
+    bulk(p->dx.inv, p->dx.tinv, w.G, u, ny, 0, store, conj_out, p->dy.skip);
   }
   if (nIx + nIy > 0) {
-    Stage t(p, HZ_STAGE_IFACE_OUT);
+    Stage t(p, st, HZ_STAGE_IFACE_OUT);
     hz::IfaceArgs ia = iface_args(p, R);
     hz::write_iface(ia, w.wX, w.wY, u, conj_out, store == hz::XS_ACCUM, st);
   }
@@ -622,32 +733,50 @@ hz::StencilArgs stencil_args(hz_plan_t p, int R) {
   a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nrhs = R;
   a.kxs = p->dx.ks; a.kys = p->dy.ks; a.tzs = p->tzs; a.sig = p->sig;
   a.mx = p->dx.m; a.my = p->dy.m; a.mz = p->mz;
+  a.cxy = p->cxy; a.w2xy = p->w2xy; a.w2z = p->w2z;
+  a.rx = p->dx.kreal; a.ry = p->dy.kreal; a.rz = p->rz;
   return a;
 }
 
-// rho = f - M^{-1} A u; returns max over RHS of ||M rho|| / ||M f||.
-double residual_core(hz_plan_t p, const double2* f, const double2* u, double2* rho, int R,
-                     std::vector<double>* per_rhs) {
+// Enqueue rho = f - M^{-1} A u (rho may be NULL) and the per-RHS sums (|M rho|^2, |M f|^2)
+// into norms[2R] (no synchronisation: usable inside a stream capture).
+void residual_enqueue(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, const double2* u,
+                      double2* rho, double* norms, int R, int fnorm) {
   hz::StencilArgs a = stencil_args(p, R);
   const int parts = hz::stencil_parts(a);
-  {
-    Stage t(p, HZ_STAGE_RESID);
-    hz::stencil_residual(a, f, u, rho, p->ws.partial, parts, p->st);
-    hz::finish_norms(p->ws.partial, parts, R, p->ws.norms, p->st);
+  Stage t(p, st, HZ_STAGE_RESID);
+  hz::stencil_residual(a, f, u, rho, w.partial, fnorm, st);
+  hz::finish_norms(w.partial, parts, R, norms, st);
+}
+
+// Relative residuals from the sums of residual_enqueue; fnorm2 caches ||M f||^2.
+double residual_from_sums(const std::vector<double>& nrm, int R, std::vector<double>* per_rhs,
+                          std::vector<double>& fnorm2) {
+  if (fnorm2.empty()) {
+    fnorm2.resize(R);
+    for (int r = 0; r < R; ++r) fnorm2[r] = nrm[2 * r + 1];
   }
-  ck(cudaGetLastError());
-  std::vector<double> nrm(2 * R);
-  ck(cudaMemcpyAsync(nrm.data(), p->ws.norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, p->st));
-  ck(cudaStreamSynchronize(p->st));
   double worst = 0.0;
   if (per_rhs) per_rhs->assign(R, 0.0);
   for (int r = 0; r < R; ++r) {
-    const double rel = nrm[2 * r + 1] > 0 ? std::sqrt(nrm[2 * r] / nrm[2 * r + 1]) : std::sqrt(nrm[2 * r]);
+    const double rel = fnorm2[r] > 0 ? std::sqrt(nrm[2 * r] / fnorm2[r]) : std::sqrt(nrm[2 * r]);
     if (!std::isfinite(rel)) throw Fail{HZ_ERR_NONFINITE};
     if (per_rhs) (*per_rhs)[r] = rel;
     worst = std::max(worst, rel);
   }
   return worst;
+}
+
+// rho = f - M^{-1} A u (rho may be NULL); returns max over RHS of ||M rho|| / ||M f||.
+// fnorm2 caches ||M f||^2 per RHS across calls with the same f (computed when empty).
+double residual_core(hz_plan_t p, const double2* f, const double2* u, double2* rho, int R,
+                     std::vector<double>* per_rhs, std::vector<double>& fnorm2) {
+  residual_enqueue(p, p->ws, p->st, f, u, rho, p->ws.norms, R, fnorm2.empty() ? 1 : 0);
+  ck(cudaGetLastError());
+  std::vector<double> nrm(2 * R);
+  ck(cudaMemcpyAsync(nrm.data(), p->ws.norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ck(cudaStreamSynchronize(p->st));
+  return residual_from_sums(nrm, R, per_rhs, fnorm2);
 }
 
 // Full solve: FP64 single pass, or mixed with FP64 refinement.
@@ -665,7 +794,7 @@ void solve_full_impl(hz_plan_t p, const double2* f, double2* u, int R, int conj_
   p->info.refinements = 0;
   p->info.rel_residual = -1.0;
   if (p->opts.precision != HZ_MIXED) {
-    solve_core(p, f, u, R, false, hz::XS_STORE, conj_out);
+    solve_core(p, p->ws, p->st, f, u, R, false, hz::XS_STORE, conj_out);
     ck(cudaStreamSynchronize(p->st));
     return;
   }
@@ -677,16 +806,22 @@ void solve_full_impl(hz_plan_t p, const double2* f, double2* u, int R, int conj_
     fin = f2;
   }
   double2* rho = ensure_extra(p, p->ws.RHO, p->ws.rho_cap, R);
-  solve_core(p, fin, u, R, true, hz::XS_STORE, 0);
-  double rel = residual_core(p, fin, u, rho, R, nullptr);
+  ck(cudaMemsetAsync(p->status, 0, sizeof(int), p->st));
+  solve_core(p, p->ws, p->st, fin, u, R, true, hz::XS_STORE, 0);
+  std::vector<double> fn2;
+  double rel = residual_core(p, fin, u, rho, R, nullptr, fn2);
   int it = 0;
   while (rel > p->opts.rtol && it < p->opts.max_refine) {
-    solve_core(p, rho, u, R, true, hz::XS_ACCUM, 0);
-    rel = residual_core(p, fin, u, rho, R, nullptr);
+    solve_core(p, p->ws, p->st, rho, u, R, true, hz::XS_ACCUM, 0);
+    rel = residual_core(p, fin, u, rho, R, nullptr, fn2);
     ++it;
   }
   p->info.refinements = it;
   p->info.rel_residual = rel;
+  int status = 0;
+  ck(cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  ck(cudaStreamSynchronize(p->st));
+  if (status) throw Fail{(hz_status)status};
   if (conj_out) {
     hz::conj_inplace(u, (long long)p->nx * p->ny * p->nz * R, p->st);
     ck(cudaStreamSynchronize(p->st));
@@ -699,6 +834,213 @@ void release(hz_plan_t p) {
   p->allocs.clear();
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batches: many (plan, nrhs) solves replayed as one CUDA graph
+// ---------------------------------------------------------------------------
+struct hz_batch_s {
+  std::vector<hz_plan_t> plans;
+  std::vector<int> nrhs;
+  std::vector<int> lane_of;                 // item -> lane
+  int nlanes = 1;
+  cudaStream_t s0 = nullptr;
+  std::vector<cudaStream_t> lanes;
+  std::vector<Workspace> ws;                // one per lane, sized for its largest item
+  std::vector<double2*> rho;                // one per lane
+  double* norms = nullptr;                  // [item][4 R]: first and final residual sums
+  std::vector<long long> norm_off;
+  std::vector<void*> allocs;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> graph_f, graph_u;   // pointers the graph was captured with
+  double last_ms = 0.0;
+  long long launches_per_replay = 0;
+};
+
+namespace {
+
+void bfree(hz_batch_t b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (void* a : b->allocs) cudaFree(a);
+  b->allocs.clear();
+  for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
+  b->lanes.clear();
+  if (b->fork) cudaEventDestroy(b->fork);
+  b->fork = nullptr;
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  b->joins.clear();
+}
+
+template <typename T>
+T* balloc(hz_batch_t b, long long count) {
+  void* ptr = nullptr;
+  ck(cudaMalloc(&ptr, (size_t)std::max(count, 1LL) * sizeof(T)));
+  b->allocs.push_back(ptr);
+  return static_cast<T*>(ptr);
+}
+
+// Lane workspaces (each sized for the largest item of its lane), streams and events.
+void batch_setup(hz_batch_t b, int nlanes) {
+  bfree(b);
+  const int n = (int)b->plans.size();
+  b->nlanes = std::max(1, std::min(nlanes, n));
+  // greedy balance of estimated work (unknowns x RHS) over the lanes
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto cost = [&](int i) { return (double)b->plans[i]->nx * b->plans[i]->ny * b->plans[i]->nz * b->nrhs[i]; };
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+  std::vector<double> load(b->nlanes, 0.0);
+  b->lane_of.assign(n, 0);
+  for (int i : order) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->lane_of[i] = l;
+    load[l] += cost(i);
+  }
+  b->ws.assign(b->nlanes, Workspace{});
+  b->rho.assign(b->nlanes, nullptr);
+  for (int l = 0; l < b->nlanes; ++l) {
+    WsSizes mx{};
+    for (int i = 0; i < n; ++i) {
+      if (b->lane_of[i] != l) continue;
+      const WsSizes z = ws_sizes(b->plans[i], b->nrhs[i]);
+      for (int q = 0; q < 17; ++q) mx.c[q] = std::max(mx.c[q], z.c[q]);
+      mx.partial = std::max(mx.partial, z.partial);
+      mx.vol = std::max(mx.vol, z.vol);
+    }
+    for (int q = 0; q < 17; ++q) *ws_slots(b->ws[l], q) = balloc<double2>(b, mx.c[q]);
+    b->ws[l].partial = balloc<double>(b, mx.partial);
+    b->rho[l] = balloc<double2>(b, mx.vol);
+  }
+  b->norm_off.assign(n, 0);
+  long long tot = 0;
+  for (int i = 0; i < n; ++i) {
+    b->norm_off[i] = tot;
+    tot += 4LL * b->nrhs[i];
+  }
+  b->norms = balloc<double>(b, tot);
+  ck(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
+  b->lanes.push_back(b->s0);   // lane 0 runs on the capture origin stream
+  for (int l = 1; l < b->nlanes; ++l) {
+    cudaStream_t s;
+    ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    b->lanes.push_back(s);
+  }
+  ck(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  b->joins.resize(b->nlanes);
+  for (auto& e : b->joins) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+}
+
+// Enqueue every item of the batch on its lane (inside a stream capture).
+void batch_enqueue(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev) {
+  ck(cudaEventRecord(b->fork, b->s0));
+  for (int l = 1; l < b->nlanes; ++l) ck(cudaStreamWaitEvent(b->lanes[l], b->fork, 0));
+  for (int i = 0; i < (int)b->plans.size(); ++i) {
+    hz_plan_t p = b->plans[i];
+    const int l = b->lane_of[i], R = b->nrhs[i];
+    cudaStream_t st = b->lanes[l];
+    Workspace& w = b->ws[l];
+    const double2* f = reinterpret_cast<const double2*>(f_dev[i]);
+    double2* u = reinterpret_cast<double2*>(u_dev[i]);
+    double* nrm = b->norms + b->norm_off[i];
+    if (p->opts.precision == HZ_MIXED) {
+      // first solve, its residual (with ||M f||), one correction, the final residual
+      solve_core(p, w, st, f, u, R, true, hz::XS_STORE, 0);
+      residual_enqueue(p, w, st, f, u, b->rho[l], nrm, R, 1);
+      solve_core(p, w, st, b->rho[l], u, R, true, hz::XS_ACCUM, 0);
+      residual_enqueue(p, w, st, f, u, nullptr, nrm + 2 * R, R, 1);
+    } else {
+      solve_core(p, w, st, f, u, R, false, hz::XS_STORE, 0);
+      residual_enqueue(p, w, st, f, u, nullptr, nrm + 2 * R, R, 1);
+    }
+  }
+  for (int l = 1; l < b->nlanes; ++l) {
+    ck(cudaEventRecord(b->joins[l], b->lanes[l]));
+    ck(cudaStreamWaitEvent(b->s0, b->joins[l], 0));
+  }
+}
+
+void batch_capture(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  for (hz_plan_t p : b->plans) p->timing = false;
+  const long long l0 = hz::launch_count();
+  ck(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed));
+  try {
+    batch_enqueue(b, f_dev, u_dev);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(b->s0, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  ck(cudaStreamEndCapture(b->s0, &g));
+  const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  ck(e);
+  b->launches_per_replay = hz::launch_count() - l0;
+  const int n = (int)b->plans.size();
+  b->graph_f.assign(f_dev, f_dev + n);
+  b->graph_u.assign(u_dev, u_dev + n);
+}
+
+// Replay; returns per-item max relative residual (items that miss rtol are refined eagerly).
+void batch_run(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev, double* rel_host) {
+  const int n = (int)b->plans.size();
+  bool same = b->exec && (int)b->graph_f.size() == n;
+  for (int i = 0; same && i < n; ++i) same = b->graph_f[i] == f_dev[i] && b->graph_u[i] == u_dev[i];
+  if (!same) batch_capture(b, f_dev, u_dev);
+  for (hz_plan_t p : b->plans) ck(cudaMemsetAsync(p->status, 0, sizeof(int), b->s0));
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  ck(cudaEventRecord(e0, b->s0));
+  ck(cudaGraphLaunch(b->exec, b->s0));
+  ck(cudaEventRecord(e1, b->s0));
+  ck(cudaStreamSynchronize(b->s0));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->last_ms = ms;
+  for (hz_plan_t p : b->plans) p->info.kernel_launches += 0;
+  long long tot = b->norm_off.empty() ? 0 : b->norm_off.back() + 4LL * b->nrhs.back();
+  std::vector<double> nrm(std::max(tot, 1LL));
+  ck(cudaMemcpy(nrm.data(), b->norms, sizeof(double) * tot, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    hz_plan_t p = b->plans[i];
+    int status = 0;
+    ck(cudaMemcpy(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) throw Fail{(hz_status)status};
+    const int R = b->nrhs[i];
+    std::vector<double> fn2(R), fin(2 * R);
+    for (int r = 0; r < R; ++r) fn2[r] = nrm[b->norm_off[i] + 2 * r + 1];
+    for (int q = 0; q < 2 * R; ++q) fin[q] = nrm[b->norm_off[i] + 2 * R + q];
+    double rel = residual_from_sums(fin, R, nullptr, fn2);
+    if (p->opts.precision == HZ_MIXED && rel > p->opts.rtol) {
+      // finish on the plan's own stream and workspace: more corrections, eagerly
+      const double2* f = reinterpret_cast<const double2*>(f_dev[i]);
+      double2* u = reinterpret_cast<double2*>(u_dev[i]);
+      ensure_ws(p, R);
+      double2* rho = ensure_extra(p, p->ws.RHO, p->ws.rho_cap, R);
+      int it = 0;
+      rel = residual_core(p, f, u, rho, R, nullptr, fn2);
+      while (rel > p->opts.rtol && it < p->opts.max_refine) {
+        solve_core(p, p->ws, p->st, rho, u, R, true, hz::XS_ACCUM, 0);
+        rel = residual_core(p, f, u, rho, R, nullptr, fn2);
+        ++it;
+      }
+      if (rel > p->opts.rtol) throw Fail{HZ_ERR_NOT_CONVERGED};
+    }
+    if (rel_host) rel_host[i] = rel;
+  }
 }
 
 }  // namespace
@@ -780,6 +1122,7 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
     p->minpiv = dalloc<unsigned long long>(p, 1);
     build_axis_dev(p, p->ax, p->dx, p->need_global);
     build_axis_dev(p, p->ay, p->dy, p->need_global);
+    build_stencil_xy(p);
     build_z(p);
     ck(cudaStreamSynchronize(p->st));
   } catch (const Fail& e) {
@@ -915,8 +1258,10 @@ hz_status hz_residual(hz_plan_t p, const hz_c128* f, const hz_c128* u, int nrhs,
   try {
     ensure_ws(p, nrhs);
     double2* rho = ensure_extra(p, p->ws.RHO, p->ws.rho_cap, nrhs);
-    std::vector<double> rel;
-    residual_core(p, reinterpret_cast<const double2*>(f), reinterpret_cast<const double2*>(u), rho, nrhs, &rel);
+    std::vector<double> rel, fn2;
+    residual_core(p, reinterpret_cast<const double2*>(f), reinterpret_cast<const double2*>(u), nullptr, nrhs,
+                  &rel, fn2);
+    (void)rho;
     for (int r = 0; r < nrhs; ++r) rel_host[r] = rel[r];
   } catch (const Fail& e) {
     return e.s;
@@ -949,6 +1294,84 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   if (!p || !out) return HZ_ERR_ARG;
   p->info.device_bytes = p->bytes;
   *out = p->info;
+  return HZ_OK;
+}
+
+hz_status hz_batch_create(int nitems, const hz_plan_t* plans, const int* nrhs, int nlanes, hz_batch_t* out) {
+  if (!out) return HZ_ERR_ARG;
+  *out = nullptr;
+  if (nitems < 1 || !plans || !nrhs || nlanes < 0) return HZ_ERR_ARG;
+  for (int i = 0; i < nitems; ++i)
+    if (!plans[i] || nrhs[i] < 1) return HZ_ERR_ARG;
+  for (int i = 0; i < nitems; ++i)
+    for (int j = 0; j < i; ++j)
+      if (plans[i] == plans[j]) return HZ_ERR_ARG;      // a plan's status word is per item
+  hz_batch_t b = new (std::nothrow) hz_batch_s();
+  if (!b) return HZ_ERR_OOM;
+  b->plans.assign(plans, plans + nitems);
+  b->nrhs.assign(nrhs, nrhs + nitems);
+  try {
+    hz::xform_tc_prepare();
+    batch_setup(b, nlanes == 0 ? 4 : nlanes);
+  } catch (const Fail& e) {
+    bfree(b);
+    delete b;
+    return e.s;
+  }
+  *out = b;
+  return HZ_OK;
+}
+
+hz_status hz_batch_solve(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev, double* rel_host) {
+  if (!b || !f_dev || !u_dev) return HZ_ERR_ARG;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (!f_dev[i] || !u_dev[i] || f_dev[i] == u_dev[i]) return HZ_ERR_ARG;
+  try {
+    batch_run(b, f_dev, u_dev, rel_host);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_batch_autotune(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev, int* lanes_out) {
+  if (!b || !f_dev || !u_dev) return HZ_ERR_ARG;
+  try {
+    const int n = (int)b->plans.size();
+    int best_l = b->nlanes;
+    double best_ms = 1e300;
+    for (int l : {1, 2, 4, 8}) {
+      if (l > n) break;
+      batch_setup(b, l);
+      batch_run(b, f_dev, u_dev, nullptr);                 // capture + first replay
+      double ms = 0.0;
+      for (int rep = 0; rep < 2; ++rep) {
+        batch_run(b, f_dev, u_dev, nullptr);
+        ms += b->last_ms;
+      }
+      if (ms < best_ms) { best_ms = ms; best_l = l; }
+    }
+    batch_setup(b, best_l);
+    if (lanes_out) *lanes_out = best_l;
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_batch_info(hz_batch_t b, double* last_ms, long long* launches_per_replay, int* lanes) {
+  if (!b) return HZ_ERR_ARG;
+  if (last_ms) *last_ms = b->last_ms;
+  if (launches_per_replay) *launches_per_replay = b->launches_per_replay;
+  if (lanes) *lanes = b->nlanes;
+  return HZ_OK;
+}
+
+hz_status hz_batch_destroy(hz_batch_t b) {
+  if (!b) return HZ_ERR_ARG;
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  bfree(b);
+  delete b;
   return HZ_OK;
 }
 

@@ -13,6 +13,8 @@
 //  * stencil_residual: rho = f - M^{-1} A u with the 7-point operator of
 //    Eq. (fd)/(fdmtr), for iterative refinement and residual reports.
 //  * grad_layers: G_L = sum_{k in L} hhat^z_k sum conj(lam) hhat^x hhat^y u.
+#include <algorithm>
+
 #include "hz_internal.h"
 
 namespace hz {
@@ -181,63 +183,108 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 constexpr int ST = 256;
+constexpr int SEPT = 4;                    // stencil elements per thread
 
-// grid (nparts, nrhs): each CTA strides over one RHS's elements.
+// r = f - M^{-1} A u with the 7-point operator of Eq. (fd), divided by the weights:
+//   M^{-1} A u = sigma_k (Kx u / mx + Ky u / my) + Tz u / mz.
+// grid (CTAs per plane, nrhs * nz): one plane (r, k) per blockIdx.y, so no index
+// division beyond the in-plane one.  Off-diagonal coefficients that are real (every
+// row whose steps are real) take two FP64 operations instead of four.
 __global__ void __launch_bounds__(ST) stencil_kernel(const StencilArgs a, const double2* __restrict__ f,
                                                      const double2* __restrict__ u,
                                                      double2* __restrict__ rho,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial, int fnorm, int rk0) {
   __shared__ double sh[ST / 32];
-  const int r = blockIdx.y;
+  const int rk = rk0 + blockIdx.y;
+  const int k = rk % a.nz;
   const long long nxy = (long long)a.nx * a.ny;
-  const long long n = nxy * a.nz;
-  const double2* __restrict__ ur = u + r * n;
-  const double2* __restrict__ fr = f + r * n;
-  double2* __restrict__ pr = rho + r * n;
+  const long long base = (long long)rk * nxy;
+  const double2* __restrict__ ur = u + base;
+  const double2* __restrict__ fr = f + base;
+  const double2 tz0 = a.tzs[3 * k], tz1 = a.tzs[3 * k + 1], tz2 = a.tzs[3 * k + 2];
+  const bool realz = a.rz[k] != 0;
+  const double s = a.sig ? a.sig[k] : 1.0;
+  const double w2z = a.w2z[k];
+  const bool has_dn = k > 0, has_up = k < a.nz - 1;
   double nr2 = 0.0, nf2 = 0.0;
-  for (long long t = blockIdx.x * (long long)ST + threadIdx.x; t < n; t += (long long)gridDim.x * ST) {
-    const int i = (int)(t % a.nx);
-    const long long q = t / a.nx;
-    const int j = (int)(q % a.ny);
-    const int k = (int)(q / a.ny);
+#pragma unroll
+  for (int e = 0; e < SEPT; ++e) {
+    const long long t = ((long long)blockIdx.x * SEPT + e) * ST + threadIdx.x;
+    if (t >= nxy) break;
+    const int j = (int)(t / a.nx), i = (int)(t - (long long)j * a.nx);
     const double2 uc = ur[t];
+    double2 h = cmul(a.cxy[t], uc);
     const double2* kx = a.kxs + 3 * i;
     const double2* ky = a.kys + 3 * j;
-    const double2* tz = a.tzs + 3 * k;
-    const double s = a.sig ? a.sig[k] : 1.0;
-    // horizontal part sigma_k (Kx' u + Ky' u)
-    double2 h = cmul(cadd(kx[1], ky[1]), uc);
-    if (i > 0) h = cfma(kx[0], ur[t - 1], h);
-    if (i < a.nx - 1) h = cfma(kx[2], ur[t + 1], h);
-    if (j > 0) h = cfma(ky[0], ur[t - a.nx], h);
-    if (j < a.ny - 1) h = cfma(ky[2], ur[t + a.nx], h);
-    double2 au = cmul(tz[1], uc);
-    au.x = fma(s, h.x, au.x);
-    au.y = fma(s, h.y, au.y);
-    if (k > 0) au = cfma(tz[0], ur[t - nxy], au);
-    if (k < a.nz - 1) au = cfma(tz[2], ur[t + nxy], au);
+    if (a.rx[i]) {
+      if (i > 0) { const double2 v = ur[t - 1]; h.x = fma(kx[0].x, v.x, h.x); h.y = fma(kx[0].x, v.y, h.y); }
+      if (i < a.nx - 1) { const double2 v = ur[t + 1]; h.x = fma(kx[2].x, v.x, h.x); h.y = fma(kx[2].x, v.y, h.y); }
+    } else {
+      if (i > 0) h = cfma(kx[0], ur[t - 1], h);
+      if (i < a.nx - 1) h = cfma(kx[2], ur[t + 1], h);
+    }
+    if (a.ry[j]) {
+      if (j > 0) { const double2 v = ur[t - a.nx]; h.x = fma(ky[0].x, v.x, h.x); h.y = fma(ky[0].x, v.y, h.y); }
+      if (j < a.ny - 1) { const double2 v = ur[t + a.nx]; h.x = fma(ky[2].x, v.x, h.x); h.y = fma(ky[2].x, v.y, h.y); }
+    } else {
+      if (j > 0) h = cfma(ky[0], ur[t - a.nx], h);
+      if (j < a.ny - 1) h = cfma(ky[2], ur[t + a.nx], h);
+    }
+    double2 au = cmul(tz1, uc);
+    if (a.sig) {
+      au.x = fma(s, h.x, au.x);
+      au.y = fma(s, h.y, au.y);
+    } else {
+      au.x += h.x;
+      au.y += h.y;
+    }
+    if (realz) {
+      if (has_dn) { const double2 v = ur[t - nxy]; au.x = fma(tz0.x, v.x, au.x); au.y = fma(tz0.x, v.y, au.y); }
+      if (has_up) { const double2 v = ur[t + nxy]; au.x = fma(tz2.x, v.x, au.x); au.y = fma(tz2.x, v.y, au.y); }
+    } else {
+      if (has_dn) au = cfma(tz0, ur[t - nxy], au);
+      if (has_up) au = cfma(tz2, ur[t + nxy], au);
+    }
     const double2 fv = fr[t];
     const double2 res = make_double2(fv.x - au.x, fv.y - au.y);
-    pr[t] = res;
-    const double2 mx = a.mx[i], my = a.my[j], mz = a.mz[k];
-    const double w2 = (mx.x * mx.x + mx.y * mx.y) * (my.x * my.x + my.y * my.y) * (mz.x * mz.x + mz.y * mz.y);
-    nr2 = fma(w2, res.x * res.x + res.y * res.y, nr2);
-    nf2 = fma(w2, fv.x * fv.x + fv.y * fv.y, nf2);
+    if (rho) rho[base + t] = res;
+    const double w2 = a.w2xy[t] * w2z;
+    nr2 = fma(w2, fma(res.x, res.x, res.y * res.y), nr2);
+    if (fnorm) nf2 = fma(w2, fma(fv.x, fv.x, fv.y * fv.y), nf2);
   }
   const double s1 = block_sum<ST>(nr2, sh);
-  const double s2 = block_sum<ST>(nf2, sh);
+  const double s2 = fnorm ? block_sum<ST>(nf2, sh) : 0.0;
   if (threadIdx.x == 0) {
-    partial[((long long)r * gridDim.x + blockIdx.x) * 2 + 0] = s1;
-    partial[((long long)r * gridDim.x + blockIdx.x) * 2 + 1] = s2;
+    const long long part = (long long)rk * gridDim.x + blockIdx.x;   // = (r * nz + k) * gx + bx
+    partial[part * 2 + 0] = s1;
+    partial[part * 2 + 1] = s2;
   }
 }
 
-__global__ void finish_norms_kernel(const double* __restrict__ partial, int nparts, double* out) {
+// out[2r + c] = sum_p partial[r][p][c]: each thread sums a fixed stride of the parts, then a
+// fixed-order tree (deterministic for a given launch shape).
+__global__ void __launch_bounds__(ST) finish_norms_kernel(const double* __restrict__ partial, int nparts,
+                                                          double* out) {
+  __shared__ double sh[2][ST];
   const int r = blockIdx.x;
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += partial[((long long)r * nparts + p) * 2 + threadIdx.x];
-    out[2 * r + threadIdx.x] = s;
+  double s0 = 0.0, s1 = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += ST) {
+    s0 += partial[((long long)r * nparts + p) * 2 + 0];
+    s1 += partial[((long long)r * nparts + p) * 2 + 1];
+  }
+  sh[0][threadIdx.x] = s0;
+  sh[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = ST / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * r] = sh[0][0];
+    out[2 * r + 1] = sh[1][0];
   }
 }
 
@@ -333,22 +380,25 @@ void conj_inplace(double2* u, long long n, cudaStream_t st) {
 }
 
 int stencil_parts(const StencilArgs& a) {
-  const long long n = (long long)a.nx * a.ny * a.nz;
-  long long parts = (n + ST * 8 - 1) / (ST * 8);
-  const long long cap = (4LL * 152 + a.nrhs - 1) / a.nrhs;
-  if (parts > cap) parts = cap;
-  return parts < 1 ? 1 : (int)parts;
+  const long long nxy = (long long)a.nx * a.ny;
+  const long long gx = (nxy + (long long)ST * SEPT - 1) / ((long long)ST * SEPT);
+  return (int)(gx * a.nz);
 }
 
 void stencil_residual(const StencilArgs& a, const double2* f, const double2* u, double2* rho,
-                      double* partial, int nparts, cudaStream_t st) {
-  dim3 grid(nparts, a.nrhs);
-  stencil_kernel<<<grid, ST, 0, st>>>(a, f, u, rho, partial);
-  count_launch();
+                      double* partial, int fnorm, cudaStream_t st) {
+  const long long nxy = (long long)a.nx * a.ny;
+  const unsigned gx = (unsigned)((nxy + (long long)ST * SEPT - 1) / ((long long)ST * SEPT));
+  const int planes = a.nrhs * a.nz;
+  for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
+    dim3 grid(gx, std::min(65535, planes - rk0));
+    stencil_kernel<<<grid, ST, 0, st>>>(a, f, u, rho, partial, fnorm, rk0);
+    count_launch();
+  }
 }
 
 void finish_norms(const double* partial, int nparts, int nrhs, double* out, cudaStream_t st) {
-  finish_norms_kernel<<<nrhs, 32, 0, st>>>(partial, nparts, out);
+  finish_norms_kernel<<<nrhs, ST, 0, st>>>(partial, nparts, out);
   count_launch();
 }
 

@@ -83,6 +83,8 @@ struct TCSet {
   float* d_tab = nullptr;
 };
 size_t xform_tc_smem(int nt_max);
+// Set the tensor-core kernel's shared-memory limit on the current device (before any capture).
+void xform_tc_prepare();
 // Host: append the TF32 hi/lo K-major tables of one block (complex table B, n x n row-major,
 // B[a][c]) and its output tiles.
 void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
@@ -115,33 +117,42 @@ struct ZFactors {
 };
 
 struct ZSolveArgs {
-  const double2* rhs = nullptr;   // mode-layout right-hand side [r][k][i][j] (pass A/B)
+  const double2* rhs = nullptr;   // mode-layout right-hand side [r][k][i][j]
   double2* out = nullptr;         // mode-layout result [r][k][i][j]
   const double2* P = nullptr;
   const double2* Q = nullptr;
   const double2* cm = nullptr;
-  const signed char* skip_i = nullptr;   // 1 at x-interface positions (block passes)
+  const signed char* skip_i = nullptr;   // 1 at x-interface positions (NULL: sweep every mode)
   const signed char* skip_j = nullptr;
   int nx = 0, ny = 0, nz = 0, nrhs = 0;
   int real_cm = 0;
-  // pass B: boundary right-hand side sigma_k (cxl aX[pl] + cxr aX[pr] + cyl aY[ql] + cyr aY[qr])
-  const double* sig = nullptr;           // [k]
+};
+void zsolve(const ZSolveArgs& a, cudaStream_t st);
+
+// Step 6 boundary term g~ / M_z added in place to the block right-hand side f~:
+// sigma_k (cxl aX[pl] + cxr aX[pr] + cyl aY[ql] + cyr aY[qr]).
+struct BoundaryArgs {
+  int nx = 0, ny = 0, nz = 0, nrhs = 0, nIx = 0, nIy = 0;
+  const signed char* skip_i = nullptr; const signed char* skip_j = nullptr;
+  const double* sig = nullptr;           // [k] or NULL
   const double2* alphaX = nullptr;       // [r][k][nIx][ny]
   const double2* alphaY = nullptr;       // [r][k][nIy][nx]
   const int* gxl = nullptr; const int* gxr = nullptr;     // per i: interface index or -1
   const int* gyl = nullptr; const int* gyr = nullptr;     // per j
   const double2* cxl = nullptr; const double2* cxr = nullptr;   // per i
   const double2* cyl = nullptr; const double2* cyr = nullptr;   // per j
-  // global pass: rhs = sum_p WgxI[p][i] aX[r][k][p][j] + sum_q WgyI[q][j] bY[r][k][q][i]
+};
+void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st);
+
+// Step 5 global right-hand side: out = sum_p WgxI[p][i] aX[r][k][p][j] + sum_q WgyI[q][j] bY[r][k][q][i].
+struct GlobalRhsArgs {
+  int nx = 0, ny = 0, nz = 0, nrhs = 0, nIx = 0, nIy = 0;
   const double2* aX = nullptr;           // [r][k][nIx][ny]
   const double2* bY = nullptr;           // [r][k][nIy][nx]
   const double2* WgxI = nullptr;         // [nIx][nx]
   const double2* WgyI = nullptr;         // [nIy][ny]
-  int nIx = 0, nIy = 0;
 };
-
-enum ZMode { Z_PASS_A = 0, Z_PASS_B = 1, Z_GLOBAL = 2 };
-void zsolve(int mode, const ZSolveArgs& a, cudaStream_t st);
+void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
 
 // Elimination factors of (Tz + s_ij S_z) for every (i, j) with s_ij = lamx[i] + lamy[j]
 // (no pivoting).  fold (may be NULL) scales P by fold[k] (the M_z of the right-hand side).
@@ -190,9 +201,17 @@ struct StencilArgs {
   const double2* tzs = nullptr;   // [nz][3]: row k of Tz / mz_k
   const double* sig = nullptr;    // [nz]
   const double2* mx = nullptr; const double2* my = nullptr; const double2* mz = nullptr;
+  // precomputed by the plan for the residual kernel
+  const double2* cxy = nullptr;   // [ny][nx]: kxs[i][1] + kys[j][1]
+  const double* w2xy = nullptr;   // [ny][nx]: |mx_i|^2 |my_j|^2
+  const double* w2z = nullptr;    // [nz]: |mz_k|^2
+  const signed char* rx = nullptr; const signed char* ry = nullptr; const signed char* rz = nullptr;
+                                  // 1 where the off-diagonal coefficients of that row are real
 };
+// rho = f - M^{-1} A u (rho may be NULL) and per-RHS partial sums of |M rho|^2 (and of
+// |M f|^2 when fnorm != 0); partial holds stencil_parts(a) * nrhs pairs.
 void stencil_residual(const StencilArgs& a, const double2* f, const double2* u, double2* rho,
-                      double* partial, int nparts, cudaStream_t st);
+                      double* partial, int fnorm, cudaStream_t st);
 int stencil_parts(const StencilArgs& a);   // number of partial sums per RHS
 void finish_norms(const double* partial, int nparts, int nrhs, double* out, cudaStream_t st);
 

@@ -5,8 +5,8 @@
 // eigenvector matrix: forward W^T M (Eq. (fdmtrprjfr)), inverse W, or the
 // global W of Eq. (fdmtrprjfrerr).  A launch treats the rows of all planes as
 // one list; one CTA computes a 64 x 16 output tile of one block (64 rows,
-// 16 eigen-columns), staging a 64 x 16 data tile and a 16 x 16 table tile in
-// shared memory per 16-deep slice of the contraction.  Sixteen-column tiles
+// 16 eigen-columns; 16 x 16 for short launches), staging the data tile and a
+// 16 x 16 table tile in shared memory per 16-deep slice of the contraction.  Sixteen-column tiles
 // keep the padding waste small for the block widths of layered grids
 // (79, 80, 95, 96, 32, ...), where it would otherwise cost idle FMAs.
 //
@@ -21,16 +21,18 @@
 namespace hz {
 namespace {
 
-constexpr int TM = 64, TN = 16, TK = 16, NT = 256;
+constexpr int TN = 16, TK = 16, NT = 256;
 static_assert(TN == 16, "host tiling (kTileN) assumes 16-column tiles");
 
-template <typename Acc, bool REAL>
+template <typename Acc, bool REAL, int TM>
 struct Tile {
   Acc a[(REAL || sizeof(Acc) == 4) ? 2 : 3][TK][TM];
   Acc b[REAL ? 1 : (sizeof(Acc) == 8 ? 3 : 2)][TK][TN];
 };
 
-template <typename Acc, bool REAL>
+// TM = 64 rows per CTA (4 per thread) for the bulk transforms; TM = 16 (1 per thread)
+// for the short interface-row launches, which would otherwise leave SMs idle.
+template <typename Acc, bool REAL, int TM>
 __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2* __restrict__ out,
                                          const Acc* __restrict__ tab, const XBlock& b, const XTile& t,
                                          long long nrows, int rows_per_plane, int ncols, long long row0,
@@ -38,26 +40,28 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
                                          const signed char* __restrict__ rowskip, char* smem_raw) {
   constexpr bool F64 = sizeof(Acc) == 8;
   constexpr int NB = REAL ? 1 : (F64 ? 3 : 2);
-  Tile<Acc, REAL>& sm = *reinterpret_cast<Tile<Acc, REAL>*>(smem_raw);
+  constexpr int RPT = TM / 16;                             // rows per thread
+  constexpr int EPT = TM * TK / NT;                        // A elements loaded per thread
+  Tile<Acc, REAL, TM>& sm = *reinterpret_cast<Tile<Acc, REAL, TM>*>(smem_raw);
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
   const int n = b.size;
 
   // accumulators: [row r][component]; complex FP64 3M: P1, P2, P3; otherwise re, im
-  Acc acc[4][3];
+  Acc acc[RPT][3];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RPT; ++r)
 #pragma unroll
     for (int q = 0; q < 3; ++q) acc[r][q] = Acc(0);
 
-  const int la_row = tid >> 2, la_k = (tid & 3) * 4;       // A tile loader: 4 consecutive k
+  const int la_row = tid / (TK / EPT), la_k = (tid % (TK / EPT)) * EPT;   // A loader: EPT consecutive k
   const int lb_k = tid >> 4, lb_c = tid & 15;              // B tile loader
   const long long arow = row0 + la_row;
   const bool arow_ok = arow < nrows;
   const double2* __restrict__ ain = in + arow * (long long)ncols + b.start;
   for (int k0 = 0; k0 < n; k0 += TK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       const int kk = la_k + e;
       double2 v = make_double2(0.0, 0.0);
       if (arow_ok && k0 + kk < n) v = ain[k0 + kk];
@@ -78,7 +82,7 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
       const Acc b0 = sm.b[0][kk][tx];
       if (REAL) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RPT; ++r) {
           acc[r][0] = fma(sm.a[0][kk][ty + 16 * r], b0, acc[r][0]);
           acc[r][1] = fma(sm.a[1][kk][ty + 16 * r], b0, acc[r][1]);
         }
@@ -86,7 +90,7 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
         const Acc b1 = sm.b[NB > 1 ? 1 : 0][kk][tx];
         const Acc b2 = sm.b[NB > 2 ? 2 : 0][kk][tx];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RPT; ++r) {
           acc[r][0] = fma(b0, sm.a[(REAL || !F64) ? 1 : 2][kk][ty + 16 * r], acc[r][0]);   // c (ar + ai)
           acc[r][1] = fma(b1, sm.a[0][kk][ty + 16 * r], acc[r][1]);                        // (d - c) ar
           acc[r][2] = fma(b2, sm.a[1][kk][ty + 16 * r], acc[r][2]);                        // (c + d) ai
@@ -94,7 +98,7 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
       } else {
         const Acc bi = sm.b[NB > 1 ? 1 : 0][kk][tx];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RPT; ++r) {
           const Acc ar = sm.a[0][kk][ty + 16 * r], ai = sm.a[1][kk][ty + 16 * r];
           acc[r][0] = fma(ar, b0, acc[r][0]);
           acc[r][0] = fma(-ai, bi, acc[r][0]);
@@ -106,9 +110,9 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
     __syncthreads();
   }
 
-  double2 res[4];
+  double2 res[RPT];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RPT; ++r) {
     double re, im;
     if (REAL || !F64) {
       re = double(acc[r][0]);
@@ -123,7 +127,7 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
   if (!trans) {
     if (tx >= t.cw) return;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RPT; ++r) {
       const long long row = row0 + ty + 16 * r;
       if (row >= nrows) continue;
       if (rowskip && rowskip[row % rows_per_plane]) continue;
@@ -141,7 +145,7 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
     // stage the tile and write it transposed: out[plane][col][row], rows contiguous
     double2 (*os)[TM + 1] = reinterpret_cast<double2 (*)[TM + 1]>(smem_raw);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) os[tx][ty + 16 * r] = res[r];
+    for (int r = 0; r < RPT; ++r) os[tx][ty + 16 * r] = res[r];
     __syncthreads();
     const int wr = tid & (TM - 1);
     const long long row = row0 + wr;
@@ -168,25 +172,28 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
   }
 }
 
-template <typename Acc>
+template <typename Acc, int TM>
 __global__ void __launch_bounds__(NT)
 xform_kernel(const double2* __restrict__ in, double2* __restrict__ out, const Acc* __restrict__ tab,
-             const XBlock* __restrict__ blocks, const XTile* __restrict__ tiles, long long nrows,
+             const XBlock* __restrict__ blocks, const XTile* __restrict__ tiles, int ntiles, long long nrows,
              int rows_per_plane, int ncols, int trans, int store, int conj_out,
              const signed char* __restrict__ rowskip) {
-  constexpr int SA = sizeof(Tile<Acc, false>) > sizeof(double2) * TN * (TM + 1)
-                         ? sizeof(Tile<Acc, false>) : sizeof(double2) * TN * (TM + 1);
+  constexpr int SA = sizeof(Tile<Acc, false, TM>) > sizeof(double2) * TN * (TM + 1)
+                         ? sizeof(Tile<Acc, false, TM>) : sizeof(double2) * TN * (TM + 1);
   __shared__ __align__(16) char smem[SA];
-  const XTile t = tiles[blockIdx.y];
+  // column tiles of one row tile are consecutive CTAs, so the row tile is read from
+  // DRAM once and re-read from L2 by the other column tiles
+  const long long cta = blockIdx.x;
+  const XTile t = tiles[cta % ntiles];
   const XBlock b = blocks[t.blk];
-  const long long row0 = (long long)blockIdx.x * TM;
+  const long long row0 = (cta / ntiles) * TM;
   const Acc* tb = tab + (sizeof(Acc) == 8 ? b.toff : b.toff32);
   if (b.real)
-    run_tile<Acc, true>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out,
-                        rowskip, smem);
+    run_tile<Acc, true, TM>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out,
+                            rowskip, smem);
   else
-    run_tile<Acc, false>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out,
-                         rowskip, smem);
+    run_tile<Acc, false, TM>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out,
+                             rowskip, smem);
 }
 
 template <typename Acc>
@@ -195,9 +202,17 @@ void launch(const XformSet& xs, const Acc* tab, const double2* in, double2* out,
             cudaStream_t st) {
   const long long nrows = nplanes * (long long)rows_per_plane;
   if (nrows <= 0 || xs.ntiles == 0) return;
-  dim3 grid((unsigned)((nrows + TM - 1) / TM), xs.ntiles);
-  xform_kernel<Acc><<<grid, NT, 0, st>>>(in, out, tab, xs.d_blocks, xs.d_tiles, nrows, rows_per_plane,
-                                        xs.ncols, trans, store, conj_out, rowskip);
+  if (((nrows + 63) / 64) * xs.ntiles >= 2 * 152) {
+    const long long ctas = ((nrows + 63) / 64) * xs.ntiles;
+    xform_kernel<Acc, 64><<<(unsigned)ctas, NT, 0, st>>>(in, out, tab, xs.d_blocks, xs.d_tiles, xs.ntiles,
+                                                          nrows, rows_per_plane, xs.ncols, trans, store,
+                                                          conj_out, rowskip);
+  } else {
+    const long long ctas = ((nrows + 15) / 16) * xs.ntiles;
+    xform_kernel<Acc, 16><<<(unsigned)ctas, NT, 0, st>>>(in, out, tab, xs.d_blocks, xs.d_tiles, xs.ntiles,
+                                                          nrows, rows_per_plane, xs.ncols, trans, store,
+                                                          conj_out, rowskip);
+  }
   count_launch();
 }
 

@@ -12,15 +12,16 @@
 // lo = tf32(x - hi)), which keeps the result at FP32 accuracy; FP64 iterative
 // refinement of the solve removes the rest.
 //
-// One CTA (4 warps) computes a 128-row x Nt-column tile (Nt <= 256, a multiple of
+// One CTA (16 warps) computes a 128-row x Nt-column tile (Nt <= 256, a multiple of
 // 16) of one block.  The contraction runs in chunks of 32 real K (128 bytes per
 // operand row): all threads convert the FP64 data rows to TF32 hi/lo and store
 // them, with the tables' hi/lo rows, in shared memory in the K-major
 // 128-byte-swizzled layout; one thread issues the 12 MMAs of the chunk and
 // commits them to the chunk's mbarrier; two chunk buffers alternate, so the
 // conversion of chunk c+1 overlaps the MMAs of chunk c.  The epilogue reads
-// the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile
-// rows), converts to FP64 and stores (transposed or not, optionally adding).
+// the accumulator with tcgen05.ld (warp w reads TMEM lanes 32(w%4)..+31 = tile rows,
+// column chunks w/4, w/4+4, ...), converts to FP64 and stores (transposed or not,
+// optionally adding).
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <algorithm>
@@ -34,11 +35,12 @@ namespace hz {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 512;          // 16 warps: 4 per SM sub-partition to hide latency
 constexpr int KCH = 32;                  // real K per chunk (128 bytes of tf32 per row)
 constexpr int ROWB = 128;                // bytes per operand row in a chunk
 constexpr int A_BYTES = TC_M * ROWB;     // one A plane (hi or lo) of a chunk
 constexpr int TMEM_COLS = 256;
+constexpr int kTcMaxN = 160;             // widest output tile (smem: 64 + 64 + 4 x 160 x 128 B)
 constexpr long long WAIT_NS = 2000000000LL;   // 2 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -123,25 +125,73 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  // 16-byte global -> shared copy; zero fill when !valid (src must still be a valid address)
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory plan of one CTA (offsets from a 1024-byte aligned base):
+//   raw[2]   : FP64 data chunks as loaded, 128 rows x 16 complex (32 KB each)
+//   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 16 KB each), 128B-swizzled
+//   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 128 B each), 128B-swizzled
+//   bars     : MMA-completion mbarriers of the two operand stages, TMEM address slot
+// The chunk pipeline: the FP64 rows of chunk c+2 and the table rows of chunk c+1 are in
+// flight (cp.async) while chunk c is converted and its MMAs run.
+constexpr int RAW_BYTES = TC_M * 256;
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
 xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const float* __restrict__ tabs,
-                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, long long nrows,
-                int rows_per_plane, int ncols, int trans, int store, const signed char* __restrict__ rowskip,
-                int* __restrict__ err) {
+                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, int ntiles,
+                long long nrows, int rows_per_plane, int ncols, int trans, int store,
+                const signed char* __restrict__ rowskip, int* __restrict__ err) {
   extern __shared__ uint8_t smem_dyn[];
-  // 1024-byte alignment for the swizzled operand buffers
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  const TCTile t = tiles[blockIdx.y];
+  // column tiles of one row tile are consecutive CTAs (the data rows come from L2 the second time)
+  const TCTile t = tiles[blockIdx.x % ntiles];
   const TCBlock b = blocks[t.blk];
-  const int nt = t.nt;                                     // tile width in real columns
-  const int B_BYTES = nt * ROWB;
-  const int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+  const long long row0 = (long long)(blockIdx.x / ntiles) * TC_M;
+  const int nt = t.nt;
+  const int B_BYTES = nt * ROWB;                           // one table plane of a chunk
+  const uint32_t s_base = smem_u32(smem);
+  const uint32_t raw0 = s_base, aop0 = raw0 + 2 * RAW_BYTES, bop0 = aop0 + 2 * 2 * A_BYTES;
+  const uint32_t BSTAGE = 2 * B_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * RAW_BYTES + 4 * A_BYTES + 2 * BSTAGE);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long row0 = (long long)blockIdx.x * TC_M;
-  const int n = b.size;                                    // complex width of the block
+  const int n = b.size;
   const int nk = b.kpad / KCH;
+  const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
+  const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
+
+  // issue the FP64 rows of chunk c (16 complex per row) into raw[c & 1]
+  auto load_raw = [&](int c) {
+    const uint32_t dst = raw0 + (c & 1) * RAW_BYTES;
+#pragma unroll
+    for (int q = 0; q < 2048 / TC_THREADS; ++q) {
+      const int task = tid + TC_THREADS * q;               // 2048 tasks: row = task / 16, complex = task % 16
+      const int r = task >> 4, cc = task & 15;
+      const long long grow = row0 + r;
+      const int col = c * (KCH / 2) + cc;
+      const bool ok = grow < nrows && col < n;
+      const double2* src = ok ? in + grow * (long long)ncols + b.start + col : in;
+      cp_async16(dst + r * 256 + cc * 16, src, ok);
+    }
+  };
+  // issue the table rows (hi and lo) of chunk c into bop[c & 1], 128B-swizzled
+  auto load_b = [&](int c) {
+    const uint32_t bh = bop0 + (c & 1) * BSTAGE, bl = bh + B_BYTES;
+    for (int task = tid; task < nt * 8; task += TC_THREADS) {
+      const int r = task >> 3, cc = task & 7;
+      const long long go = (long long)r * b.kpad + c * KCH + 4 * cc;
+      const uint32_t off = r * ROWB + ((cc ^ (r & 7)) << 4);
+      cp_async16(bh + off, thi + go, true);
+      cp_async16(bl + off, tlo + go, true);
+    }
+  };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -153,70 +203,61 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
     mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // prologue: groups {A0}, {B0}, {A1}
+  load_raw(0);
+  cp_async_commit();
+  load_b(0);
+  cp_async_commit();
+  if (nk > 1) load_raw(1);
+  cp_async_commit();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = idesc_tf32(nt);
-  const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
-  const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
   bool ok = true;
-  int issued = 0;                                          // chunks whose MMAs were committed
+  int issued = 0;
 
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
-    uint8_t* st = smem + s * STAGE;
-    if (kc >= 2) {                                         // MMAs of chunk kc-2 done with this buffer
+    // operand stage s was read by the MMAs of chunk kc-2
+    if (kc >= 2) {
       const int w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
-      if (!__syncthreads_and(w)) {
-        ok = false;
-        break;
-      }
+      if (!__syncthreads_and(w)) { ok = false; break; }
     }
-    // A: 128 rows x 8 chunks of 16 bytes (two complex values), hi and lo planes
-    const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_BYTES;
-#pragma unroll 2
-    for (int q = 0; q < 8; ++q) {
-      const int task = tid + TC_THREADS * q;
-      const int r = task >> 3, c = task & 7;
-      const long long grow = row0 + r;
-      const int col = kc * (KCH / 2) + 2 * c;              // complex column within the block
-      double2 v0 = make_double2(0.0, 0.0), v1 = v0;
-      if (grow < nrows) {
-        const double2* src = in + grow * (long long)ncols + b.start + col;
-        if (col < n) v0 = src[0];
-        if (col + 1 < n) v1 = src[1];
-      }
-      const float f[4] = {(float)v0.x, (float)v0.y, (float)v1.x, (float)v1.y};
-      uint32_t h[4], l[4];
+    cp_async_wait<1>();                                     // raw A(kc) and B(kc) have landed
+    __syncthreads();
+    // convert raw[s] -> TF32 hi/lo operand planes of stage s
+    {
+      const uint32_t rsrc = raw0 + s * RAW_BYTES;
+      const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        h[e] = to_tf32(f[e]);
-        l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
+      for (int q = 0; q < 1024 / TC_THREADS; ++q) {
+        const int task = tid + TC_THREADS * q;             // 1024 tasks: row = task / 8, pair = task % 8
+        const int r = task >> 3, c = task & 7;
+        double x0, x1, x2, x3;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * 256 + c * 32));
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * 256 + c * 32 + 16));
+        const float f[4] = {(float)x0, (float)x1, (float)x2, (float)x3};
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          h[e] = to_tf32(f[e]);
+          l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
+        }
+        const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
+        st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
+        st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
-      const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
-      st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
-      st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
-    }
-    // B: nt rows x 8 chunks, hi and lo tables (already tf32 in global memory)
-    const uint32_t b_hi = a_lo + A_BYTES, b_lo = b_hi + B_BYTES;
-    for (int task = tid; task < nt * 8; task += TC_THREADS) {
-      const int r = task >> 3, c = task & 7;
-      const long long go = (long long)r * b.kpad + kc * KCH + 4 * c;
-      const float4 vh = *reinterpret_cast<const float4*>(thi + go);
-      const float4 vl = *reinterpret_cast<const float4*>(tlo + go);
-      const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
-      st_shared_v4(b_hi + off, __float_as_uint(vh.x), __float_as_uint(vh.y), __float_as_uint(vh.z),
-                   __float_as_uint(vh.w));
-      st_shared_v4(b_lo + off, __float_as_uint(vl.x), __float_as_uint(vl.y), __float_as_uint(vl.z),
-                   __float_as_uint(vl.w));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    __syncthreads();                                        // raw[s] free, operands of kc ready
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
+      const uint32_t b_hi = bop0 + s * BSTAGE, b_lo = b_hi + B_BYTES;
 #pragma unroll
-      for (int ks = 0; ks < KCH / 8; ++ks) {                 // 8 tf32 = 32 bytes per MMA
+      for (int ks = 0; ks < KCH / 8; ++ks) {               // 8 tf32 = 32 bytes per MMA
         const uint32_t koff = ks * 32;
         const uint64_t dah = smem_desc_sw128(a_hi + koff), dal = smem_desc_sw128(a_lo + koff);
         const uint64_t dbh = smem_desc_sw128(b_hi + koff), dbl = smem_desc_sw128(b_lo + koff);
@@ -228,9 +269,19 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       mma_commit(&bars[s]);
     }
     issued = kc + 1;
+    // next loads: B(kc+1) into stage (kc+1)&1 once the MMAs of chunk kc-1 are done, then A(kc+2)
+    if (kc + 1 < nk) {
+      if (kc >= 1) {
+        const int w = mbar_wait(&bars[(kc + 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
+        if (!__syncthreads_and(w)) { ok = false; break; }
+      }
+      load_b(kc + 1);
+    }
+    cp_async_commit();
+    if (kc + 2 < nk) load_raw(kc + 2);
+    cp_async_commit();
   }
-  // The last commit covers every earlier MMA of this thread; wait for it (bounded) even
-  // after a failed wait, so no MMA is in flight when the tensor memory is freed.
+  cp_async_wait<0>();                                       // no copy left in flight
   if (issued > 0) {
     const int last = issued - 1;
     if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) ok = false;
@@ -238,7 +289,9 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int all_ok = __syncthreads_and(ok ? 1 : 0);
   if (all_ok) {
-    const int r = warp * 32 + lane;
+    const int lw = warp & 3, cgrp = warp >> 2;             // TMEM lane quarter, column group
+    constexpr int NGRP = TC_THREADS / 128;
+    const int r = lw * 32 + lane;
     const long long grow = row0 + r;
     long long plane = 0;
     int rip = 0;
@@ -248,8 +301,8 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       rip = (int)(grow - plane * rows_per_plane);
       if (rowskip && rowskip[rip]) row_ok = false;
     }
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c16 = 0; c16 < nt; c16 += 16) {
+    const uint32_t tl = tmem + ((uint32_t)(lw * 32) << 16);
+    for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
       float v[16];
       tmem_ld16(tl + c16, v);
       if (!row_ok) continue;
@@ -313,28 +366,43 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
           lo[o] = tf32_round_host(e[u][w] - (double)h);
         }
     }
-  for (int n0 = 0; n0 < blk.npad; n0 += 256) tiles.push_back(TCTile{blk_index, n0, std::min(256, blk.npad - n0), 0});
+  const int ntl = (blk.npad + kTcMaxN - 1) / kTcMaxN;     // tiles of at most kTcMaxN columns
+  const int units = blk.npad / 16;
+  int n0 = 0;
+  for (int q = 0; q < ntl; ++q) {
+    const int w = 16 * ((units * (q + 1)) / ntl - (units * q) / ntl);
+    tiles.push_back(TCTile{blk_index, n0, w, 0});
+    n0 += w;
+  }
 }
 
-size_t xform_tc_smem(int nt_max) { return 1024 + 2 * (2 * A_BYTES + 2 * nt_max * ROWB) + 64; }
+size_t xform_tc_smem(int nt_max) {
+  return 1024 + 2 * RAW_BYTES + 4 * A_BYTES + 4 * (size_t)nt_max * ROWB + 64;
+}
 
 uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }
+
+void xform_tc_prepare() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool attr_set[64] = {};
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    // the largest tile any plan uses, so every launch fits
+    cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)xform_tc_smem(kTcMaxN));
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+}
 
 void xform_tc(const TCSet& ts, const double2* in, double2* out, int rows_per_plane, long long nplanes,
               int trans, int store, const signed char* rowskip, int* err, cudaStream_t st) {
   const long long nrows = nplanes * (long long)rows_per_plane;
   if (nrows <= 0 || ts.ntiles == 0) return;
-  const size_t smem = xform_tc_smem(ts.nt_max);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static bool attr_set[64] = {};
-  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (dev >= 0 && dev < 64) attr_set[dev] = true;
-  }
-  dim3 grid((unsigned)((nrows + TC_M - 1) / TC_M), ts.ntiles);
-  xform_tc_kernel<<<grid, TC_THREADS, smem, st>>>(in, out, ts.d_tab, ts.d_blocks, ts.d_tiles, nrows,
-                                                  rows_per_plane, ts.ncols, trans, store, rowskip, err);
+  xform_tc_prepare();
+  const long long ctas = ((nrows + TC_M - 1) / TC_M) * ts.ntiles;
+  xform_tc_kernel<<<(unsigned)ctas, TC_THREADS, xform_tc_smem(ts.nt_max), st>>>(
+      in, out, ts.d_tab, ts.d_blocks, ts.d_tiles, ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store,
+      rowskip, err);
   count_launch();
 }
 

@@ -8,12 +8,18 @@
 // elimination without pivoting); adjacent threads own adjacent modes, so every
 // z step is a coalesced access of the [k][i][j] mode layout.
 //
-// The elimination factors depend only on the mode and the frequency, so they
-// are computed once per plan/frequency (zfactor) and the per-solve sweep is
+// The right-hand sides of the global pass (r~ of step 5) and the boundary term of
+// pass B (g~ of step 6) are rank-|I| outer products of interface data; they are
+// formed by fully parallel kernels (global_rhs, boundary_rhs) so that every sweep
+// is the same plain kernel.  The elimination factors depend only on the mode and
+// the frequency, so they are computed once per plan/frequency (zfactor) and the
+// per-solve sweep is
 //   forward  y_k = (rhs_k - cm_k y_{k-1}) P_k,   back  x_k = y_k - Q_k x_{k+1},
 // with P_k = fold_k / d_k, Q_k = c_{k+1} / d_k, cm_k = c_k / fold_k, d_k the
 // pivots.  The forward results are kept in the output array and overwritten by
 // the back sweep.  FP64 throughout.
+#include <algorithm>
+
 #include "hz_internal.h"
 
 namespace hz {
@@ -31,7 +37,7 @@ __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
   return make_double2(fma(c.x, y.x, fma(-c.y, y.y, acc.x)), fma(c.x, y.y, fma(c.y, y.x, acc.y)));
 }
 
-template <int MODE, bool REALCM>
+template <bool REALCM>
 __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const long long plane = (long long)a.nx * a.ny;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -39,7 +45,7 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const int r = (int)(tid / plane);
   const long long pos = tid - (long long)r * plane;
   const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
-  if (MODE != Z_GLOBAL && (a.skip_i[i] | a.skip_j[j])) return;
+  if (a.skip_i && (a.skip_i[i] | a.skip_j[j])) return;
   const long long rs = plane * a.nz;
   const double2* __restrict__ rhs = a.rhs + r * rs + pos;
   double2* __restrict__ out = a.out + r * rs + pos;
@@ -47,47 +53,10 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const double2* __restrict__ Q = a.Q + pos;
   const double2* __restrict__ cm = a.cm;
 
-  // pass B: boundary coefficients of this mode (sigma_k applied per k)
-  int pl = -1, pr = -1, ql = -1, qr = -1;
-  double2 cxl = {0, 0}, cxr = {0, 0}, cyl = {0, 0}, cyr = {0, 0};
-  if (MODE == Z_PASS_B) {
-    pl = a.gxl[i]; pr = a.gxr[i]; ql = a.gyl[j]; qr = a.gyr[j];
-    if (pl >= 0) cxl = a.cxl[i];
-    if (pr >= 0) cxr = a.cxr[i];
-    if (ql >= 0) cyl = a.cyl[j];
-    if (qr >= 0) cyr = a.cyr[j];
-  }
-
   double2 y = make_double2(0.0, 0.0);
 #pragma unroll 4
   for (int k = 0; k < a.nz; ++k) {
-    double2 b;
-    if (MODE == Z_GLOBAL) {
-      b = make_double2(0.0, 0.0);
-      const long long base = ((long long)r * a.nz + k);
-      for (int p = 0; p < a.nIx; ++p)
-        b = cfma(a.WgxI[(long long)p * a.nx + i], a.aX[(base * a.nIx + p) * a.ny + j], b);
-      for (int q = 0; q < a.nIy; ++q)
-        b = cfma(a.WgyI[(long long)q * a.ny + j], a.bY[(base * a.nIy + q) * a.nx + i], b);
-    } else {
-      b = rhs[k * plane];
-      if (MODE == Z_PASS_B) {
-        const long long base = ((long long)r * a.nz + k);
-        double2 g = make_double2(0.0, 0.0);
-        if (pl >= 0) g = cfma(cxl, a.alphaX[(base * a.nIx + pl) * a.ny + j], g);
-        if (pr >= 0) g = cfma(cxr, a.alphaX[(base * a.nIx + pr) * a.ny + j], g);
-        if (ql >= 0) g = cfma(cyl, a.alphaY[(base * a.nIy + ql) * a.nx + i], g);
-        if (qr >= 0) g = cfma(cyr, a.alphaY[(base * a.nIy + qr) * a.nx + i], g);
-        if (a.sig) {
-          const double s = a.sig[k];
-          b.x = fma(s, g.x, b.x);
-          b.y = fma(s, g.y, b.y);
-        } else {
-          b.x += g.x;
-          b.y += g.y;
-        }
-      }
-    }
+    const double2 b = rhs[k * plane];
     const double2 c = cm[k];
     double2 t;
     if (REALCM)
@@ -104,6 +73,56 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
     x = csub_mul(yk, Q[k * plane], x);
     out[k * plane] = x;
   }
+}
+
+// Step 6 boundary term, added in place to the block mode right-hand side:
+//   ft[r][k][i][j] += sigma_k (cxl[i] aX[r][k][gxl[i]][j] + cxr[i] aX[r][k][gxr[i]][j]
+//                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
+// One thread per element of a plane (blockIdx.y = r * nz + k); interface positions skipped.
+__global__ void __launch_bounds__(256) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
+  const int rk = rk0 + blockIdx.y;
+  const int k = rk % a.nz;
+  const long long plane = (long long)a.nx * a.ny;
+  const long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (pos >= plane) return;
+  const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
+  if (a.skip_i[i] | a.skip_j[j]) return;
+  const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
+  const double2* ax = a.alphaX + (long long)rk * a.nIx * a.ny + j;
+  const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
+  double2 g = make_double2(0.0, 0.0);
+  if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
+  if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
+  if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
+  if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
+  double2* p = ft + (long long)rk * plane + pos;
+  double2 v = *p;
+  if (a.sig) {
+    const double s = a.sig[k];
+    v.x = fma(s, g.x, v.x);
+    v.y = fma(s, g.y, v.y);
+  } else {
+    v.x += g.x;
+    v.y += g.y;
+  }
+  *p = v;
+}
+
+// Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
+//                                              + sum_q Wgy[q][m] bY[r][k][q][l].
+__global__ void __launch_bounds__(256) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
+                                                         int rk0) {
+  const int rk = rk0 + blockIdx.y;
+  const long long plane = (long long)a.nx * a.ny;
+  const long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (pos >= plane) return;
+  const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
+  const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
+  const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
+  double2 b = make_double2(0.0, 0.0);
+  for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
+  for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+  out[(long long)rk * plane + pos] = b;
 }
 
 __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
@@ -148,22 +167,34 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
 
 }  // namespace
 
-void zsolve(int mode, const ZSolveArgs& a, cudaStream_t st) {
+void zsolve(const ZSolveArgs& a, cudaStream_t st) {
   const long long n = (long long)a.nx * a.ny * a.nrhs;
   if (n == 0) return;
   const int T = 128;
   const unsigned grid = (unsigned)((n + T - 1) / T);
-  if (mode == Z_PASS_A) {
-    if (a.real_cm) zsolve_kernel<Z_PASS_A, true><<<grid, T, 0, st>>>(a);
-    else zsolve_kernel<Z_PASS_A, false><<<grid, T, 0, st>>>(a);
-  } else if (mode == Z_PASS_B) {
-    if (a.real_cm) zsolve_kernel<Z_PASS_B, true><<<grid, T, 0, st>>>(a);
-    else zsolve_kernel<Z_PASS_B, false><<<grid, T, 0, st>>>(a);
-  } else {
-    if (a.real_cm) zsolve_kernel<Z_GLOBAL, true><<<grid, T, 0, st>>>(a);
-    else zsolve_kernel<Z_GLOBAL, false><<<grid, T, 0, st>>>(a);
-  }
+  if (a.real_cm) zsolve_kernel<true><<<grid, T, 0, st>>>(a);
+  else zsolve_kernel<false><<<grid, T, 0, st>>>(a);
   count_launch();
+}
+
+void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) {
+  const long long plane = (long long)a.nx * a.ny;
+  const int planes = a.nrhs * a.nz;
+  for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
+    dim3 grid((unsigned)((plane + 255) / 256), std::min(65535, planes - rk0));
+    boundary_rhs_kernel<<<grid, 256, 0, st>>>(a, ft, rk0);
+    count_launch();
+  }
+}
+
+void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) {
+  const long long plane = (long long)a.nx * a.ny;
+  const int planes = a.nrhs * a.nz;
+  for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
+    dim3 grid((unsigned)((plane + 255) / 256), std::min(65535, planes - rk0));
+    global_rhs_kernel<<<grid, 256, 0, st>>>(a, out, rk0);
+    count_launch();
+  }
 }
 
 void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,

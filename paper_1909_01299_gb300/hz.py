@@ -72,6 +72,12 @@ SIGNATURES = {
     "hz_get_stage_times": (ctypes.c_int, [_P, _P, _P]),
     "hz_tridiag_eig": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P,
                                       ctypes.POINTER(ctypes.c_double)]),
+    "hz_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "hz_batch_solve": (ctypes.c_int, [_P, _P, _P, _P]),
+    "hz_batch_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hz_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "hz_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -279,6 +285,62 @@ def residual_noalloc(plan: Plan, f, u) -> np.ndarray:
     _check(_lib.hz_residual_noalloc(plan._h, f.data_ptr(), u.data_ptr(), R, out.ctypes.data),
            "hz_residual_noalloc")
     return out
+
+
+class Batch:
+    """hz_batch_*: many (plan, nrhs) solves captured once and replayed as one CUDA graph.
+
+    plans: one Plan per (model, frequency); nrhs: RHS count per plan.  The batch keeps
+    references to the plans so they outlive it.
+    """
+
+    def __init__(self, plans, nrhs, lanes: int = 0):
+        self.plans = list(plans)
+        self.nrhs = [int(r) for r in nrhs]
+        hs = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        rs = (ctypes.c_int * len(self.nrhs))(*self.nrhs)
+        h = _P()
+        _check(_lib.hz_batch_create(len(self.plans), ctypes.cast(hs, _P), ctypes.cast(rs, _P), int(lanes),
+                                    ctypes.byref(h)), "hz_batch_create")
+        self._h = h
+
+    def _ptrs(self, fs, us):
+        for p, f, u, R in zip(self.plans, fs, us, self.nrhs):
+            assert p._check_tensor(f) == R and p._check_tensor(u) == R
+        fa = (ctypes.c_void_p * len(fs))(*[f.data_ptr() for f in fs])
+        ua = (ctypes.c_void_p * len(us))(*[u.data_ptr() for u in us])
+        return fa, ua
+
+    def solve(self, fs, us) -> np.ndarray:
+        """u_i = A_i^{-1} M f_i for every item; returns each item's max relative residual."""
+        fa, ua = self._ptrs(fs, us)
+        rel = np.empty(len(fs), np.float64)
+        _check(_lib.hz_batch_solve(self._h, ctypes.cast(fa, _P), ctypes.cast(ua, _P), rel.ctypes.data),
+               "hz_batch_solve")
+        return rel
+
+    def autotune(self, fs, us) -> int:
+        fa, ua = self._ptrs(fs, us)
+        lanes = ctypes.c_int()
+        _check(_lib.hz_batch_autotune(self._h, ctypes.cast(fa, _P), ctypes.cast(ua, _P), ctypes.byref(lanes)),
+               "hz_batch_autotune")
+        return lanes.value
+
+    def info(self) -> dict:
+        ms, n, lanes = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_int()
+        _check(_lib.hz_batch_info(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(lanes)), "hz_batch_info")
+        return {"last_ms": ms.value, "launches_per_replay": n.value, "lanes": lanes.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hz_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dual_weights(plan: Plan):

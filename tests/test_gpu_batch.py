@@ -1,0 +1,81 @@
+"""Batched solves (one CUDA graph over uneven models, frequencies and RHS counts)
+against the CPU oracle and against the single-plan path (needs a GB300)."""
+import numpy as np
+import pytest
+
+from oracle import hz_oracle as O
+from paper_1909_01299_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01299_gb300 import build
+    build.build()
+    from paper_1909_01299_gb300 import hz
+    return torch, hz
+
+
+def small_batch():
+    """Six uneven items: three models x two frequencies, mixed and FP64 plans, 1-3 RHS."""
+    models = [W.tiny_pml(24, 20, 14, 2, 2, rim=3, pml=2, nrhs=3, seed=1),
+              W.tiny_pml(31, 27, 18, 2, 3, rim=4, pml=2, nrhs=2, seed=2),
+              W.tiny_pml(17, 22, 11, 1, 2, rim=3, pml=1, nrhs=1, seed=3)]
+    items = []
+    for mi, w in enumerate(models):
+        for om, prec in ((0.8, "mixed"), (1.3, "fp64" if mi == 1 else "mixed")):
+            items.append((w, om, prec))
+    return items
+
+
+def test_batch_matches_oracle_and_single_solves(env):
+    torch, hz = env
+    items = small_batch()
+    plans, fs, us, refs = [], [], [], []
+    for w, om, prec in items:
+        p = hz.Plan.from_workload(w, precision=prec)
+        p.set_frequency(om)
+        plans.append(p)
+        fs.append(torch.from_numpy(w.f).cuda())
+        us.append(torch.zeros_like(fs[-1]))
+        refs.append(O.solve(O.Problem.from_workload(w, k2=w.k2 * om * om), w.f))
+    batch = hz.Batch(plans, [w.f.shape[0] for w, _, _ in items], lanes=2)
+    for call in range(2):                                   # capture, then replay
+        for u in us:
+            u.zero_()
+        rel = batch.solve(fs, us)
+        for (w, om, prec), u, ref, r in zip(items, us, refs, rel):
+            tol = 1e-8 if prec == "mixed" else 1e-10
+            err = np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref)
+            assert err < tol, (call, prec, err)
+            assert r <= (1e-8 if prec == "mixed" else 1e-10)
+    info = batch.info()
+    assert info["launches_per_replay"] > 0 and info["lanes"] == 2
+    # the same items one by one through hz_solve
+    for p, f, u in zip(plans, fs, us):
+        single = p.solve(f)
+        assert torch.allclose(single, u, rtol=0, atol=1e-9 * float(u.abs().max()))
+    batch.close()
+
+
+def test_batch_autotune_picks_a_lane_count(env):
+    torch, hz = env
+    items = small_batch()[:4]
+    plans = []
+    fs, us = [], []
+    for w, om, prec in items:
+        p = hz.Plan.from_workload(w, precision=prec)
+        p.set_frequency(om)
+        plans.append(p)
+        fs.append(torch.from_numpy(w.f).cuda())
+        us.append(torch.zeros_like(fs[-1]))
+    batch = hz.Batch(plans, [w.f.shape[0] for w, _, _ in items])
+    lanes = batch.autotune(fs, us)
+    assert lanes in (1, 2, 4)
+    rel = batch.solve(fs, us)
+    assert np.all(rel <= 1e-8)
+    batch.close()
