@@ -82,6 +82,9 @@ struct hz_plan_s {
   double omega = 1.0;
   bool need_global = false;
   bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
+  // second stream for the y-side interface work (runs beside the x side)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int real_cm = 1;
   AxisDev dx, dy;
   // z tables
@@ -623,6 +626,17 @@ hz::IfaceArgs iface_args(hz_plan_t p, int R) {
   return a;
 }
 
+// The x-side and y-side interface chains are independent: the y side runs on the
+// plan's second stream between fork() and join().
+void fork(hz_plan_t p, cudaStream_t st) {
+  ck(cudaEventRecord(p->ev_fork, st));
+  ck(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+}
+void join(hz_plan_t p, cudaStream_t st) {
+  ck(cudaEventRecord(p->ev_join, p->side));
+  ck(cudaStreamWaitEvent(st, p->ev_join, 0));
+}
+
 // One pass of steps 1-7: u (=|+=) S(f).  lo = FP32 bulk transforms (mixed path).
 void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* u, int R, bool lo,
                 int store, int conj_out) {
@@ -663,14 +677,17 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   if (nIx + nIy > 0) {
     // Step 3: v at the nodes next to the interfaces
     std::unique_ptr<Stage> t3(new Stage(p, st, HZ_STAGE_EDGES));
+    const cudaStream_t sy = p->side;
+    fork(p, st);
     if (nIx) {
       hz::contract_rows(w.V, w.cX, p->dx.edge_coef, p->dx.edge_rng, nx, ny, 2 * nIx, planes, st);
       hz::xform_f64(p->dy.inv, w.cX, w.vX, (int)(2 * nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     if (nIy) {
-      hz::contract_cols(w.V, w.cY, p->dy.edge_coef, p->dy.edge_rng, nx, ny, 2 * nIy, planes, st);
-      hz::xform_f64(p->dx.inv, w.cY, w.vY, (int)(2 * nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::contract_cols(w.V, w.cY, p->dy.edge_coef, p->dy.edge_rng, nx, ny, 2 * nIy, planes, sy);
+      hz::xform_f64(p->dx.inv, w.cY, w.vY, (int)(2 * nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
     }
+    join(p, st);
     t3.reset();
     // Step 4: r = M f - A v on the interfaces
     hz::IfaceArgs ia = iface_args(p, R);
@@ -680,8 +697,10 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     }
     // Step 5: w on the interfaces through the whole-axis eigenbasis
     std::unique_ptr<Stage> t5(new Stage(p, st, HZ_STAGE_GLOBAL));
+    fork(p, st);
     if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
-    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
+    join(p, st);
     hz::GlobalRhsArgs ga;
     ga.nx = nx; ga.ny = ny; ga.nz = nz; ga.nrhs = R; ga.nIx = nIx; ga.nIy = nIy;
     ga.aX = w.aX; ga.bY = w.bY; ga.WgxI = p->dx.gcoef; ga.WgyI = p->dy.gcoef;
@@ -691,6 +710,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     zg.rhs = w.G; zg.out = w.V;                     // w~ (v~ in V is no longer needed)
     zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
     hz::zsolve(zg, st);
+    fork(p, st);
     if (nIx) {
       hz::contract_rows(w.V, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
       hz::xform_f64(p->dy.ginv, w.cg, w.wX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
@@ -698,10 +718,11 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
       hz::xform_f64(p->dy.fwd, w.wX, w.alX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
     }
     if (nIy) {
-      hz::contract_cols(w.V, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, st);
-      hz::xform_f64(p->dx.ginv, w.dg, w.wY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
-      hz::xform_f64(p->dx.fwd, w.wY, w.alY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      hz::contract_cols(w.V, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, sy);
+      hz::xform_f64(p->dx.ginv, w.dg, w.wY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
+      hz::xform_f64(p->dx.fwd, w.wY, w.alY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
     }
+    join(p, st);
     t5.reset();
     // Step 6: pass B, (Tz + s S_z) u~ = M_z f~ + g~ with g~ formed from the interface data
     Stage t6(p, st, HZ_STAGE_PASS_B);
@@ -834,6 +855,11 @@ void release(hz_plan_t p) {
   p->allocs.clear();
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  p->side = nullptr;
+  p->ev_fork = p->ev_join = nullptr;
 }
 
 }  // namespace
@@ -1084,6 +1110,7 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   }
   const int nbx = blocks ? blocks->nbx : 1, nby = blocks ? blocks->nby : 1;
   if (nbx < 1 || nby < 1 || nbx > grid->nx || nby > grid->ny) return HZ_ERR_ARG;
+  if ((long long)grid->nx * grid->ny >= (1LL << 31)) return HZ_ERR_ARG;      // in-plane indices are 32-bit
   if (opts && (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED)) return HZ_ERR_ARG;
 
   hz_plan_t p = new (std::nothrow) hz_plan_s();
@@ -1118,6 +1145,9 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   }
   if (s != HZ_OK) { delete p; return s; }
   try {
+    ck(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    ck(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     p->status = dalloc<int>(p, 1);
     p->minpiv = dalloc<unsigned long long>(p, 1);
     build_axis_dev(p, p->ax, p->dx, p->need_global);

@@ -187,9 +187,12 @@ constexpr int SEPT = 4;                    // stencil elements per thread
 
 // r = f - M^{-1} A u with the 7-point operator of Eq. (fd), divided by the weights:
 //   M^{-1} A u = sigma_k (Kx u / mx + Ky u / my) + Tz u / mz.
-// grid (CTAs per plane, nrhs * nz): one plane (r, k) per blockIdx.y, so no index
-// division beyond the in-plane one.  Off-diagonal coefficients that are real (every
-// row whose steps are real) take two FP64 operations instead of four.
+// grid (CTAs per plane, nrhs * nz): one plane (r, k) per blockIdx.y, so the z-row of the
+// operator and the weight |mz_k|^2 are CTA constants.  Every term is one FMA into the
+// accumulator that starts at f (real off-diagonal coefficients -- rows whose steps are
+// real -- take two FP64 operations, complex ones four); the centre coefficient
+// sigma_k cxy + tz1 is formed first.  ~21 FP64 operations per unknown for real rows.
+template <bool SIGMA>
 __global__ void __launch_bounds__(ST) stencil_kernel(const StencilArgs a, const double2* __restrict__ f,
                                                      const double2* __restrict__ u,
                                                      double2* __restrict__ rho,
@@ -203,57 +206,61 @@ __global__ void __launch_bounds__(ST) stencil_kernel(const StencilArgs a, const 
   const double2* __restrict__ fr = f + base;
   const double2 tz0 = a.tzs[3 * k], tz1 = a.tzs[3 * k + 1], tz2 = a.tzs[3 * k + 2];
   const bool realz = a.rz[k] != 0;
-  const double s = a.sig ? a.sig[k] : 1.0;
-  const double w2z = a.w2z[k];
+  const double s = SIGMA ? a.sig[k] : 1.0;
   const bool has_dn = k > 0, has_up = k < a.nz - 1;
   double nr2 = 0.0, nf2 = 0.0;
 #pragma unroll
   for (int e = 0; e < SEPT; ++e) {
-    const long long t = ((long long)blockIdx.x * SEPT + e) * ST + threadIdx.x;
+    const int t = ((int)blockIdx.x * SEPT + e) * ST + (int)threadIdx.x;   // in-plane index (< 2^31)
     if (t >= nxy) break;
-    const int j = (int)(t / a.nx), i = (int)(t - (long long)j * a.nx);
+    const int j = t / a.nx, i = t - j * a.nx;
     const double2 uc = ur[t];
-    double2 h = cmul(a.cxy[t], uc);
+    const double2 fv = fr[t];
+    const double2 cx = a.cxy[t];
+    // centre: acc = f - (sigma cxy + tz1) u
+    double2 c;
+    if (SIGMA) c = make_double2(fma(s, cx.x, tz1.x), fma(s, cx.y, tz1.y));
+    else c = make_double2(cx.x + tz1.x, cx.y + tz1.y);
+    double2 acc = make_double2(fma(-c.x, uc.x, fma(c.y, uc.y, fv.x)), fma(-c.x, uc.y, fma(-c.y, uc.x, fv.y)));
+    // horizontal neighbours (scaled by sigma_k): into hz, which is acc itself when sigma = 1
+    double2 hz = SIGMA ? make_double2(0.0, 0.0) : acc;
     const double2* kx = a.kxs + 3 * i;
     const double2* ky = a.kys + 3 * j;
     if (a.rx[i]) {
-      if (i > 0) { const double2 v = ur[t - 1]; h.x = fma(kx[0].x, v.x, h.x); h.y = fma(kx[0].x, v.y, h.y); }
-      if (i < a.nx - 1) { const double2 v = ur[t + 1]; h.x = fma(kx[2].x, v.x, h.x); h.y = fma(kx[2].x, v.y, h.y); }
+      if (i > 0) { const double2 v = ur[t - 1]; hz.x = fma(-kx[0].x, v.x, hz.x); hz.y = fma(-kx[0].x, v.y, hz.y); }
+      if (i < a.nx - 1) { const double2 v = ur[t + 1]; hz.x = fma(-kx[2].x, v.x, hz.x); hz.y = fma(-kx[2].x, v.y, hz.y); }
     } else {
-      if (i > 0) h = cfma(kx[0], ur[t - 1], h);
-      if (i < a.nx - 1) h = cfma(kx[2], ur[t + 1], h);
+      if (i > 0) hz = cfma(make_double2(-kx[0].x, -kx[0].y), ur[t - 1], hz);
+      if (i < a.nx - 1) hz = cfma(make_double2(-kx[2].x, -kx[2].y), ur[t + 1], hz);
     }
     if (a.ry[j]) {
-      if (j > 0) { const double2 v = ur[t - a.nx]; h.x = fma(ky[0].x, v.x, h.x); h.y = fma(ky[0].x, v.y, h.y); }
-      if (j < a.ny - 1) { const double2 v = ur[t + a.nx]; h.x = fma(ky[2].x, v.x, h.x); h.y = fma(ky[2].x, v.y, h.y); }
+      if (j > 0) { const double2 v = ur[t - a.nx]; hz.x = fma(-ky[0].x, v.x, hz.x); hz.y = fma(-ky[0].x, v.y, hz.y); }
+      if (j < a.ny - 1) { const double2 v = ur[t + a.nx]; hz.x = fma(-ky[2].x, v.x, hz.x); hz.y = fma(-ky[2].x, v.y, hz.y); }
     } else {
-      if (j > 0) h = cfma(ky[0], ur[t - a.nx], h);
-      if (j < a.ny - 1) h = cfma(ky[2], ur[t + a.nx], h);
+      if (j > 0) hz = cfma(make_double2(-ky[0].x, -ky[0].y), ur[t - a.nx], hz);
+      if (j < a.ny - 1) hz = cfma(make_double2(-ky[2].x, -ky[2].y), ur[t + a.nx], hz);
     }
-    double2 au = cmul(tz1, uc);
-    if (a.sig) {
-      au.x = fma(s, h.x, au.x);
-      au.y = fma(s, h.y, au.y);
+    if (SIGMA) {
+      acc.x = fma(s, hz.x, acc.x);
+      acc.y = fma(s, hz.y, acc.y);
     } else {
-      au.x += h.x;
-      au.y += h.y;
+      acc = hz;
     }
     if (realz) {
-      if (has_dn) { const double2 v = ur[t - nxy]; au.x = fma(tz0.x, v.x, au.x); au.y = fma(tz0.x, v.y, au.y); }
-      if (has_up) { const double2 v = ur[t + nxy]; au.x = fma(tz2.x, v.x, au.x); au.y = fma(tz2.x, v.y, au.y); }
+      if (has_dn) { const double2 v = ur[t - nxy]; acc.x = fma(-tz0.x, v.x, acc.x); acc.y = fma(-tz0.x, v.y, acc.y); }
+      if (has_up) { const double2 v = ur[t + nxy]; acc.x = fma(-tz2.x, v.x, acc.x); acc.y = fma(-tz2.x, v.y, acc.y); }
     } else {
-      if (has_dn) au = cfma(tz0, ur[t - nxy], au);
-      if (has_up) au = cfma(tz2, ur[t + nxy], au);
+      if (has_dn) acc = cfma(make_double2(-tz0.x, -tz0.y), ur[t - nxy], acc);
+      if (has_up) acc = cfma(make_double2(-tz2.x, -tz2.y), ur[t + nxy], acc);
     }
-    const double2 fv = fr[t];
-    const double2 res = make_double2(fv.x - au.x, fv.y - au.y);
-    if (rho) rho[base + t] = res;
-    const double w2 = a.w2xy[t] * w2z;
-    nr2 = fma(w2, fma(res.x, res.x, res.y * res.y), nr2);
+    if (rho) rho[base + t] = acc;
+    const double w2 = a.w2xy[t];
+    nr2 = fma(w2, fma(acc.x, acc.x, acc.y * acc.y), nr2);
     if (fnorm) nf2 = fma(w2, fma(fv.x, fv.x, fv.y * fv.y), nf2);
   }
-  const double s1 = block_sum<ST>(nr2, sh);
-  const double s2 = fnorm ? block_sum<ST>(nf2, sh) : 0.0;
+  const double wz = a.w2z[k];
+  const double s1 = block_sum<ST>(nr2, sh) * wz;
+  const double s2 = fnorm ? block_sum<ST>(nf2, sh) * wz : 0.0;
   if (threadIdx.x == 0) {
     const long long part = (long long)rk * gridDim.x + blockIdx.x;   // = (r * nz + k) * gx + bx
     partial[part * 2 + 0] = s1;
@@ -392,7 +399,8 @@ void stencil_residual(const StencilArgs& a, const double2* f, const double2* u, 
   const int planes = a.nrhs * a.nz;
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    stencil_kernel<<<grid, ST, 0, st>>>(a, f, u, rho, partial, fnorm, rk0);
+    if (a.sig) stencil_kernel<true><<<grid, ST, 0, st>>>(a, f, u, rho, partial, fnorm, rk0);
+    else stencil_kernel<false><<<grid, ST, 0, st>>>(a, f, u, rho, partial, fnorm, rk0);
     count_launch();
   }
 }

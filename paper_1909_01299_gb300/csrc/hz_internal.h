@@ -126,6 +126,7 @@ struct ZSolveArgs {
   const signed char* skip_j = nullptr;
   int nx = 0, ny = 0, nz = 0, nrhs = 0;
   int real_cm = 0;
+  int rhs_per_thread = 0;                // 1 or 2; 0 = chosen from the launch size
 };
 void zsolve(const ZSolveArgs& a, cudaStream_t st);
 

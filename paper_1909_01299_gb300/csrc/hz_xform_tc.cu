@@ -47,6 +47,29 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// FP64 <-> FP32 conversions with integer operations.  GB300's FP64 pipe executes two
+// operations per clock per SM, and the hardware conversions F2F.F32.F64 / F2F.F64.F32
+// run on it; done this way they take the integer pipe instead.
+// FP64 -> FP32, round to nearest (ties away); |x| below the FP32 normal range -> signed 0.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e32 = (int)((b >> 52) & 0x7ff) - 896;              // FP32 biased exponent
+  if (e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long full = ((unsigned long long)e32 << 52) + (b & 0x000fffffffffffffULL) + (1ULL << 28);
+  return __uint_as_float(sign | (uint32_t)(full >> 29));       // a rounding carry moves into the exponent
+}
+// FP32 -> FP64 (exact for normal numbers; FP32 denormals -> signed 0).
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const uint32_t e64 = (e == 255u) ? 2047u : e + 896u;
+  return __hiloint2double((int)(sign | (e64 << 20) | ((u & 0x7fffffu) >> 3)), (int)((u & 7u) << 29));
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -218,16 +241,23 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   bool ok = true;
   int issued = 0;
 
+  // Iteration kc: (1) once the MMAs of chunk kc-1 are done, start the table rows of chunk
+  // kc+1 (their stage is free) -- they then have a whole iteration to arrive; (2) wait for
+  // A(kc), B(kc); (3) convert; (4) issue the MMAs of kc; (5) start the data rows of kc+2.
+  // cp.async groups are committed in the order A0 B0 A1 | B1 A2 | B2 A3 | ..., so at step
+  // (2) everything but the newest two groups {A(kc+1), B(kc+1)} must be complete.
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
-    // operand stage s was read by the MMAs of chunk kc-2
-    if (kc >= 2) {
-      const int w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
+    if (kc >= 1) {
+      const int w = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
       if (!__syncthreads_and(w)) { ok = false; break; }
     }
-    cp_async_wait<1>();                                     // raw A(kc) and B(kc) have landed
+    if (kc + 1 < nk) load_b(kc + 1);
+    cp_async_commit();
+    cp_async_wait<2>();                                     // raw A(kc) and B(kc) have landed
     __syncthreads();
-    // convert raw[s] -> TF32 hi/lo operand planes of stage s
+    // convert raw[s] -> TF32 hi/lo operand planes of stage s (free: MMA(kc-2) finished
+    // before the wait on MMA(kc-1) above)
     {
       const uint32_t rsrc = raw0 + s * RAW_BYTES;
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
@@ -238,7 +268,7 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
         double x0, x1, x2, x3;
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * 256 + c * 32));
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * 256 + c * 32 + 16));
-        const float f[4] = {(float)x0, (float)x1, (float)x2, (float)x3};
+        const float f[4] = {f64_to_f32(x0), f64_to_f32(x1), f64_to_f32(x2), f64_to_f32(x3)};
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -269,15 +299,6 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       mma_commit(&bars[s]);
     }
     issued = kc + 1;
-    // next loads: B(kc+1) into stage (kc+1)&1 once the MMAs of chunk kc-1 are done, then A(kc+2)
-    if (kc + 1 < nk) {
-      if (kc >= 1) {
-        const int w = mbar_wait(&bars[(kc + 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
-        if (!__syncthreads_and(w)) { ok = false; break; }
-      }
-      load_b(kc + 1);
-    }
-    cp_async_commit();
     if (kc + 2 < nk) load_raw(kc + 2);
     cp_async_commit();
   }
@@ -310,7 +331,7 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       for (int e = 0; e < 8; ++e) {
         const int ccol = (t.n0 + c16) / 2 + e;               // complex column within the block
         if (ccol >= n) continue;
-        double2 val = make_double2((double)v[2 * e], (double)v[2 * e + 1]);
+        double2 val = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
         double2* p = trans ? out + plane * (long long)ncols * rows_per_plane +
                                  (long long)(b.start + ccol) * rows_per_plane + rip
                            : out + grow * (long long)ncols + b.start + ccol;

@@ -37,41 +37,59 @@ __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
   return make_double2(fma(c.x, y.x, fma(-c.y, y.y, acc.x)), fma(c.x, y.y, fma(c.y, y.x, acc.y)));
 }
 
-template <bool REALCM>
+// RB right-hand sides per thread share each factor load and give the sweep RB independent
+// dependency chains.
+template <bool REALCM, int RB>
 __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const long long plane = (long long)a.nx * a.ny;
+  const int ngrp = (a.nrhs + RB - 1) / RB;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= plane * a.nrhs) return;
-  const int r = (int)(tid / plane);
-  const long long pos = tid - (long long)r * plane;
+  if (tid >= plane * ngrp) return;
+  const int grp = (int)(tid / plane);
+  const long long pos = tid - (long long)grp * plane;
   const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
   if (a.skip_i && (a.skip_i[i] | a.skip_j[j])) return;
   const long long rs = plane * a.nz;
-  const double2* __restrict__ rhs = a.rhs + r * rs + pos;
-  double2* __restrict__ out = a.out + r * rs + pos;
+  const int r0 = grp * RB;
+  const int nr = min(RB, a.nrhs - r0);
+  const double2* __restrict__ rhs = a.rhs + r0 * rs + pos;
+  double2* __restrict__ out = a.out + r0 * rs + pos;
   const double2* __restrict__ P = a.P + pos;
   const double2* __restrict__ Q = a.Q + pos;
   const double2* __restrict__ cm = a.cm;
 
-  double2 y = make_double2(0.0, 0.0);
-#pragma unroll 4
+  double2 y[RB];
+#pragma unroll
+  for (int q = 0; q < RB; ++q) y[q] = make_double2(0.0, 0.0);
+#pragma unroll 2
   for (int k = 0; k < a.nz; ++k) {
-    const double2 b = rhs[k * plane];
     const double2 c = cm[k];
-    double2 t;
-    if (REALCM)
-      t = make_double2(fma(-c.x, y.x, b.x), fma(-c.x, y.y, b.y));
-    else
-      t = csub_mul(b, c, y);
-    y = cmul(t, P[k * plane]);
-    out[k * plane] = y;
+    const double2 pk = P[k * plane];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      if (q < nr) {
+        const double2 b = rhs[q * rs + k * plane];
+        double2 t;
+        if (REALCM)
+          t = make_double2(fma(-c.x, y[q].x, b.x), fma(-c.x, y[q].y, b.y));
+        else
+          t = csub_mul(b, c, y[q]);
+        y[q] = cmul(t, pk);
+        out[q * rs + k * plane] = y[q];
+      }
+    }
   }
-  double2 x = y;
-#pragma unroll 4
+#pragma unroll 2
   for (int k = a.nz - 2; k >= 0; --k) {
-    const double2 yk = out[k * plane];
-    x = csub_mul(yk, Q[k * plane], x);
-    out[k * plane] = x;
+    const double2 qk = Q[k * plane];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      if (q < nr) {
+        const double2 yk = out[q * rs + k * plane];
+        y[q] = csub_mul(yk, qk, y[q]);
+        out[q * rs + k * plane] = y[q];
+      }
+    }
   }
 }
 
@@ -79,44 +97,50 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
 //   ft[r][k][i][j] += sigma_k (cxl[i] aX[r][k][gxl[i]][j] + cxr[i] aX[r][k][gxr[i]][j]
 //                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
 // One thread per element of a plane (blockIdx.y = r * nz + k); interface positions skipped.
-__global__ void __launch_bounds__(256) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
+__global__ void __launch_bounds__(128) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
+  // blockIdx.x = (row i, 128-wide column tile); blockIdx.y = plane r * nz + k
   const int rk = rk0 + blockIdx.y;
   const int k = rk % a.nz;
+  const int jt = (a.ny + 127) >> 7;
+  const int i = blockIdx.x / jt;
+  const int j = (blockIdx.x - i * jt) * 128 + threadIdx.x;
+  if (j >= a.ny || a.skip_i[i] | a.skip_j[j]) return;
   const long long plane = (long long)a.nx * a.ny;
-  const long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (pos >= plane) return;
-  const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
-  if (a.skip_i[i] | a.skip_j[j]) return;
+  const long long pos = (long long)i * a.ny + j;
   const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
   const double2* ax = a.alphaX + (long long)rk * a.nIx * a.ny + j;
   const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
-  double2 g = make_double2(0.0, 0.0);
-  if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
-  if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
-  if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
-  if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
   double2* p = ft + (long long)rk * plane + pos;
   double2 v = *p;
   if (a.sig) {
+    double2 g = make_double2(0.0, 0.0);
+    if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
+    if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
+    if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
+    if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
     const double s = a.sig[k];
     v.x = fma(s, g.x, v.x);
     v.y = fma(s, g.y, v.y);
-  } else {
-    v.x += g.x;
-    v.y += g.y;
+  } else {                                     // sigma = 1: accumulate straight into f~
+    if (pl >= 0) v = cfma(a.cxl[i], ax[(long long)pl * a.ny], v);
+    if (pr >= 0) v = cfma(a.cxr[i], ax[(long long)pr * a.ny], v);
+    if (ql >= 0) v = cfma(a.cyl[j], ay[(long long)ql * a.nx], v);
+    if (qr >= 0) v = cfma(a.cyr[j], ay[(long long)qr * a.nx], v);
   }
   *p = v;
 }
 
 // Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
 //                                              + sum_q Wgy[q][m] bY[r][k][q][l].
-__global__ void __launch_bounds__(256) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
+__global__ void __launch_bounds__(128) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
                                                          int rk0) {
   const int rk = rk0 + blockIdx.y;
+  const int jt = (a.ny + 127) >> 7;
+  const int i = blockIdx.x / jt;
+  const int j = (blockIdx.x - i * jt) * 128 + threadIdx.x;
+  if (j >= a.ny) return;
   const long long plane = (long long)a.nx * a.ny;
-  const long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (pos >= plane) return;
-  const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
+  const long long pos = (long long)i * a.ny + j;
   const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
   const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
   double2 b = make_double2(0.0, 0.0);
@@ -168,31 +192,39 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
 }  // namespace
 
 void zsolve(const ZSolveArgs& a, cudaStream_t st) {
-  const long long n = (long long)a.nx * a.ny * a.nrhs;
-  if (n == 0) return;
+  if ((long long)a.nx * a.ny * a.nrhs == 0) return;
   const int T = 128;
+  // one right-hand side per thread unless asked otherwise (measured faster on GB300 for
+  // the benchmark sizes: more independent sweeps in flight beat shared factor loads)
+  const int rb = (a.rhs_per_thread == 2) ? 2 : 1;
+  const long long n = (long long)a.nx * a.ny * ((a.nrhs + rb - 1) / rb);
   const unsigned grid = (unsigned)((n + T - 1) / T);
-  if (a.real_cm) zsolve_kernel<true><<<grid, T, 0, st>>>(a);
-  else zsolve_kernel<false><<<grid, T, 0, st>>>(a);
+  if (rb == 2) {
+    if (a.real_cm) zsolve_kernel<true, 2><<<grid, T, 0, st>>>(a);
+    else zsolve_kernel<false, 2><<<grid, T, 0, st>>>(a);
+  } else {
+    if (a.real_cm) zsolve_kernel<true, 1><<<grid, T, 0, st>>>(a);
+    else zsolve_kernel<false, 1><<<grid, T, 0, st>>>(a);
+  }
   count_launch();
 }
 
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) {
-  const long long plane = (long long)a.nx * a.ny;
   const int planes = a.nrhs * a.nz;
+  const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
-    dim3 grid((unsigned)((plane + 255) / 256), std::min(65535, planes - rk0));
-    boundary_rhs_kernel<<<grid, 256, 0, st>>>(a, ft, rk0);
+    dim3 grid(gx, std::min(65535, planes - rk0));
+    boundary_rhs_kernel<<<grid, 128, 0, st>>>(a, ft, rk0);
     count_launch();
   }
 }
 
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) {
-  const long long plane = (long long)a.nx * a.ny;
   const int planes = a.nrhs * a.nz;
+  const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
-    dim3 grid((unsigned)((plane + 255) / 256), std::min(65535, planes - rk0));
-    global_rhs_kernel<<<grid, 256, 0, st>>>(a, out, rk0);
+    dim3 grid(gx, std::min(65535, planes - rk0));
+    global_rhs_kernel<<<grid, 128, 0, st>>>(a, out, rk0);
     count_launch();
   }
 }

@@ -243,3 +243,65 @@ def test_singular_mode_is_reported(hz, torch_cuda):
     with pytest.raises(hz.HzError) as e:
         hz.Plan(W.uniform_steps(1), W.uniform_steps(1), W.uniform_steps(3), [0, 3], [6.0 + 0j])
     assert e.value.code == 3
+
+
+def _complex_z(w):
+    """Give the z axis an absorbing (complex) end: the last 3 steps times (1 + 0.5i)."""
+    hz = w.hz.copy()
+    hz[-3:] *= (1 + 0.5j)
+    w.hz = hz
+    return w
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_complex_z_steps(hz, torch_cuda, precision):
+    # complex z steps make the z off-diagonals complex (the general sweep and stencil paths)
+    w = _complex_z(W.tiny_pml(26, 22, 15, 2, 2, rim=3, pml=2, nrhs=2))
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sigma_layers(hz, torch_cuda, precision):
+    w = W.tiny_pml(30, 26, 17, 3, 2, rim=4, pml=2, nrhs=2, sigma=True)
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    plan, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
+    res = plan.residual(torch_cuda.from_numpy(w.f).cuda(), torch_cuda.from_numpy(u).cuda())
+    assert np.allclose(res, O.residual(P, u, w.f), rtol=1e-3, atol=1e-15)
+
+
+def test_mixed_adjoint_and_host_entry(hz, torch_cuda):
+    torch = torch_cuda
+    w = W.tiny_pml(28, 24, 16, 2, 2, rim=3, pml=2, nrhs=2)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal(w.f.shape) + 1j * rng.standard_normal(w.f.shape)
+    lam_o = O.adjoint_solve(O.Problem.from_workload(w), g, method="lu")
+    plan = hz.Plan.from_workload(w, precision="mixed")
+    lam = plan.solve_adjoint(torch.from_numpy(g).cuda()).cpu().numpy()
+    assert rel(lam, lam_o) < TOLMIX
+    uh = plan.solve_host(w.f)
+    assert rel(uh, O.solve(O.Problem.from_workload(w), w.f)) < TOLMIX
+
+
+def test_refinement_not_converged_is_reported(hz, torch_cuda):
+    # zero corrections allowed and an unreachable tolerance: the mixed path must say so
+    w = W.tiny_pml(20, 18, 12, 2, 2, rim=3, pml=2, nrhs=1)
+    plan = hz.Plan.from_workload(w, precision="mixed", rtol=1e-15, max_refine=0)
+    with pytest.raises(hz.HzError) as e:
+        plan.solve(torch_cuda.from_numpy(w.f).cuda())
+    assert e.value.code == 5
+
+
+def test_nonfinite_input_is_reported(hz, torch_cuda):
+    w = W.tiny_pml(20, 18, 12, 2, 2, rim=3, pml=2, nrhs=1)
+    f = w.f.copy()
+    f[0, 3, 4, 5] = np.nan
+    plan = hz.Plan.from_workload(w)
+    fd = torch_cuda.from_numpy(f).cuda()
+    u = plan.solve(fd)
+    with pytest.raises(hz.HzError) as e:
+        plan.residual(fd, u)
+    assert e.value.code == 4
