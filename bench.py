@@ -113,6 +113,31 @@ def dist_env():
     return rank, world, local
 
 
+def measured_peaks():
+    """HBM GB/s and bf16 TFLOP/s measured on this machine (MEASURED_PEAKS.json), with fallbacks."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6786.2)), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time: all-reduce(MAX) of a per-rank scalar (identity without dist)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(unknowns_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job solved unknowns/s: every rank's unknowns over the slowest rank's time."""
+    return world * unknowns_per_rank / seconds_max
+
+
 def block_sizes(n, ifaces):
     edges = [-1] + [int(p) for p in ifaces] + [int(n)]
     return [edges[b + 1] - edges[b] - 1 for b in range(len(edges) - 1)]
@@ -129,21 +154,21 @@ def bulk_macs(w, nrhs):
     return [per * rows_x * sx, per * rows_y * sy, per * rows_y * sy, per * rows_x * sx]
 
 
-def kernel_source_hash():
+def kernel_source_hash(fname: str = "hz_xform.cu"):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1909_01299_gb300", "csrc", "hz_xform.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_1909_01299_gb300", "csrc", fname), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, workload: str):
+def profiled_traffic(kernel: str, workload: str, fname: str = "hz_xform.cu"):
     """dram bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             data = json.load(fh)
         ent = data.get(kernel, {})
-        if ent.get("source_sha") == kernel_source_hash() and ent.get("workload") == workload:
+        if ent.get("source_sha") == kernel_source_hash(fname) and ent.get("workload") == workload:
             return ent.get("bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -227,11 +252,7 @@ def time_path(torch, hz, plan, f, u, steps, warmup, dist, world, device):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
     launches = plan.info()["kernel_launches"] - l0
     stages = plan.stage_times()
     plan.set_stage_timing(False)
@@ -284,14 +305,10 @@ def run_hz(args):
     e2e_steps = max(3, args.steps // 2)
     for _ in range(e2e_steps):
         plan.solve_host(fh, out=uh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
 
     unknowns = w.unknowns * R
-    value = world * unknowns / (ms64 * 1e-3)
+    value = job_throughput(unknowns, world, ms64 * 1e-3)
     # roofline of the dominant kernel: the FP64 bulk transform (4 launches per solve)
     macs = bulk_macs(w, R)
     complex_w = True
@@ -300,6 +317,15 @@ def run_hz(args):
     achieved = flops_per_launch / (t_launch * 1e-3) / 1e12
     peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
     total_ms = sum(v[0] for v in st64.values())
+    # mixed path: the tensor-core bulk transform (HBM-bound: it reads and writes one volume)
+    hbm_peak, hbm_src = measured_peaks()
+    tc_launch_ms = (stmx["fwd"][0] + stmx["inv"][0]) / max(1, stmx["fwd"][1] + stmx["inv"][1])
+    tc_bytes = 2 * 16 * w.unknowns * R
+    roof_tc = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
+               "achieved": tc_bytes / (tc_launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "frac": tc_bytes / (tc_launch_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
+               "bytes_per_launch": tc_bytes, "launch_ms": tc_launch_ms,
+               "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -326,7 +352,8 @@ def run_hz(args):
                      "traffic": profiled_traffic("xform_kernel<double>", w.name),
                      "share_of_step": (st64["fwd"][0] + st64["inv"][0]) / max(total_ms, 1e-9)},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in st64.items() if v[1]},
-        "mixed": {"value": world * unknowns / (msmx * 1e-3), "ms_per_step": msmx,
+        "mixed": {"value": job_throughput(unknowns, world, msmx * 1e-3), "ms_per_step": msmx,
+                  "roofline": roof_tc,
                   "speedup_vs_fp64": ms64 / msmx, "refinements": infomx["refinements"],
                   "rel_residual_max": resmx, "gpu_launches": launchesmx, "dtype": "c64 transforms + f64",
                   "stages_ms_per_step": {k: v[0] / args.steps for k, v in stmx.items() if v[1]},

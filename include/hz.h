@@ -144,6 +144,13 @@ hz_status hz_plan_set_frequency(hz_plan_t plan, double omega);
  * Eq. (fdmtrprjfr)).  The current frequency scaling omega^2 still applies. */
 hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
 
+/* Autotuner: times one solve of nrhs right-hand sides (on zero data, in the plan's
+ * workspace) for each kernel variant the plan can use -- one or two right-hand sides per
+ * thread in the z sweeps ("pencil batch"), and for mixed plans tensor-core or CUDA-core
+ * FP32 bulk transforms -- and keeps the fastest.  *choice_out (may be NULL) receives
+ * rhs_per_thread + 10 * tensor_cores. */
+hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
+
 /* Change the options' stream, precision, rtol and max_refine of a plan. */
 hz_status hz_plan_set_options(hz_plan_t plan, const hz_options *opts);
 
@@ -204,8 +211,8 @@ typedef struct hz_batch_s *hz_batch_t;
 hz_status hz_batch_create(int nitems, const hz_plan_t *plans, const int *nrhs, int nlanes, hz_batch_t *out);
 hz_status hz_batch_solve(hz_batch_t batch, const hz_c128 *const *f_dev, hz_c128 *const *u_dev,
                          double *rel_host);
-/* Autotuner: times graph replays with 1, 2, 4 and 8 lanes on the given inputs and keeps
- * the fastest (written to *lanes_out). */
+/* Autotuner: tunes every plan of the batch (hz_plan_autotune), then times graph replays
+ * with 1, 2, 4 and 8 lanes on the given inputs and keeps the fastest (*lanes_out). */
 hz_status hz_batch_autotune(hz_batch_t batch, const hz_c128 *const *f_dev, hz_c128 *const *u_dev,
                             int *lanes_out);
 /* Last replay's CUDA-event time (ms), kernels per replay, lanes in use. */

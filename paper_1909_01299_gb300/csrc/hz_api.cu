@@ -82,6 +82,7 @@ struct hz_plan_s {
   double omega = 1.0;
   bool need_global = false;
   bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
+  int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -668,6 +669,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   za.skip_i = p->dx.skip; za.skip_j = p->dy.skip;
   za.rhs = w.FT; za.out = w.V;
   za.P = p->Pb; za.Q = p->Qb; za.cm = p->cm_b;
+  za.rhs_per_thread = p->zs_rb;
   // Step 2: mode-wise z solves of every block (pass A)
   {
     Stage t(p, st, HZ_STAGE_PASS_A);
@@ -1327,6 +1329,47 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   return HZ_OK;
 }
 
+hz_status hz_plan_autotune(hz_plan_t p, int nrhs, int* choice_out) {
+  if (!p || nrhs < 1) return HZ_ERR_ARG;
+  try {
+    ensure_ws(p, nrhs);
+    double2* buf = ensure_extra(p, p->ws.F2, p->ws.f2_cap, nrhs);
+    double2* out = ensure_extra(p, p->ws.HU, p->ws.hu_cap, nrhs);
+    ck(cudaMemsetAsync(buf, 0, sizeof(double2) * (size_t)p->nx * p->ny * p->nz * nrhs, p->st));
+    const bool mixed = p->opts.precision == HZ_MIXED;
+    const bool timing = p->timing;
+    p->timing = false;
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_rb = p->zs_rb;
+    bool best_tc = p->use_tc;
+    for (int rb = 1; rb <= 2; ++rb)
+      for (int tc = mixed ? 0 : 1; tc <= 1; ++tc) {
+        p->zs_rb = rb;
+        p->use_tc = tc != 0;
+        solve_core(p, p->ws, p->st, buf, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up
+        ck(cudaEventRecord(e0, p->st));
+        for (int rep = 0; rep < 3; ++rep) solve_core(p, p->ws, p->st, buf, out, nrhs, mixed, hz::XS_STORE, 0);
+        ck(cudaEventRecord(e1, p->st));
+        ck(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->zs_rb = best_rb;
+    p->use_tc = best_tc;
+    p->timing = timing;
+    if (choice_out) *choice_out = best_rb + (best_tc ? 10 : 0);
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
 hz_status hz_batch_create(int nitems, const hz_plan_t* plans, const int* nrhs, int nlanes, hz_batch_t* out) {
   if (!out) return HZ_ERR_ARG;
   *out = nullptr;
@@ -1368,6 +1411,10 @@ hz_status hz_batch_autotune(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* 
   if (!b || !f_dev || !u_dev) return HZ_ERR_ARG;
   try {
     const int n = (int)b->plans.size();
+    for (int i = 0; i < n; ++i) {
+      const hz_status st = hz_plan_autotune(b->plans[i], b->nrhs[i], nullptr);
+      if (st != HZ_OK) throw Fail{st};
+    }
     int best_l = b->nlanes;
     double best_ms = 1e300;
     for (int l : {1, 2, 4, 8}) {

@@ -59,6 +59,7 @@ SIGNATURES = {
     "hz_plan_set_frequency": (ctypes.c_int, [_P, ctypes.c_double]),
     "hz_plan_set_k2": (ctypes.c_int, [_P, _P]),
     "hz_plan_set_options": (ctypes.c_int, [_P, ctypes.POINTER(hz_options)]),
+    "hz_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
@@ -194,6 +195,12 @@ class Plan:
             self._opts.max_refine = max_refine
         self._opts.cuda_stream = _stream_handle(stream)
         _check(_lib.hz_plan_set_options(self._h, ctypes.byref(self._opts)), "hz_plan_set_options")
+
+    def autotune(self, nrhs: int) -> dict:
+        """hz_plan_autotune: pick the fastest kernel variants for nrhs right-hand sides."""
+        c = ctypes.c_int()
+        _check(_lib.hz_plan_autotune(self._h, int(nrhs), ctypes.byref(c)), "hz_plan_autotune")
+        return {"rhs_per_thread": c.value % 10, "tensor_cores": c.value >= 10}
 
     def set_frequency(self, omega: float):
         _check(_lib.hz_plan_set_frequency(self._h, float(omega)), "hz_plan_set_frequency")

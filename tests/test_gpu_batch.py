@@ -79,3 +79,17 @@ def test_batch_autotune_picks_a_lane_count(env):
     rel = batch.solve(fs, us)
     assert np.all(rel <= 1e-8)
     batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plan_autotune_keeps_results(env, precision):
+    torch, hz = env
+    w = W.tiny_pml(40, 36, 20, 2, 2, rim=4, pml=2, nrhs=3)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan = hz.Plan.from_workload(w, precision=precision)
+    choice = plan.autotune(w.nrhs)
+    assert choice["rhs_per_thread"] in (1, 2)
+    assert precision == "mixed" or choice["tensor_cores"]
+    u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < tol
