@@ -51,6 +51,8 @@ struct AxisDev {
   double2* gcoef = nullptr;      int2* grng = nullptr;       // nI slots (step 5), Wg[p][:]
   int *gl = nullptr, *gr = nullptr;                          // pass B interface indices
   double2 *cl = nullptr, *cr = nullptr;                      // pass B coefficients
+  float2 *edge_coef32 = nullptr, *gcoef32 = nullptr;         // FP32 copies (mixed path)
+  float2 *cl32 = nullptr, *cr32 = nullptr;
   double2* ks = nullptr;                                     // stencil rows / mhat
   signed char* kreal = nullptr;                              // off-diagonals of row real
 };
@@ -198,6 +200,12 @@ T* upload(hz_plan_t p, const std::vector<T>& v) {
 double2* upload_c(hz_plan_t p, const std::vector<cd>& v) {
   std::vector<double2> t(v.size());
   for (size_t i = 0; i < v.size(); ++i) t[i] = make_double2(v[i].real(), v[i].imag());
+  return upload(p, t);
+}
+
+float2* upload_c32(hz_plan_t p, const std::vector<cd>& v) {
+  std::vector<float2> t(v.size());
+  for (size_t i = 0; i < v.size(); ++i) t[i] = make_float2((float)v[i].real(), (float)v[i].imag());
   return upload(p, t);
 }
 
@@ -388,6 +396,7 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
     erng[2 * q + 1] = make_int2(sr, sr + nr);
   }
   D.edge_coef = upload_c(p, ecoef);
+  D.edge_coef32 = upload_c32(p, ecoef);
   D.edge_rng = upload(p, erng);
   // step 5: rows of the whole-axis W at the interfaces
   std::vector<cd> gcoef((size_t)std::max(nI, 1) * n, cd(0));
@@ -396,6 +405,7 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
     for (int q = 0; q < nI; ++q)
       for (int l = 0; l < n; ++l) gcoef[(size_t)q * n + l] = A.gW[(size_t)A.iface[q] * n + l];
   D.gcoef = upload_c(p, gcoef);
+  D.gcoef32 = upload_c32(p, gcoef);
   D.grng = upload(p, grng);
   // step 6: boundary right-hand side coefficients W[e][l] / h across the interface
   std::vector<int> gl(n, -1), grr(n, -1);
@@ -417,6 +427,8 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
   D.gr = upload(p, grr);
   D.cl = upload_c(p, cl);
   D.cr = upload_c(p, cr);
+  D.cl32 = upload_c32(p, cl);
+  D.cr32 = upload_c32(p, cr);
   // stencil rows divided by hhat
   std::vector<cd> ks((size_t)3 * n, cd(0));
   for (int i = 0; i < n; ++i) {
@@ -656,6 +668,24 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   };
   // The interface-row transforms below are non-transposed, so their rows are
   // flattened across planes (one launch row tile covers 32 rows of any planes).
+  // On the mixed path the interface transforms of steps 3, 5 and 6 (contractions with
+  // eigenvector rows, short row transforms, the rank-|I| right-hand sides) run in FP32
+  // like the bulk transforms; the z eliminations, the interface residual and the
+  // refinement residual stay FP64.
+  auto rowx = [&](const hz::XformSet& xs, const double2* in, double2* out, long long rows, cudaStream_t s) {
+    if (lo) hz::xform_f32(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
+    else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
+  };
+  auto crows = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
+    const int2* rng = edge ? d.edge_rng : d.grng;
+    if (lo) hz::contract_rows(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+    else hz::contract_rows(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+  };
+  auto ccols = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
+    const int2* rng = edge ? d.edge_rng : d.grng;
+    if (lo) hz::contract_cols(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+    else hz::contract_cols(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+  };
   // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
   {
     Stage t(p, st, HZ_STAGE_FWD);
@@ -682,12 +712,12 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     const cudaStream_t sy = p->side;
     fork(p, st);
     if (nIx) {
-      hz::contract_rows(w.V, w.cX, p->dx.edge_coef, p->dx.edge_rng, nx, ny, 2 * nIx, planes, st);
-      hz::xform_f64(p->dy.inv, w.cX, w.vX, (int)(2 * nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      crows(p->dx, w.V, w.cX, true, 2 * nIx, st);
+      rowx(p->dy.inv, w.cX, w.vX, 2 * nIx * planes, st);
     }
     if (nIy) {
-      hz::contract_cols(w.V, w.cY, p->dy.edge_coef, p->dy.edge_rng, nx, ny, 2 * nIy, planes, sy);
-      hz::xform_f64(p->dx.inv, w.cY, w.vY, (int)(2 * nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
+      ccols(p->dy, w.V, w.cY, true, 2 * nIy, sy);
+      rowx(p->dx.inv, w.cY, w.vY, 2 * nIy * planes, sy);
     }
     join(p, st);
     t3.reset();
@@ -700,12 +730,13 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     // Step 5: w on the interfaces through the whole-axis eigenbasis
     std::unique_ptr<Stage> t5(new Stage(p, st, HZ_STAGE_GLOBAL));
     fork(p, st);
-    if (nIx) hz::xform_f64(p->dy.gfwd, w.rX, w.aX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
-    if (nIy) hz::xform_f64(p->dx.gfwd, w.rY, w.bY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
+    if (nIx) rowx(p->dy.gfwd, w.rX, w.aX, nIx * planes, st);
+    if (nIy) rowx(p->dx.gfwd, w.rY, w.bY, nIy * planes, sy);
     join(p, st);
     hz::GlobalRhsArgs ga;
     ga.nx = nx; ga.ny = ny; ga.nz = nz; ga.nrhs = R; ga.nIx = nIx; ga.nIy = nIy;
     ga.aX = w.aX; ga.bY = w.bY; ga.WgxI = p->dx.gcoef; ga.WgyI = p->dy.gcoef;
+    if (lo) { ga.WgxI32 = p->dx.gcoef32; ga.WgyI32 = p->dy.gcoef32; }
     hz::global_rhs(ga, w.G, st);                    // r~ (G is free until step 7)
     hz::ZSolveArgs zg = za;
     zg.skip_i = nullptr; zg.skip_j = nullptr;
@@ -714,15 +745,15 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     hz::zsolve(zg, st);
     fork(p, st);
     if (nIx) {
-      hz::contract_rows(w.V, w.cg, p->dx.gcoef, p->dx.grng, nx, ny, nIx, planes, st);
-      hz::xform_f64(p->dy.ginv, w.cg, w.wX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      crows(p->dx, w.V, w.cg, false, nIx, st);
+      rowx(p->dy.ginv, w.cg, w.wX, nIx * planes, st);
       // Step 6 (x interfaces): forward y-transform of w on the interface rows
-      hz::xform_f64(p->dy.fwd, w.wX, w.alX, (int)(nIx * planes), 1, 0, hz::XS_STORE, 0, nullptr, st);
+      rowx(p->dy.fwd, w.wX, w.alX, nIx * planes, st);
     }
     if (nIy) {
-      hz::contract_cols(w.V, w.dg, p->dy.gcoef, p->dy.grng, nx, ny, nIy, planes, sy);
-      hz::xform_f64(p->dx.ginv, w.dg, w.wY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
-      hz::xform_f64(p->dx.fwd, w.wY, w.alY, (int)(nIy * planes), 1, 0, hz::XS_STORE, 0, nullptr, sy);
+      ccols(p->dy, w.V, w.dg, false, nIy, sy);
+      rowx(p->dx.ginv, w.dg, w.wY, nIy * planes, sy);
+      rowx(p->dx.fwd, w.wY, w.alY, nIy * planes, sy);
     }
     join(p, st);
     t5.reset();
@@ -734,6 +765,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     ba.alphaX = w.alX; ba.alphaY = w.alY;
     ba.gxl = p->dx.gl; ba.gxr = p->dx.gr; ba.gyl = p->dy.gl; ba.gyr = p->dy.gr;
     ba.cxl = p->dx.cl; ba.cxr = p->dx.cr; ba.cyl = p->dy.cl; ba.cyr = p->dy.cr;
+    if (lo) { ba.cxl32 = p->dx.cl32; ba.cxr32 = p->dx.cr32; ba.cyl32 = p->dy.cl32; ba.cyr32 = p->dy.cr32; }
     hz::boundary_rhs(ba, w.FT, st);                 // f~ + g~ / M_z, in place
     hz::zsolve(za, st);
   }

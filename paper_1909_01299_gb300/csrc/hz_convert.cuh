@@ -1,0 +1,46 @@
+// Device-side FP64 <-> FP32 conversions and FP32 complex arithmetic for the
+// mixed path (included by .cu files only).
+//
+// GB300's FP64 pipe executes two operations per clock per SM, and the hardware
+// conversions F2F.F32.F64 / F2F.F64.F32 issue to it; the FP32 parts of the mixed
+// path convert with integer operations instead, so that reading FP64 data into
+// FP32 arithmetic costs no FP64-pipe time.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hz {
+
+// FP64 -> FP32, round to nearest (ties away); |x| below the FP32 normal range -> signed 0,
+// above it -> signed infinity.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e32 = (int)((b >> 52) & 0x7ff) - 896;              // FP32 biased exponent
+  if (e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long full = ((unsigned long long)e32 << 52) + (b & 0x000fffffffffffffULL) + (1ULL << 28);
+  return __uint_as_float(sign | (uint32_t)(full >> 29));       // a rounding carry moves into the exponent
+}
+
+// FP32 -> FP64 (exact for normal numbers; FP32 denormals -> signed 0).
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const uint32_t e64 = (e == 255u) ? 2047u : e + 896u;
+  return __hiloint2double((int)(sign | (e64 << 20) | ((u & 0x7fffffu) >> 3)), (int)((u & 7u) << 29));
+}
+
+__device__ __forceinline__ float2 to_c64(double2 v) { return make_float2(f64_to_f32(v.x), f64_to_f32(v.y)); }
+__device__ __forceinline__ double2 to_c128(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
+
+// acc + c * y in FP32
+__device__ __forceinline__ float2 cfma32(float2 c, float2 y, float2 acc) {
+  return make_float2(fmaf(c.x, y.x, fmaf(-c.y, y.y, acc.x)), fmaf(c.x, y.y, fmaf(c.y, y.x, acc.y)));
+}
+
+}  // namespace hz

@@ -15,6 +15,7 @@
 //  * grad_layers: G_L = sum_{k in L} hhat^z_k sum conj(lam) hhat^x hhat^y u.
 #include <algorithm>
 
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
@@ -28,8 +29,10 @@ __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// C = double2: FP64 arithmetic; C = float2: FP32 arithmetic on FP64 data (mixed path).
+template <typename C>
 __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __restrict__ out,
-                                     const double2* __restrict__ coef, const int2* __restrict__ range,
+                                     const C* __restrict__ coef, const int2* __restrict__ range,
                                      int nrows, int ncols, int nslots, long long nplanes) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long total = nplanes * nslots * (long long)ncols;
@@ -40,14 +43,21 @@ __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __r
   const long long plane = ps / nslots;
   const int2 rg = range[s];
   const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
-  const double2* __restrict__ c = coef + (long long)s * nrows;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int i = rg.x; i < rg.y; ++i) acc = cfma(c[i], v[(long long)i * ncols], acc);
-  out[t] = acc;
+  const C* __restrict__ c = coef + (long long)s * nrows;
+  if constexpr (sizeof(C) == sizeof(double2)) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = rg.x; i < rg.y; ++i) acc = cfma(c[i], v[(long long)i * ncols], acc);
+    out[t] = acc;
+  } else {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = rg.x; i < rg.y; ++i) acc = cfma32(c[i], to_c64(v[(long long)i * ncols]), acc);
+    out[t] = to_c128(acc);
+  }
 }
 
+template <typename C>
 __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __restrict__ out,
-                                     const double2* __restrict__ coef, const int2* __restrict__ range,
+                                     const C* __restrict__ coef, const int2* __restrict__ range,
                                      int nrows, int ncols, int nslots, long long nplanes) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long total = nplanes * nslots * (long long)nrows;
@@ -58,10 +68,16 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
   const long long plane = ps / nslots;
   const int2 rg = range[s];
   const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
-  const double2* __restrict__ c = coef + (long long)s * ncols;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
-  out[t] = acc;
+  const C* __restrict__ c = coef + (long long)s * ncols;
+  if constexpr (sizeof(C) == sizeof(double2)) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
+    out[t] = acc;
+  } else {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = rg.x; j < rg.y; ++j) acc = cfma32(c[j], to_c64(v[j]), acc);
+    out[t] = to_c128(acc);
+  }
 }
 
 // rX[r][k][p][j] for all j; rY[r][k][q][i] for all i (0 where i is an x-interface).
@@ -340,20 +356,39 @@ unsigned blocks_for(long long n, int T) { return (unsigned)((n + T - 1) / T); }
 
 }  // namespace
 
-void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
-                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+template <typename C>
+void contract_rows_t(const double2* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
+                     int nslots, long long nplanes, cudaStream_t st) {
   const long long n = nplanes * nslots * (long long)ncols;
   if (n == 0) return;
-  contract_rows_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  contract_rows_kernel<C><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
   count_launch();
 }
 
-void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
-                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+template <typename C>
+void contract_cols_t(const double2* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
+                     int nslots, long long nplanes, cudaStream_t st) {
   const long long n = nplanes * nslots * (long long)nrows;
   if (n == 0) return;
-  contract_cols_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  contract_cols_kernel<C><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
   count_launch();
+}
+
+void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+}
+void contract_rows(const double2* V, double2* out, const float2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+}
+void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+}
+void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
 }
 
 void iface_residual(const IfaceArgs& a, const double2* f, const double2* vX, const double2* vY,

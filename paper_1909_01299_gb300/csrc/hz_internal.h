@@ -142,6 +142,10 @@ struct BoundaryArgs {
   const int* gyl = nullptr; const int* gyr = nullptr;     // per j
   const double2* cxl = nullptr; const double2* cxr = nullptr;   // per i
   const double2* cyl = nullptr; const double2* cyr = nullptr;   // per j
+  // FP32 copies of the four coefficient arrays: when set, the boundary term is formed in
+  // FP32 and added to f~ in FP64 (mixed path)
+  const float2* cxl32 = nullptr; const float2* cxr32 = nullptr;
+  const float2* cyl32 = nullptr; const float2* cyr32 = nullptr;
 };
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st);
 
@@ -152,6 +156,8 @@ struct GlobalRhsArgs {
   const double2* bY = nullptr;           // [r][k][nIy][nx]
   const double2* WgxI = nullptr;         // [nIx][nx]
   const double2* WgyI = nullptr;         // [nIy][ny]
+  const float2* WgxI32 = nullptr;        // FP32 copies: when set, FP32 arithmetic (mixed path)
+  const float2* WgyI32 = nullptr;
 };
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
 
@@ -170,6 +176,11 @@ void contract_rows(const double2* V, double2* out, const double2* coef, const in
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
 // out[plane][s][i] = sum_{j in [lo_s, hi_s)} coef[s][j] V[plane][i][j]  (contraction within rows)
 void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+// The same contractions with FP32 arithmetic on the FP64 data (mixed path).
+void contract_rows(const double2* V, double2* out, const float2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
 
 struct IfaceArgs {

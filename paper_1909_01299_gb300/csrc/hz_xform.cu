@@ -16,12 +16,20 @@
 // three DFMA per complex multiply-add instead of four.  Real tables (blocks whose
 // steps are all real) take two DFMA.  FP32 variant (mixed path): the same tiling in
 // FFMA with the four-product form on an FP32 copy of the tables.
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
 namespace {
 
 constexpr int TN = 16, TK = 16, NT = 256;
+
+// data in and results out: FP32 through the integer conversions (no FP64-pipe work)
+template <typename Acc> __device__ __forceinline__ Acc to_acc(double v);
+template <> __device__ __forceinline__ double to_acc<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_acc<float>(double v) { return f64_to_f32(v); }
+__device__ __forceinline__ double from_acc(double v) { return v; }
+__device__ __forceinline__ double from_acc(float v) { return f32_to_f64(v); }
 static_assert(TN == 16, "host tiling (kTileN) assumes 16-column tiles");
 
 template <typename Acc, bool REAL, int TM>
@@ -65,8 +73,8 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
       const int kk = la_k + e;
       double2 v = make_double2(0.0, 0.0);
       if (arow_ok && k0 + kk < n) v = ain[k0 + kk];
-      sm.a[0][kk][la_row] = Acc(v.x);
-      sm.a[1][kk][la_row] = Acc(v.y);
+      sm.a[0][kk][la_row] = to_acc<Acc>(v.x);
+      sm.a[1][kk][la_row] = to_acc<Acc>(v.y);
       if (!REAL && F64) sm.a[(REAL || !F64) ? 1 : 2][kk][la_row] = Acc(v.x + v.y);
     }
     {
@@ -115,8 +123,8 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
   for (int r = 0; r < RPT; ++r) {
     double re, im;
     if (REAL || !F64) {
-      re = double(acc[r][0]);
-      im = double(acc[r][1]);
+      re = from_acc(acc[r][0]);
+      im = from_acc(acc[r][1]);
     } else {
       re = double(acc[r][0]) - double(acc[r][2]);
       im = double(acc[r][0]) + double(acc[r][1]);

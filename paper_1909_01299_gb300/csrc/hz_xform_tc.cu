@@ -29,6 +29,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
@@ -45,29 +46,6 @@ constexpr long long WAIT_NS = 2000000000LL;   // 2 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// FP64 <-> FP32 conversions with integer operations.  GB300's FP64 pipe executes two
-// operations per clock per SM, and the hardware conversions F2F.F32.F64 / F2F.F64.F32
-// run on it; done this way they take the integer pipe instead.
-// FP64 -> FP32, round to nearest (ties away); |x| below the FP32 normal range -> signed 0.
-__device__ __forceinline__ float f64_to_f32(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  const int e32 = (int)((b >> 52) & 0x7ff) - 896;              // FP32 biased exponent
-  if (e32 <= 0) return __uint_as_float(sign);
-  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
-  const unsigned long long full = ((unsigned long long)e32 << 52) + (b & 0x000fffffffffffffULL) + (1ULL << 28);
-  return __uint_as_float(sign | (uint32_t)(full >> 29));       // a rounding carry moves into the exponent
-}
-// FP32 -> FP64 (exact for normal numbers; FP32 denormals -> signed 0).
-__device__ __forceinline__ double f32_to_f64(float v) {
-  const uint32_t u = __float_as_uint(v);
-  const uint32_t sign = u & 0x80000000u;
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0) return __hiloint2double((int)sign, 0);
-  const uint32_t e64 = (e == 255u) ? 2047u : e + 896u;
-  return __hiloint2double((int)(sign | (e64 << 20) | ((u & 0x7fffffu) >> 3)), (int)((u & 7u) << 29));
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -313,34 +291,84 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
     const int lw = warp & 3, cgrp = warp >> 2;             // TMEM lane quarter, column group
     constexpr int NGRP = TC_THREADS / 128;
     const int r = lw * 32 + lane;
-    const long long grow = row0 + r;
-    long long plane = 0;
-    int rip = 0;
-    bool row_ok = grow < nrows;
-    if (row_ok) {
-      plane = grow / rows_per_plane;
-      rip = (int)(grow - plane * rows_per_plane);
-      if (rowskip && rowskip[rip]) row_ok = false;
-    }
     const uint32_t tl = tmem + ((uint32_t)(lw * 32) << 16);
-    for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
-      float v[16];
-      tmem_ld16(tl + c16, v);
-      if (!row_ok) continue;
+    if (trans) {
+      // out[plane][col][row]: the 32 rows of a warp are consecutive addresses of one column
+      const long long grow = row0 + r;
+      long long plane = 0;
+      int rip = 0;
+      bool row_ok = grow < nrows;
+      if (row_ok) {
+        plane = grow / rows_per_plane;
+        rip = (int)(grow - plane * rows_per_plane);
+        if (rowskip && rowskip[rip]) row_ok = false;
+      }
+      for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
+        float v[16];
+        tmem_ld16(tl + c16, v);
+        if (!row_ok) continue;
+        double2* p[8];
+        double2 val[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int ccol = (t.n0 + c16) / 2 + e;               // complex column within the block
-        if (ccol >= n) continue;
-        double2 val = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
-        double2* p = trans ? out + plane * (long long)ncols * rows_per_plane +
-                                 (long long)(b.start + ccol) * rows_per_plane + rip
-                           : out + grow * (long long)ncols + b.start + ccol;
-        if (store == XS_ACCUM) {
-          const double2 o = *p;
-          val.x += o.x;
-          val.y += o.y;
+        for (int e = 0; e < 8; ++e) {
+          const int ccol = (t.n0 + c16) / 2 + e;             // complex column within the block
+          p[e] = ccol < n ? out + plane * (long long)ncols * rows_per_plane +
+                                (long long)(b.start + ccol) * rows_per_plane + rip
+                          : nullptr;
+          val[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
         }
-        *p = val;
+        if (store == XS_ACCUM) {                           // all old values in flight at once
+          double2 o[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) o[e] = p[e] ? *p[e] : make_double2(0.0, 0.0);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) { val[e].x += o[e].x; val[e].y += o[e].y; }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (p[e]) *p[e] = val[e];
+      }
+    } else {
+      // Rows are contiguous in memory: stage the FP64 tile in the (now idle) pipeline
+      // buffers, row stride padded by 16 bytes so that the row-per-lane writes are
+      // conflict-free, then let each warp write whole rows with consecutive lanes on
+      // consecutive columns.  The tile needs nt * 1024 + 2048 bytes; the buffers hold
+      // 2 * RAW_BYTES + 4 * A_BYTES + 512 * nt, enough for every nt <= 252.
+      const int ncx = nt / 2;
+      const int sstride = ncx * 16 + 16;
+      for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
+        float v[16];
+        tmem_ld16(tl + c16, v);
+        double2* dst = reinterpret_cast<double2*>(smem + (size_t)r * sstride) + c16 / 2;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
+      }
+      __syncthreads();
+      const int ccount = min(ncx, n - t.n0 / 2);            // complex columns of the block in this tile
+      for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
+        const long long g = row0 + rr;
+        if (g >= nrows) break;
+        if (rowskip) {
+          const long long pl = g / rows_per_plane;
+          if (rowskip[g - pl * rows_per_plane]) continue;
+        }
+        const double2* src = reinterpret_cast<const double2*>(smem + (size_t)rr * sstride);
+        double2* dg = out + g * (long long)ncols + b.start + t.n0 / 2;
+        if (store == XS_ACCUM) {
+          for (int c = lane; c < ccount; c += 64) {         // two old values in flight per lane
+            const bool two = c + 32 < ccount;
+            const double2 o0 = dg[c];
+            const double2 o1 = two ? dg[c + 32] : make_double2(0.0, 0.0);
+            const double2 v0 = src[c];
+            dg[c] = make_double2(v0.x + o0.x, v0.y + o0.y);
+            if (two) {
+              const double2 v1 = src[c + 32];
+              dg[c + 32] = make_double2(v1.x + o1.x, v1.y + o1.y);
+            }
+          }
+        } else {
+          for (int c = lane; c < ccount; c += 32) dg[c] = src[c];
+        }
       }
     }
   } else if (tid == 0) {

@@ -20,6 +20,7 @@
 // the back sweep.  FP64 throughout.
 #include <algorithm>
 
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
@@ -97,6 +98,8 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
 //   ft[r][k][i][j] += sigma_k (cxl[i] aX[r][k][gxl[i]][j] + cxr[i] aX[r][k][gxr[i]][j]
 //                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
 // One thread per element of a plane (blockIdx.y = r * nz + k); interface positions skipped.
+// LO: the term is formed in FP32 (mixed path) and added to ft in FP64.
+template <bool LO>
 __global__ void __launch_bounds__(128) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
   // blockIdx.x = (row i, 128-wide column tile); blockIdx.y = plane r * nz + k
   const int rk = rk0 + blockIdx.y;
@@ -112,7 +115,22 @@ __global__ void __launch_bounds__(128) boundary_rhs_kernel(const BoundaryArgs a,
   const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
   double2* p = ft + (long long)rk * plane + pos;
   double2 v = *p;
-  if (a.sig) {
+  if (LO) {
+    float2 g = make_float2(0.f, 0.f);
+    if (pl >= 0) g = cfma32(a.cxl32[i], to_c64(ax[(long long)pl * a.ny]), g);
+    if (pr >= 0) g = cfma32(a.cxr32[i], to_c64(ax[(long long)pr * a.ny]), g);
+    if (ql >= 0) g = cfma32(a.cyl32[j], to_c64(ay[(long long)ql * a.nx]), g);
+    if (qr >= 0) g = cfma32(a.cyr32[j], to_c64(ay[(long long)qr * a.nx]), g);
+    const double2 gd = to_c128(g);
+    if (a.sig) {
+      const double s = a.sig[k];
+      v.x = fma(s, gd.x, v.x);
+      v.y = fma(s, gd.y, v.y);
+    } else {
+      v.x += gd.x;
+      v.y += gd.y;
+    }
+  } else if (a.sig) {
     double2 g = make_double2(0.0, 0.0);
     if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
     if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
@@ -132,6 +150,8 @@ __global__ void __launch_bounds__(128) boundary_rhs_kernel(const BoundaryArgs a,
 
 // Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
 //                                              + sum_q Wgy[q][m] bY[r][k][q][l].
+// LO: FP32 arithmetic on the FP64 data (mixed path).
+template <bool LO>
 __global__ void __launch_bounds__(128) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
                                                          int rk0) {
   const int rk = rk0 + blockIdx.y;
@@ -143,9 +163,17 @@ __global__ void __launch_bounds__(128) global_rhs_kernel(const GlobalRhsArgs a, 
   const long long pos = (long long)i * a.ny + j;
   const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
   const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
-  double2 b = make_double2(0.0, 0.0);
-  for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
-  for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+  double2 b;
+  if (LO) {
+    float2 g = make_float2(0.f, 0.f);
+    for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64(ax[(long long)p * a.ny]), g);
+    for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64(by[(long long)q * a.nx]), g);
+    b = to_c128(g);
+  } else {
+    b = make_double2(0.0, 0.0);
+    for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
+    for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+  }
   out[(long long)rk * plane + pos] = b;
 }
 
@@ -214,7 +242,8 @@ void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) {
   const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    boundary_rhs_kernel<<<grid, 128, 0, st>>>(a, ft, rk0);
+    if (a.cxl32) boundary_rhs_kernel<true><<<grid, 128, 0, st>>>(a, ft, rk0);
+    else boundary_rhs_kernel<false><<<grid, 128, 0, st>>>(a, ft, rk0);
     count_launch();
   }
 }
@@ -224,7 +253,8 @@ void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) {
   const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    global_rhs_kernel<<<grid, 128, 0, st>>>(a, out, rk0);
+    if (a.WgxI32) global_rhs_kernel<true><<<grid, 128, 0, st>>>(a, out, rk0);
+    else global_rhs_kernel<false><<<grid, 128, 0, st>>>(a, out, rk0);
     count_launch();
   }
 }
