@@ -12,16 +12,19 @@
 // lo = tf32(x - hi)), which keeps the result at FP32 accuracy; FP64 iterative
 // refinement of the solve removes the rest.
 //
-// One CTA (16 warps) computes a 128-row x Nt-column tile (Nt <= 256, a multiple of
-// 16) of one block.  The contraction runs in chunks of 32 real K (128 bytes per
-// operand row): all threads convert the FP64 data rows to TF32 hi/lo and store
-// them, with the tables' hi/lo rows, in shared memory in the K-major
-// 128-byte-swizzled layout; one thread issues the 12 MMAs of the chunk and
-// commits them to the chunk's mbarrier; two chunk buffers alternate, so the
-// conversion of chunk c+1 overlaps the MMAs of chunk c.  The epilogue reads
-// the accumulator with tcgen05.ld (warp w reads TMEM lanes 32(w%4)..+31 = tile rows,
-// column chunks w/4, w/4+4, ...), converts to FP64 and stores (transposed or not,
-// optionally adding).
+// One CTA (8 warps) computes a 128-row x Nt-column tile (Nt <= 160, a multiple of
+// 16) of one block; two CTAs share an SM (about 105 KB of shared memory and 256 TMEM
+// columns each), so that one CTA's loads overlap the other's prologue and epilogue.
+// The contraction runs in chunks of 16 real K (64 bytes per operand row): all
+// threads convert the FP64 data rows to TF32 hi/lo and store them, with the tables'
+// hi/lo rows, in shared memory in the K-major 64-byte-swizzled layout; one thread
+// issues the 6 MMAs of the chunk and commits them to the chunk's mbarrier; two chunk
+// buffers alternate, so the conversion of chunk c+1 overlaps the MMAs of chunk c.
+// The epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM lanes
+// 32(w%4)..+31 = tile rows, column chunks w/4, w/4+2, ...), converts to FP64 and
+// stores: transposed outputs straight from registers (a warp's 32 rows are
+// consecutive addresses), row-contiguous outputs through a shared-memory staging
+// tile written out row by row; optionally adding to the old values.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <algorithm>
@@ -36,12 +39,13 @@ namespace hz {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 512;          // 16 warps: 4 per SM sub-partition to hide latency
-constexpr int KCH = 32;                  // real K per chunk (128 bytes of tf32 per row)
-constexpr int ROWB = 128;                // bytes per operand row in a chunk
+constexpr int TC_THREADS = 256;          // 8 warps; two CTAs per SM overlap each other's phases
+constexpr int TC_CTAS_PER_SM = 2;
+constexpr int KCH = 16;                  // real K per chunk (64 bytes of tf32 per operand row)
+constexpr int ROWB = 64;                 // bytes per operand row in a chunk (64-byte swizzle)
 constexpr int A_BYTES = TC_M * ROWB;     // one A plane (hi or lo) of a chunk
-constexpr int TMEM_COLS = 256;
-constexpr int kTcMaxN = 160;             // widest output tile (smem: 64 + 64 + 4 x 160 x 128 B)
+constexpr int TMEM_COLS = 256;           // two CTAs per SM share the 512 columns
+constexpr int kTcMaxN = 160;             // widest output tile (real columns)
 constexpr long long WAIT_NS = 2000000000LL;   // 2 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -79,15 +83,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+// Shared-memory matrix descriptor of a K-major operand with 64-byte rows and the 64-byte
+// swizzle (16-byte unit u of row r stored at unit u ^ ((r >> 1) & 3)); 8-row groups are
+// 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
-  d |= (uint64_t)1u << 16;                          // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;     // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1u << 46;                          // descriptor version
-  d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+  d |= (uint64_t)4u << 61;                          // 64-byte swizzle
   return d;
 }
+__device__ __forceinline__ uint32_t swz64(int r, int u) { return (uint32_t)(r * ROWB + ((u ^ ((r >> 1) & 3)) << 4)); }
 
 // kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
@@ -136,15 +144,16 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory plan of one CTA (offsets from a 1024-byte aligned base):
-//   raw[2]   : FP64 data chunks as loaded, 128 rows x 16 complex (32 KB each)
-//   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 16 KB each), 128B-swizzled
-//   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 128 B each), 128B-swizzled
+//   raw[2]   : FP64 data chunks as loaded, 128 rows x 8 complex (16 KB each)
+//   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 8 KB each), 64B-swizzled
+//   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled
 //   bars     : MMA-completion mbarriers of the two operand stages, TMEM address slot
 // The chunk pipeline: the FP64 rows of chunk c+2 and the table rows of chunk c+1 are in
 // flight (cp.async) while chunk c is converted and its MMAs run.
-constexpr int RAW_BYTES = TC_M * 256;
+constexpr int RAW_ROWB = KCH * 8;        // FP64 bytes of a data row in a chunk (KCH / 2 complex)
+constexpr int RAW_BYTES = TC_M * RAW_ROWB;
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM)
 xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const float* __restrict__ tabs,
                 const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, int ntiles,
                 long long nrows, int rows_per_plane, int ncols, int trans, int store,
@@ -172,23 +181,23 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   auto load_raw = [&](int c) {
     const uint32_t dst = raw0 + (c & 1) * RAW_BYTES;
 #pragma unroll
-    for (int q = 0; q < 2048 / TC_THREADS; ++q) {
-      const int task = tid + TC_THREADS * q;               // 2048 tasks: row = task / 16, complex = task % 16
-      const int r = task >> 4, cc = task & 15;
+    for (int q = 0; q < TC_M * (KCH / 2) / TC_THREADS; ++q) {
+      const int task = tid + TC_THREADS * q;               // row = task / 8, complex = task % 8
+      const int r = task >> 3, cc = task & 7;
       const long long grow = row0 + r;
       const int col = c * (KCH / 2) + cc;
       const bool ok = grow < nrows && col < n;
       const double2* src = ok ? in + grow * (long long)ncols + b.start + col : in;
-      cp_async16(dst + r * 256 + cc * 16, src, ok);
+      cp_async16(dst + r * RAW_ROWB + cc * 16, src, ok);
     }
   };
   // issue the table rows (hi and lo) of chunk c into bop[c & 1], 128B-swizzled
   auto load_b = [&](int c) {
     const uint32_t bh = bop0 + (c & 1) * BSTAGE, bl = bh + B_BYTES;
-    for (int task = tid; task < nt * 8; task += TC_THREADS) {
-      const int r = task >> 3, cc = task & 7;
+    for (int task = tid; task < nt * (ROWB / 16); task += TC_THREADS) {
+      const int r = task >> 2, cc = task & 3;
       const long long go = (long long)r * b.kpad + c * KCH + 4 * cc;
-      const uint32_t off = r * ROWB + ((cc ^ (r & 7)) << 4);
+      const uint32_t off = swz64(r, cc);
       cp_async16(bh + off, thi + go, true);
       cp_async16(bl + off, tlo + go, true);
     }
@@ -240,12 +249,12 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       const uint32_t rsrc = raw0 + s * RAW_BYTES;
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
 #pragma unroll
-      for (int q = 0; q < 1024 / TC_THREADS; ++q) {
-        const int task = tid + TC_THREADS * q;             // 1024 tasks: row = task / 8, pair = task % 8
-        const int r = task >> 3, c = task & 7;
+      for (int q = 0; q < TC_M * (ROWB / 16) / TC_THREADS; ++q) {
+        const int task = tid + TC_THREADS * q;             // row = task / 4, 16-byte unit = task % 4
+        const int r = task >> 2, c = task & 3;
         double x0, x1, x2, x3;
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * 256 + c * 32));
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * 256 + c * 32 + 16));
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * RAW_ROWB + c * 32));
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * RAW_ROWB + c * 32 + 16));
         const float f[4] = {f64_to_f32(x0), f64_to_f32(x1), f64_to_f32(x2), f64_to_f32(x3)};
         uint32_t h[4], l[4];
 #pragma unroll
@@ -253,7 +262,7 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
           h[e] = to_tf32(f[e]);
           l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
         }
-        const uint32_t off = r * ROWB + ((c ^ (r & 7)) << 4);
+        const uint32_t off = swz64(r, c);
         st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
         st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
@@ -267,8 +276,8 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
 #pragma unroll
       for (int ks = 0; ks < KCH / 8; ++ks) {               // 8 tf32 = 32 bytes per MMA
         const uint32_t koff = ks * 32;
-        const uint64_t dah = smem_desc_sw128(a_hi + koff), dal = smem_desc_sw128(a_lo + koff);
-        const uint64_t dbh = smem_desc_sw128(b_hi + koff), dbl = smem_desc_sw128(b_lo + koff);
+        const uint64_t dah = smem_desc_sw64(a_hi + koff), dal = smem_desc_sw64(a_lo + koff);
+        const uint64_t dbh = smem_desc_sw64(b_hi + koff), dbl = smem_desc_sw64(b_lo + koff);
         const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
         mma_tf32(tmem, dah, dbh, idesc, first);
         mma_tf32(tmem, dah, dbl, idesc, 1u);
@@ -329,46 +338,52 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
           if (p[e]) *p[e] = val[e];
       }
     } else {
-      // Rows are contiguous in memory: stage the FP64 tile in the (now idle) pipeline
-      // buffers, row stride padded by 16 bytes so that the row-per-lane writes are
-      // conflict-free, then let each warp write whole rows with consecutive lanes on
-      // consecutive columns.  The tile needs nt * 1024 + 2048 bytes; the buffers hold
-      // 2 * RAW_BYTES + 4 * A_BYTES + 512 * nt, enough for every nt <= 252.
-      const int ncx = nt / 2;
-      const int sstride = ncx * 16 + 16;
-      for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
-        float v[16];
-        tmem_ld16(tl + c16, v);
-        double2* dst = reinterpret_cast<double2*>(smem + (size_t)r * sstride) + c16 / 2;
+      // Rows are contiguous in memory: stage the FP64 result in the (now idle) pipeline
+      // buffers, at most 80 real columns per pass, row stride padded by 16 bytes so that the
+      // row-per-lane writes are conflict-free; then each warp writes whole rows with
+      // consecutive lanes on consecutive columns.  A pass needs 1024 * pw + 2048 bytes; the
+      // buffers hold 2 * RAW_BYTES + 4 * A_BYTES + 256 * nt = 65536 + 256 * nt, which covers
+      // pw = nt for nt <= 80 and pw = 80 for nt >= 72.
+      const int PW = min(nt, 80);
+      const int sstride = PW * 8 + 16;
+      for (int p0 = 0; p0 < nt; p0 += PW) {
+        const int pw = min(PW, nt - p0);
+        for (int c16 = p0 + 16 * cgrp; c16 < p0 + pw; c16 += 16 * NGRP) {
+          float v[16];
+          tmem_ld16(tl + c16, v);
+          double2* dst = reinterpret_cast<double2*>(smem + (size_t)r * sstride) + (c16 - p0) / 2;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) dst[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
-      }
-      __syncthreads();
-      const int ccount = min(ncx, n - t.n0 / 2);            // complex columns of the block in this tile
-      for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
-        const long long g = row0 + rr;
-        if (g >= nrows) break;
-        if (rowskip) {
-          const long long pl = g / rows_per_plane;
-          if (rowskip[g - pl * rows_per_plane]) continue;
+          for (int e = 0; e < 8; ++e) dst[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
         }
-        const double2* src = reinterpret_cast<const double2*>(smem + (size_t)rr * sstride);
-        double2* dg = out + g * (long long)ncols + b.start + t.n0 / 2;
-        if (store == XS_ACCUM) {
-          for (int c = lane; c < ccount; c += 64) {         // two old values in flight per lane
-            const bool two = c + 32 < ccount;
-            const double2 o0 = dg[c];
-            const double2 o1 = two ? dg[c + 32] : make_double2(0.0, 0.0);
-            const double2 v0 = src[c];
-            dg[c] = make_double2(v0.x + o0.x, v0.y + o0.y);
-            if (two) {
-              const double2 v1 = src[c + 32];
-              dg[c + 32] = make_double2(v1.x + o1.x, v1.y + o1.y);
-            }
+        __syncthreads();
+        const int cbase = (t.n0 + p0) / 2;                   // first complex column of the pass in the block
+        const int ccount = min(pw / 2, n - cbase);
+        for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
+          const long long g = row0 + rr;
+          if (g >= nrows) break;
+          if (rowskip) {
+            const long long pl = g / rows_per_plane;
+            if (rowskip[g - pl * rows_per_plane]) continue;
           }
-        } else {
-          for (int c = lane; c < ccount; c += 32) dg[c] = src[c];
+          const double2* src = reinterpret_cast<const double2*>(smem + (size_t)rr * sstride);
+          double2* dg = out + g * (long long)ncols + b.start + cbase;
+          if (store == XS_ACCUM) {
+            for (int c = lane; c < ccount; c += 64) {       // two old values in flight per lane
+              const bool two = c + 32 < ccount;
+              const double2 o0 = dg[c];
+              const double2 o1 = two ? dg[c + 32] : make_double2(0.0, 0.0);
+              const double2 v0 = src[c];
+              dg[c] = make_double2(v0.x + o0.x, v0.y + o0.y);
+              if (two) {
+                const double2 v1 = src[c + 32];
+                dg[c + 32] = make_double2(v1.x + o1.x, v1.y + o1.y);
+              }
+            }
+          } else {
+            for (int c = lane; c < ccount; c += 32) dg[c] = src[c];
+          }
         }
+        __syncthreads();
       }
     }
   } else if (tid == 0) {
@@ -396,7 +411,7 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
   blk.start = start;
   blk.size = n;
   blk.npad = ((2 * n + 15) / 16) * 16;
-  blk.kpad = ((2 * n + 31) / 32) * 32;
+  blk.kpad = ((2 * n + KCH - 1) / KCH) * KCH;
   blk.toff = (long long)tab.size();
   const size_t plane = (size_t)blk.npad * blk.kpad;
   tab.resize(tab.size() + 2 * plane, 0.0f);
@@ -426,7 +441,9 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
 }
 
 size_t xform_tc_smem(int nt_max) {
-  return 1024 + 2 * RAW_BYTES + 4 * A_BYTES + 4 * (size_t)nt_max * ROWB + 64;
+  // at least 80 KB, so that no more than TC_CTAS_PER_SM CTAs (each holding TMEM_COLS) share an SM
+  const size_t need = 1024 + 2 * RAW_BYTES + 4 * A_BYTES + 4 * (size_t)nt_max * ROWB + 64;
+  return std::max(need, (size_t)80 * 1024);
 }
 
 uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }

@@ -94,87 +94,92 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   }
 }
 
+constexpr int RT = 256, REPT = 2;      // right-hand-side kernels: threads, positions per thread
+
 // Step 6 boundary term, added in place to the block mode right-hand side:
 //   ft[r][k][i][j] += sigma_k (cxl[i] aX[r][k][gxl[i]][j] + cxr[i] aX[r][k][gxr[i]][j]
 //                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
-// One thread per element of a plane (blockIdx.y = r * nz + k); interface positions skipped.
+// REPT positions of a plane per thread (blockIdx.y = r * nz + k); interface positions skipped.
 // LO: the term is formed in FP32 (mixed path) and added to ft in FP64.
 template <bool LO>
-__global__ void __launch_bounds__(128) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
-  // blockIdx.x = (row i, 128-wide column tile); blockIdx.y = plane r * nz + k
+__global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
+  // blockIdx.x: RT * REPT consecutive positions of the plane; blockIdx.y = plane r * nz + k
   const int rk = rk0 + blockIdx.y;
   const int k = rk % a.nz;
-  const int jt = (a.ny + 127) >> 7;
-  const int i = blockIdx.x / jt;
-  const int j = (blockIdx.x - i * jt) * 128 + threadIdx.x;
-  if (j >= a.ny || a.skip_i[i] | a.skip_j[j]) return;
   const long long plane = (long long)a.nx * a.ny;
-  const long long pos = (long long)i * a.ny + j;
-  const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
-  const double2* ax = a.alphaX + (long long)rk * a.nIx * a.ny + j;
-  const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
-  double2* p = ft + (long long)rk * plane + pos;
-  double2 v = *p;
-  if (LO) {
-    float2 g = make_float2(0.f, 0.f);
-    if (pl >= 0) g = cfma32(a.cxl32[i], to_c64(ax[(long long)pl * a.ny]), g);
-    if (pr >= 0) g = cfma32(a.cxr32[i], to_c64(ax[(long long)pr * a.ny]), g);
-    if (ql >= 0) g = cfma32(a.cyl32[j], to_c64(ay[(long long)ql * a.nx]), g);
-    if (qr >= 0) g = cfma32(a.cyr32[j], to_c64(ay[(long long)qr * a.nx]), g);
-    const double2 gd = to_c128(g);
-    if (a.sig) {
+#pragma unroll
+  for (int e = 0; e < REPT; ++e) {
+    const long long pos = ((long long)blockIdx.x * REPT + e) * RT + threadIdx.x;
+    if (pos >= plane) break;
+    const int i = (int)pos / a.ny, j = (int)pos - i * a.ny;          // nx * ny < 2^31
+    if (a.skip_i[i] | a.skip_j[j]) continue;
+    const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
+    const double2* ax = a.alphaX + (long long)rk * a.nIx * a.ny + j;
+    const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
+    double2* p = ft + (long long)rk * plane + pos;
+    double2 v = *p;
+    if (LO) {
+      float2 g = make_float2(0.f, 0.f);
+      if (pl >= 0) g = cfma32(a.cxl32[i], to_c64(ax[(long long)pl * a.ny]), g);
+      if (pr >= 0) g = cfma32(a.cxr32[i], to_c64(ax[(long long)pr * a.ny]), g);
+      if (ql >= 0) g = cfma32(a.cyl32[j], to_c64(ay[(long long)ql * a.nx]), g);
+      if (qr >= 0) g = cfma32(a.cyr32[j], to_c64(ay[(long long)qr * a.nx]), g);
+      const double2 gd = to_c128(g);
+      if (a.sig) {
+        const double s = a.sig[k];
+        v.x = fma(s, gd.x, v.x);
+        v.y = fma(s, gd.y, v.y);
+      } else {
+        v.x += gd.x;
+        v.y += gd.y;
+      }
+    } else if (a.sig) {
+      double2 g = make_double2(0.0, 0.0);
+      if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
+      if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
+      if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
+      if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
       const double s = a.sig[k];
-      v.x = fma(s, gd.x, v.x);
-      v.y = fma(s, gd.y, v.y);
-    } else {
-      v.x += gd.x;
-      v.y += gd.y;
+      v.x = fma(s, g.x, v.x);
+      v.y = fma(s, g.y, v.y);
+    } else {                                     // sigma = 1: accumulate straight into f~
+      if (pl >= 0) v = cfma(a.cxl[i], ax[(long long)pl * a.ny], v);
+      if (pr >= 0) v = cfma(a.cxr[i], ax[(long long)pr * a.ny], v);
+      if (ql >= 0) v = cfma(a.cyl[j], ay[(long long)ql * a.nx], v);
+      if (qr >= 0) v = cfma(a.cyr[j], ay[(long long)qr * a.nx], v);
     }
-  } else if (a.sig) {
-    double2 g = make_double2(0.0, 0.0);
-    if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
-    if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
-    if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
-    if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
-    const double s = a.sig[k];
-    v.x = fma(s, g.x, v.x);
-    v.y = fma(s, g.y, v.y);
-  } else {                                     // sigma = 1: accumulate straight into f~
-    if (pl >= 0) v = cfma(a.cxl[i], ax[(long long)pl * a.ny], v);
-    if (pr >= 0) v = cfma(a.cxr[i], ax[(long long)pr * a.ny], v);
-    if (ql >= 0) v = cfma(a.cyl[j], ay[(long long)ql * a.nx], v);
-    if (qr >= 0) v = cfma(a.cyr[j], ay[(long long)qr * a.nx], v);
+    *p = v;
   }
-  *p = v;
 }
 
 // Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
 //                                              + sum_q Wgy[q][m] bY[r][k][q][l].
 // LO: FP32 arithmetic on the FP64 data (mixed path).
 template <bool LO>
-__global__ void __launch_bounds__(128) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
-                                                         int rk0) {
+__global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
+                                                        int rk0) {
   const int rk = rk0 + blockIdx.y;
-  const int jt = (a.ny + 127) >> 7;
-  const int i = blockIdx.x / jt;
-  const int j = (blockIdx.x - i * jt) * 128 + threadIdx.x;
-  if (j >= a.ny) return;
   const long long plane = (long long)a.nx * a.ny;
-  const long long pos = (long long)i * a.ny + j;
-  const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
-  const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
-  double2 b;
-  if (LO) {
-    float2 g = make_float2(0.f, 0.f);
-    for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64(ax[(long long)p * a.ny]), g);
-    for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64(by[(long long)q * a.nx]), g);
-    b = to_c128(g);
-  } else {
-    b = make_double2(0.0, 0.0);
-    for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
-    for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+#pragma unroll
+  for (int e = 0; e < REPT; ++e) {
+    const long long pos = ((long long)blockIdx.x * REPT + e) * RT + threadIdx.x;
+    if (pos >= plane) break;
+    const int i = (int)pos / a.ny, j = (int)pos - i * a.ny;          // nx * ny < 2^31
+    const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
+    const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
+    double2 b;
+    if (LO) {
+      float2 g = make_float2(0.f, 0.f);
+      for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64(ax[(long long)p * a.ny]), g);
+      for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64(by[(long long)q * a.nx]), g);
+      b = to_c128(g);
+    } else {
+      b = make_double2(0.0, 0.0);
+      for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
+      for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+    }
+    out[(long long)rk * plane + pos] = b;
   }
-  out[(long long)rk * plane + pos] = b;
 }
 
 __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
@@ -239,22 +244,22 @@ void zsolve(const ZSolveArgs& a, cudaStream_t st) {
 
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) {
   const int planes = a.nrhs * a.nz;
-  const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
+  const unsigned gx = (unsigned)(((long long)a.nx * a.ny + RT * REPT - 1) / (RT * REPT));
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    if (a.cxl32) boundary_rhs_kernel<true><<<grid, 128, 0, st>>>(a, ft, rk0);
-    else boundary_rhs_kernel<false><<<grid, 128, 0, st>>>(a, ft, rk0);
+    if (a.cxl32) boundary_rhs_kernel<true><<<grid, RT, 0, st>>>(a, ft, rk0);
+    else boundary_rhs_kernel<false><<<grid, RT, 0, st>>>(a, ft, rk0);
     count_launch();
   }
 }
 
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) {
   const int planes = a.nrhs * a.nz;
-  const unsigned gx = (unsigned)a.nx * (unsigned)((a.ny + 127) / 128);
+  const unsigned gx = (unsigned)(((long long)a.nx * a.ny + RT * REPT - 1) / (RT * REPT));
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    if (a.WgxI32) global_rhs_kernel<true><<<grid, 128, 0, st>>>(a, out, rk0);
-    else global_rhs_kernel<false><<<grid, 128, 0, st>>>(a, out, rk0);
+    if (a.WgxI32) global_rhs_kernel<true><<<grid, RT, 0, st>>>(a, out, rk0);
+    else global_rhs_kernel<false><<<grid, RT, 0, st>>>(a, out, rk0);
     count_launch();
   }
 }
