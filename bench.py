@@ -178,12 +178,13 @@ def profiled_traffic(kernel: str, workload: str, fname: str = "hz_xform.cu"):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(budget_s: float = 12.0, max_runs: int = 3):
+def oracle_sample(budget_s: float = 12.0, max_runs: int = 3, w=None, of: str = "4"):
     """Time the CPU oracle's block solver on 1 RHS of the workload (bounded sample)."""
     import numpy as np
     from oracle import hz_oracle as O
     from paper_1909_01299_gb300 import workloads as W
-    w = W.pml_160x160x128(nrhs=1)
+    if w is None:
+        w = W.pml_160x160x128(nrhs=1)
     P = O.Problem.from_workload(w)
     A, _ = O.assemble(P)
     times = []
@@ -195,7 +196,7 @@ def oracle_sample(budget_s: float = 12.0, max_runs: int = 3):
     res = float(np.max(O.residual(P, u, w.f, A)))
     best = min(times)
     return {"value": w.unknowns / best, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 of 4 RHS of {w.name} through the full 7-step block algorithm, "
+            "sample": f"1 of {of} RHS of {w.name} through the full 7-step block algorithm, "
                       f"{len(times)} run(s), best {best:.2f} s, residual {res:.1e}; BLAS threads = "
                       f"cores, per-mode z solves single-threaded"}, best, w.unknowns
 
@@ -410,8 +411,9 @@ def run_extra(args):
                     batch.info()["launches_per_replay"], "rel_residual_max": float(np.max(rel)),
                     "plan_seconds": plan_s})
     else:
-        w = {"uniform320": W.uniform_320x320x200, "adjoint192": W.adjoint_192x192x128,
-             "uniform32": W.single_block_32, "pml160": W.pml_160x160x128}[args.workload]()
+        gen = {"uniform320": W.uniform_320x320x200, "adjoint192": W.adjoint_192x192x128,
+               "uniform32": W.single_block_32, "pml160": W.pml_160x160x128}[args.workload]
+        w = gen()
         f = torch.from_numpy(w.f).cuda()
         u = torch.empty_like(f)
         plan = hz.Plan.from_workload(w, precision="fp64")
@@ -440,6 +442,9 @@ def run_extra(args):
             torch.cuda.synchronize()
             out["gradient_ms"] = e0.elapsed_time(e1) / args.steps
         out["unit"] = UNIT
+        if not args.no_cpu_baseline:
+            # the oracle on the machine's host cores, one right-hand side of the same workload
+            out["cpu_baseline"] = oracle_sample(budget_s=20.0, max_runs=2, w=gen(1), of=str(w.nrhs))[0]
     print(json.dumps(out), flush=True)
 
 

@@ -29,8 +29,9 @@
  * they are never retained after a call returns.  f == u (in place) is allowed.
  *
  * Errors: every entry point returns an hz_status; nothing is printed and no
- * exception crosses the ABI.  Kernels report a zero/non-finite pivot or a
- * non-finite value through a device status word that the call reads back.
+ * exception crosses the ABI.  Kernels report a singular pivot (zero, non-finite, or
+ * at the rounding level of the terms that formed it) or a non-finite value through a
+ * device status word that the call reads back.
  */
 #ifndef HZ_H_
 #define HZ_H_
@@ -45,7 +46,8 @@ typedef enum {
   HZ_OK = 0,
   HZ_ERR_ARG = 1,            /* bad size, pointer or option                            */
   HZ_ERR_EIG = 2,            /* a 1D eigen-decomposition failed its identity checks    */
-  HZ_ERR_SINGULAR = 3,       /* zero or non-finite pivot in a z tridiagonal            */
+  HZ_ERR_SINGULAR = 3,       /* singular pivot in a z tridiagonal: zero, non-finite, or
+                                |d| <= 64 eps (sum of the magnitudes that formed d)     */
   HZ_ERR_NONFINITE = 4,      /* non-finite value in the input or the result            */
   HZ_ERR_NOT_CONVERGED = 5,  /* mixed path: refinement did not reach rtol              */
   HZ_ERR_OOM = 6,            /* device allocation failed                               */
@@ -130,7 +132,7 @@ hz_status hz_get_stage_times(hz_plan_t plan, double *ms, long long *launches);
  * (K_d W = M_d W Lambda, W^T M_d W = I; the display after Eq. (fdmtrprj) and
  * before Eq. (fdmtrprjfrerr)), the z elimination factors of every mode, and all
  * device tables.  Errors: HZ_ERR_ARG on bad sizes/pointers, HZ_ERR_EIG when an
- * eigen-decomposition fails its checks, HZ_ERR_SINGULAR on a zero pivot,
+ * eigen-decomposition fails its checks, HZ_ERR_SINGULAR on a singular pivot,
  * HZ_ERR_OOM / HZ_ERR_CUDA on device failures.  *out is NULL on error. */
 hz_status hz_plan_create(const hz_grid *grid, const hz_layers *layers, const hz_blocks *blocks,
                          const hz_options *opts, hz_plan_t *out);

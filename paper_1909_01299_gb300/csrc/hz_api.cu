@@ -34,8 +34,9 @@ struct AxisPlan {
   std::vector<int> bstart, bsize, iface;
   std::vector<std::vector<cd>> blam, bW;     // per block eigenpairs (W row-major [node][mode])
   std::vector<int> breal;
+  std::vector<int> bsym;                     // uniform block: sine pairs, symmetric modes first
   std::vector<cd> glam, gW;                  // whole-axis eigenpairs (when the plan needs them)
-  int greal = 0;
+  int greal = 0, gsym = 0;
   double eig_res = 0.0;
 };
 
@@ -214,6 +215,17 @@ bool finite(cd z) { return std::isfinite(z.real()) && std::isfinite(z.imag()); }
 // ---------------------------------------------------------------------------
 // Plan construction
 // ---------------------------------------------------------------------------
+// True when the sz + 1 steps h[s .. s + sz] that touch the nodes s .. s + sz - 1 are all
+// equal, real and positive: that block's pencil has the closed-form sine pairs.
+bool uniform_steps(const std::vector<cd>& h, int s, int sz, double* hu) {
+  const cd h0 = h[s];
+  if (h0.imag() != 0.0 || !(h0.real() > 0.0)) return false;
+  for (int i = s; i <= s + sz; ++i)
+    if (h[i] != h0) return false;
+  *hu = h0.real();
+  return true;
+}
+
 hz_status build_axis(AxisPlan& A, int n, const hz_c128* h, int nb, const int* ifc) {
   A.n = n;
   A.nb = nb;
@@ -246,12 +258,19 @@ hz_status build_axis(AxisPlan& A, int n, const hz_c128* h, int nb, const int* if
   A.blam.assign(nb, {});
   A.bW.assign(nb, {});
   A.breal.assign(nb, 1);
+  A.bsym.assign(nb, 0);
   A.eig_res = 0.0;
   for (int b = 0; b < nb; ++b) {
     const int s = A.bstart[b], sz = A.bsize[b];
     double res = 0.0;
-    if (!hz::tridiag_eig(sz, &A.kd[s], sz > 1 ? &A.ko[s] : nullptr, &A.mh[s], A.blam[b], A.bW[b], &res))
-      return HZ_ERR_EIG;
+    double hu = 0.0;
+    A.bsym[b] = uniform_steps(A.h, s, sz, &hu) ? 1 : 0;
+    const bool ok = A.bsym[b]
+                        ? hz::sine_eig(sz, hu, &A.kd[s], sz > 1 ? &A.ko[s] : nullptr, &A.mh[s], A.blam[b],
+                                       A.bW[b], &res)
+                        : hz::tridiag_eig(sz, &A.kd[s], sz > 1 ? &A.ko[s] : nullptr, &A.mh[s], A.blam[b],
+                                          A.bW[b], &res);
+    if (!ok) return HZ_ERR_EIG;
     A.eig_res = std::max(A.eig_res, res);
     for (const cd& w : A.bW[b])
       if (w.imag() != 0.0) { A.breal[b] = 0; break; }
@@ -264,10 +283,16 @@ hz_status build_global(AxisPlan& A) {
     A.glam = A.blam[0];
     A.gW = A.bW[0];
     A.greal = A.breal[0];
+    A.gsym = A.bsym[0];
     return HZ_OK;
   }
   double res = 0.0;
-  if (!hz::tridiag_eig(A.n, A.kd.data(), A.ko.data(), A.mh.data(), A.glam, A.gW, &res)) return HZ_ERR_EIG;
+  double hu = 0.0;
+  A.gsym = uniform_steps(A.h, 0, A.n, &hu) ? 1 : 0;
+  const bool ok = A.gsym
+                      ? hz::sine_eig(A.n, hu, A.kd.data(), A.ko.data(), A.mh.data(), A.glam, A.gW, &res)
+                      : hz::tridiag_eig(A.n, A.kd.data(), A.ko.data(), A.mh.data(), A.glam, A.gW, &res);
+  if (!ok) return HZ_ERR_EIG;
   A.eig_res = std::max(A.eig_res, res);
   A.greal = 1;
   for (const cd& w : A.gW)
@@ -277,8 +302,12 @@ hz_status build_global(AxisPlan& A) {
 
 // Pack a block-diagonal transform: tab(b)[a][c] = get(b, a, c).
 template <typename Get>
+// sym[b] marks a uniform block (sine pairs, symmetric modes first); dir = 1 for a forward
+// table (rows = nodes), 2 for an inverse table (rows = modes).  The table is stored whole
+// either way; symmetric blocks read half of it (see the row-transform kernels).
 void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>& start,
-                const std::vector<int>& size, const std::vector<int>& real, Get get) {
+                const std::vector<int>& size, const std::vector<int>& real, const std::vector<int>& sym,
+                int dir, Get get) {
   xs.ncols = ncols;
   xs.nblocks = (int)start.size();
   std::vector<hz::XBlock> blocks;
@@ -291,6 +320,8 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
     xb.start = start[b];
     xb.size = n;
     xb.real = real[b];
+    xb.sym = (sym[b] && real[b]) ? dir : 0;
+    xb.ns = (n + 1) / 2;
     xb.toff = (long long)t64.size();
     xb.toff32 = (long long)t32.size();
     const size_t nn = (size_t)n * n;
@@ -318,7 +349,9 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
         }
     }
     blocks.push_back(xb);
-    for (int c0 = 0; c0 < n; c0 += kTileN) tiles.push_back(hz::XTile{b, c0, std::min(kTileN, n - c0), 0});
+    // inverse tables of symmetric blocks produce two nodes per column: tiles cover the first ns
+    const int ncov = xb.sym == 2 ? xb.ns : n;
+    for (int c0 = 0; c0 < ncov; c0 += kTileN) tiles.push_back(hz::XTile{b, c0, std::min(kTileN, ncov - c0), 0});
   }
   xs.ntiles = (int)tiles.size();
   xs.h_blocks = blocks;
@@ -358,10 +391,10 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
   });
   make_tc(p, D.tinv, n, A.bstart, A.bsize,
           [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
-  make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, [&](int b, int a, int c) {
+  make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, A.bsym, 1, [&](int b, int a, int c) {
     return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
   });
-  make_xform(p, D.inv, n, A.bstart, A.bsize, A.breal,
+  make_xform(p, D.inv, n, A.bstart, A.bsize, A.breal, A.bsym, 2,
              [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
   std::vector<cd> lam_b(n, cd(0)), lam_g(n, cd(0));
   std::vector<signed char> skip(n, 0);
@@ -369,9 +402,9 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
   for (int b = 0; b < A.nb; ++b)
     for (int a = 0; a < A.bsize[b]; ++a) lam_b[A.bstart[b] + a] = A.blam[b][a];
   if (need_global) {
-    std::vector<int> s0{0}, sn{n}, gr{A.greal};
-    make_xform(p, D.gfwd, n, s0, sn, gr, [&](int, int a, int c) { return A.gW[(size_t)a * n + c]; });
-    make_xform(p, D.ginv, n, s0, sn, gr, [&](int, int a, int c) { return A.gW[(size_t)c * n + a]; });
+    std::vector<int> s0{0}, sn{n}, gr{A.greal}, gs{A.gsym};
+    make_xform(p, D.gfwd, n, s0, sn, gr, gs, 1, [&](int, int a, int c) { return A.gW[(size_t)a * n + c]; });
+    make_xform(p, D.ginv, n, s0, sn, gr, gs, 2, [&](int, int a, int c) { return A.gW[(size_t)c * n + a]; });
     lam_g = A.glam;
   }
   D.lam_b = upload_c(p, lam_b);
@@ -678,11 +711,15 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   };
   auto crows = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
     const int2* rng = edge ? d.edge_rng : d.grng;
+    // FP32: one pass over V for all slots; FP64 stays per slot (bound by the FP64 pipe, where
+    // one pass saves no work but gives fewer threads)
+    if (!edge && lo && hz::contract_all(true, V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
     if (lo) hz::contract_rows(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
     else hz::contract_rows(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
   };
   auto ccols = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
     const int2* rng = edge ? d.edge_rng : d.grng;
+    if (!edge && lo && hz::contract_all(false, V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
     if (lo) hz::contract_cols(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
     else hz::contract_cols(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
   };
@@ -737,11 +774,11 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     ga.nx = nx; ga.ny = ny; ga.nz = nz; ga.nrhs = R; ga.nIx = nIx; ga.nIy = nIy;
     ga.aX = w.aX; ga.bY = w.bY; ga.WgxI = p->dx.gcoef; ga.WgyI = p->dy.gcoef;
     if (lo) { ga.WgxI32 = p->dx.gcoef32; ga.WgyI32 = p->dy.gcoef32; }
-    hz::global_rhs(ga, w.G, st);                    // r~ (G is free until step 7)
     hz::ZSolveArgs zg = za;
     zg.skip_i = nullptr; zg.skip_j = nullptr;
     zg.rhs = w.G; zg.out = w.V;                     // w~ (v~ in V is no longer needed)
     zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
+    hz::global_rhs(ga, w.G, st);                    // r~ (G is free until step 7)
     hz::zsolve(zg, st);
     fork(p, st);
     if (nIx) {

@@ -112,7 +112,16 @@ bool tridiag_eig(int n, const cd* kd, const cd* ko, const cd* m, std::vector<cd>
     lam[col] = d[src];
     for (int i = 0; i < n; ++i) W[(size_t)i * n + col] = Z[(size_t)i * n + src] / sm[i];
   }
-  // Checks: ||K W - M W Lambda||_F / (||K||_F ||W||_F) and ||W^T M W - I||_F / n.
+  const double res = eig_check(n, kd, ko, m, lam, W);
+  if (eig_residual) *eig_residual = res;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(lam[i].real()) || !std::isfinite(lam[i].imag())) return false;
+  return true;
+}
+
+// max(||K W - M W Lambda||_F / (||K||_F ||W||_F), max |W^T M W - I|).
+double eig_check(int n, const cd* kd, const cd* ko, const cd* m, const std::vector<cd>& lam,
+                 const std::vector<cd>& W) {
   double rk = 0, nk = 0, nw = 0, orth = 0;
   for (int i = 0; i < n; ++i) {
     nk += std::norm(kd[i]) + (i + 1 < n ? 2.0 * std::norm(ko[i]) : 0.0);
@@ -131,10 +140,35 @@ bool tridiag_eig(int n, const cd* kd, const cd* ko, const cd* m, std::vector<cd>
       const double dev = std::abs(g - (a == b ? cd(1.0) : cd(0.0)));
       orth = std::max(orth, dev);
     }
-  const double res = std::sqrt(rk) / (std::sqrt(nk) * std::sqrt(nw));
-  if (eig_residual) *eig_residual = std::max(res, orth);
-  for (int i = 0; i < n; ++i)
-    if (!std::isfinite(lam[i].real()) || !std::isfinite(lam[i].imag())) return false;
+  return std::max(std::sqrt(rk) / (std::sqrt(nk) * std::sqrt(nw)), orth);
+}
+
+// Uniform real block (n nodes, all n + 1 steps equal to h > 0): K = tridiag(-1, 2, -1) / h and
+// M = h I have the discrete sine eigenpairs
+//   lambda_m = (4 / h^2) sin^2(m pi / (2 (n + 1))),  w_m[i] = sqrt(2 / ((n + 1) h)) sin((i + 1) m pi / (n + 1)),
+// m = 1..n, with W^T M W = I.  w_m is symmetric under i -> n - 1 - i for odd m and
+// antisymmetric for even m; the columns hold the odd m first (column l < (n + 1) / 2 is
+// m = 2 l + 1), then the even m, which the row transforms use to halve their work.
+bool sine_eig(int n, double h, const cd* kd, const cd* ko, const cd* m, std::vector<cd>& lam,
+              std::vector<cd>& W, double* eig_residual) {
+  if (n < 1 || !(h > 0.0)) return false;
+  const double pi = 3.14159265358979323846;
+  const double L = n + 1.0;
+  const double c = std::sqrt(2.0 / (L * h));
+  lam.assign(n, cd(0));
+  W.assign((size_t)n * n, cd(0));
+  const int ns = (n + 1) / 2;
+  for (int col = 0; col < n; ++col) {
+    const int mm = col < ns ? 2 * col + 1 : 2 * (col - ns) + 2;
+    const double sn = std::sin(mm * pi / (2.0 * L));
+    lam[col] = cd(4.0 / (h * h) * sn * sn, 0.0);
+    for (int i = 0; i < n; ++i) {
+      const long long arg = (long long)(i + 1) * mm % (2 * (n + 1));   // exact reduction mod 2 pi
+      W[(size_t)i * n + col] = cd(c * std::sin((double)arg * pi / L), 0.0);
+    }
+  }
+  const double res = eig_check(n, kd, ko, m, lam, W);
+  if (eig_residual) *eig_residual = res;
   return true;
 }
 

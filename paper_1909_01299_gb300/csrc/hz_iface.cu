@@ -55,13 +55,19 @@ __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __r
   }
 }
 
+// FP64: one thread per output (plane, slot, row i) walking its row (the loads of a warp hit
+// 32 rows; every line is reused from L1 by the next iterations).  FP32: one warp per
+// output, lanes reading the row's range coalesced, then a shuffle reduction in fixed order.
 template <typename C>
 __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __restrict__ out,
                                      const C* __restrict__ coef, const int2* __restrict__ range,
                                      int nrows, int ncols, int nslots, long long nplanes) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  constexpr bool F64 = sizeof(C) == sizeof(double2);
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long t = F64 ? gt : gt >> 5;
+  const int lane = F64 ? 0 : (int)(threadIdx.x & 31);
   const long long total = nplanes * nslots * (long long)nrows;
-  if (t >= total) return;
+  if (t >= total) return;                                  // warp-uniform in the FP32 variant
   const int i = (int)(t % nrows);
   const long long ps = t / nrows;
   const int s = (int)(ps % nslots);
@@ -69,14 +75,76 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
   const int2 rg = range[s];
   const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
   const C* __restrict__ c = coef + (long long)s * ncols;
-  if constexpr (sizeof(C) == sizeof(double2)) {
+  if constexpr (F64) {
     double2 acc = make_double2(0.0, 0.0);
     for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
     out[t] = acc;
   } else {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int j = rg.x; j < rg.y; ++j) acc = cfma32(c[j], to_c64(v[j]), acc);
-    out[t] = to_c128(acc);
+    float2 a32 = make_float2(0.f, 0.f);
+    for (int j = rg.x + lane; j < rg.y; j += 32) a32 = cfma32(c[j], to_c64(v[j]), a32);
+    for (int o = 16; o > 0; o >>= 1) {
+      a32.x += __shfl_down_sync(0xffffffffu, a32.x, o);
+      a32.y += __shfl_down_sync(0xffffffffu, a32.y, o);
+    }
+    if (lane == 0) out[t] = to_c128(a32);
+  }
+}
+
+// Step 5 on the mixed path with several interfaces per axis: every slot contracts the
+// whole row or column (the whole-axis eigenvector rows), so one pass over V accumulates all
+// nslots sums (nslots <= kMultiSlots) in FP32 instead of reading V once per slot.
+constexpr int kMultiSlots = 8;
+
+__global__ void contract_rows_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+                                           const float2* __restrict__ coef, int nrows, int ncols, int nslots,
+                                           long long nplanes) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nplanes * (long long)ncols) return;
+  const int j = (int)(t % ncols);
+  const long long plane = t / ncols;
+  const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
+  float2 acc[kMultiSlots];
+#pragma unroll
+  for (int q = 0; q < kMultiSlots; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int i = 0; i < nrows; ++i) {
+    const float2 x = to_c64(v[(long long)i * ncols]);
+#pragma unroll
+    for (int q = 0; q < kMultiSlots; ++q)
+      if (q < nslots) acc[q] = cfma32(coef[(long long)q * nrows + i], x, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < kMultiSlots; ++q)
+    if (q < nslots) out[(plane * nslots + q) * (long long)ncols + j] = to_c128(acc[q]);
+}
+
+// One warp per (plane, row i): lanes stride over the row, then a shuffle reduction per slot.
+__global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+                                           const float2* __restrict__ coef, int nrows, int ncols, int nslots,
+                                           long long nplanes) {
+  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= nplanes * (long long)nrows) return;             // warp-uniform
+  const int i = (int)(t % nrows);
+  const long long plane = t / nrows;
+  const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
+  float2 acc[kMultiSlots];
+#pragma unroll
+  for (int q = 0; q < kMultiSlots; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int j = lane; j < ncols; j += 32) {
+    const float2 x = to_c64(v[j]);
+#pragma unroll
+    for (int q = 0; q < kMultiSlots; ++q)
+      if (q < nslots) acc[q] = cfma32(coef[(long long)q * ncols + j], x, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < kMultiSlots; ++q) {
+    if (q < nslots) {
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+        acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
+      }
+      if (lane == 0) out[(plane * nslots + q) * (long long)nrows + i] = to_c128(acc[q]);
+    }
   }
 }
 
@@ -370,8 +438,27 @@ void contract_cols_t(const double2* V, double2* out, const C* coef, const int2* 
                      int nslots, long long nplanes, cudaStream_t st) {
   const long long n = nplanes * nslots * (long long)nrows;
   if (n == 0) return;
-  contract_cols_kernel<C><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  const long long threads = sizeof(C) == sizeof(double2) ? n : n * 32;   // FP32: one warp per output
+  contract_cols_kernel<C><<<blocks_for(threads, 256), 256, 0, st>>>(V, out, coef, range, nrows, ncols, nslots,
+                                                                   nplanes);
   count_launch();
+}
+
+bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st) {
+  if (nslots < 2 || nslots > kMultiSlots) return false;
+  if (rows) {
+    const long long n = nplanes * (long long)ncols;
+    if (n == 0) return true;
+    contract_rows_multi_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, nrows, ncols, nslots, nplanes);
+  } else {
+    const long long n = nplanes * (long long)nrows;
+    if (n == 0) return true;
+    contract_cols_multi_kernel<<<blocks_for(n * 32, 256), 256, 0, st>>>(V, out, coef, nrows, ncols, nslots,
+                                                                       nplanes);
+  }
+  count_launch();
+  return true;
 }
 
 void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,

@@ -23,6 +23,13 @@ long long launch_count();
 // (W[i*n + l] = component at node i of mode l).  Returns false on failure.
 bool tridiag_eig(int n, const cd* kd, const cd* ko, const cd* m, std::vector<cd>& lam,
                  std::vector<cd>& W, double* eig_residual);
+// Closed-form pairs of a uniform real block (every step equal to h): the discrete sine
+// transform.  kd, ko, m are the block's pencil, used only for the residual check.
+bool sine_eig(int n, double h, const cd* kd, const cd* ko, const cd* m, std::vector<cd>& lam,
+              std::vector<cd>& W, double* eig_residual);
+// max(||K W - M W Lambda||_F / (||K||_F ||W||_F), max |W^T M W - I|) of a computed pencil.
+double eig_check(int n, const cd* kd, const cd* ko, const cd* m, const std::vector<cd>& lam,
+                 const std::vector<cd>& W);
 
 // ---------------------------------------------------------------------------
 // Row transforms: out_row[s + c] = sum_a in_row[s + a] * B_b[a][c] for every block b
@@ -32,6 +39,10 @@ struct XBlock {
   int start;            // first column of the block in the row
   int size;             // block width n
   int real;             // 1: table is real (one n*n plane); 0: complex
+  int sym;              // mirror-symmetric real block (uniform steps, sine eigenvectors with the
+                        //   ns = (n + 1) / 2 symmetric modes first): 1 = forward table (rows =
+                        //   nodes, folded), 2 = inverse table (rows = modes, outputs unfolded)
+  int ns;               // number of symmetric modes when sym != 0
   int pad;
   long long toff;       // offset (doubles) of the FP64 table; complex entries c + i d are
                         //    stored for the 3M product as three planes [c | d - c | c + d]
@@ -161,6 +172,7 @@ struct GlobalRhsArgs {
 };
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
 
+
 // Elimination factors of (Tz + s_ij S_z) for every (i, j) with s_ij = lamx[i] + lamy[j]
 // (no pivoting).  fold (may be NULL) scales P by fold[k] (the M_z of the right-hand side).
 void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,
@@ -177,6 +189,11 @@ void contract_rows(const double2* V, double2* out, const double2* coef, const in
 // out[plane][s][i] = sum_{j in [lo_s, hi_s)} coef[s][j] V[plane][i][j]  (contraction within rows)
 void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+// Contractions whose every slot covers the whole row (rows = true: over i, out[plane][s][j];
+// false: over j, out[plane][s][i]) in one pass over V; false (nothing launched) unless
+// 2 <= nslots <= 8.  FP32 arithmetic (mixed path).
+bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st);
 // The same contractions with FP32 arithmetic on the FP64 data (mixed path).
 void contract_rows(const double2* V, double2* out, const float2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);

@@ -180,14 +180,176 @@ __device__ __forceinline__ void run_tile(const double2* __restrict__ in, double2
   }
 }
 
+// Mirror-symmetric real blocks (uniform steps): the eigenvectors are the discrete sines,
+// mode m (1-based) symmetric under i -> n-1-i for odd m and antisymmetric for even m, and
+// the plan stores the ns = (n + 1) / 2 symmetric modes first.  Forward (sym = 1): column c
+// needs only the folded data x_a + x_{n-1-a} (c < ns) or x_a - x_{n-1-a} (c >= ns) over
+// the first ns nodes, so the contraction is half as long.  Inverse (sym = 2): the tile
+// covers the first ns nodes a; S_a sums the symmetric modes, D_a the antisymmetric ones,
+// and the two outputs are x_a = S_a + D_a and x_{n-1-a} = S_a - D_a.  Either way a block
+// costs about n^2 / 2 multiply-adds per row instead of n^2.
+template <typename Acc, int TM>
+struct SymTile {
+  Acc a[2][2][TK][TM];       // [folded sum | difference][re | im][k][row] (inverse: plane 0 only)
+  Acc b[TK][TN];
+};
+
+template <typename Acc, int TM>
+__device__ __forceinline__ void run_tile_sym(const double2* __restrict__ in, double2* __restrict__ out,
+                                             const Acc* __restrict__ tab, const XBlock& b, const XTile& t,
+                                             long long nrows, int rows_per_plane, int ncols, long long row0,
+                                             int trans, int store, int conj_out,
+                                             const signed char* __restrict__ rowskip, char* smem_raw) {
+  constexpr int RPT = TM / 16;
+  constexpr int EPT = TM * TK / NT;
+  SymTile<Acc, TM>& sm = *reinterpret_cast<SymTile<Acc, TM>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int n = b.size, ns = b.ns;
+  const bool fwd = b.sym == 1;
+  const int cls = (fwd && t.c0 + tx >= ns) ? 1 : 0;        // forward: which folded plane column tx uses
+
+  Acc sacc[RPT][2], dacc[RPT][2];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) sacc[r][0] = sacc[r][1] = dacc[r][0] = dacc[r][1] = Acc(0);
+
+  const int la_row = tid / (TK / EPT), la_k = (tid % (TK / EPT)) * EPT;
+  const int lb_k = tid >> 4, lb_c = tid & 15;
+  const long long arow = row0 + la_row;
+  const bool arow_ok = arow < nrows;
+  const double2* __restrict__ ain = in + arow * (long long)ncols + b.start;
+  const int klen = fwd ? ns : n;                           // contraction length
+  for (int k0 = 0; k0 < klen; k0 += TK) {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int kk = la_k + e;
+      const int a = k0 + kk;
+      double2 v = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
+      if (arow_ok && a < klen) {
+        v = ain[a];
+        if (fwd && n - 1 - a != a) w = ain[n - 1 - a];
+      }
+      const Acc vx = to_acc<Acc>(v.x), vy = to_acc<Acc>(v.y);
+      if (fwd) {
+        const Acc wx = to_acc<Acc>(w.x), wy = to_acc<Acc>(w.y);
+        sm.a[0][0][kk][la_row] = vx + wx;
+        sm.a[0][1][kk][la_row] = vy + wy;
+        sm.a[1][0][kk][la_row] = vx - wx;
+        sm.a[1][1][kk][la_row] = vy - wy;
+      } else {
+        sm.a[0][0][kk][la_row] = vx;
+        sm.a[0][1][kk][la_row] = vy;
+      }
+    }
+    {
+      const int a = k0 + lb_k;
+      sm.b[lb_k][lb_c] = (a < klen && lb_c < t.cw) ? tab[(long long)a * n + t.c0 + lb_c] : Acc(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      const Acc bv = sm.b[kk][tx];
+      if (fwd || k0 + kk < ns) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          sacc[r][0] = fma(sm.a[cls][0][kk][ty + 16 * r], bv, sacc[r][0]);
+          sacc[r][1] = fma(sm.a[cls][1][kk][ty + 16 * r], bv, sacc[r][1]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          dacc[r][0] = fma(sm.a[0][0][kk][ty + 16 * r], bv, dacc[r][0]);
+          dacc[r][1] = fma(sm.a[0][1][kk][ty + 16 * r], bv, dacc[r][1]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // result columns: forward -> mode c0 + tx; inverse -> node c0 + tx (S + D) and its mirror (S - D)
+  double2 rp[RPT], rm[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const double sr = from_acc(sacc[r][0]), si = from_acc(sacc[r][1]);
+    const double dr = from_acc(dacc[r][0]), di = from_acc(dacc[r][1]);
+    rp[r] = make_double2(sr + dr, conj_out ? -(si + di) : si + di);
+    rm[r] = make_double2(sr - dr, conj_out ? -(si - di) : si - di);
+  }
+  const int col = t.c0 + tx;                               // within the block
+  const int mir = n - 1 - col;
+  const bool has_mir = !fwd && mir != col;
+
+  if (!trans) {
+    if (tx >= t.cw) return;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const long long row = row0 + ty + 16 * r;
+      if (row >= nrows) continue;
+      if (rowskip && rowskip[row % rows_per_plane]) continue;
+      double2* p = out + row * (long long)ncols + b.start;
+      if (store == XS_ACCUM) {
+        double2 o = p[col];
+        o.x += rp[r].x;
+        o.y += rp[r].y;
+        p[col] = o;
+        if (has_mir) {
+          double2 q = p[mir];
+          q.x += rm[r].x;
+          q.y += rm[r].y;
+          p[mir] = q;
+        }
+      } else {
+        p[col] = rp[r];
+        if (has_mir) p[mir] = rm[r];
+      }
+    }
+  } else {
+    // stage [node tile | mirrored tile] and write it transposed: out[plane][col][row]
+    double2 (*os)[TM + 1] = reinterpret_cast<double2 (*)[TM + 1]>(smem_raw);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      os[tx][ty + 16 * r] = rp[r];
+      os[TN + tx][ty + 16 * r] = rm[r];
+    }
+    __syncthreads();
+    const int wr = tid & (TM - 1);
+    const long long row = row0 + wr;
+    if (row >= nrows) return;
+    const long long plane = row / rows_per_plane;
+    const int rip = (int)(row - plane * rows_per_plane);
+    if (rowskip && rowskip[rip]) return;
+    double2* base = out + plane * (long long)ncols * rows_per_plane + rip;
+    const int ncol_st = fwd ? TN : 2 * TN;
+    for (int cc = tid / TM; cc < ncol_st; cc += NT / TM) {
+      const int ct = cc & (TN - 1);
+      if (ct >= t.cw) continue;
+      int c = t.c0 + ct;
+      if (cc >= TN) {
+        if (n - 1 - c == c) continue;                      // the middle node has no mirror
+        c = n - 1 - c;
+      }
+      double2* p = base + (long long)(b.start + c) * rows_per_plane;
+      if (store == XS_ACCUM) {
+        double2 o = *p;
+        o.x += os[cc][wr].x;
+        o.y += os[cc][wr].y;
+        *p = o;
+      } else {
+        *p = os[cc][wr];
+      }
+    }
+  }
+}
+
 template <typename Acc, int TM>
 __global__ void __launch_bounds__(NT)
 xform_kernel(const double2* __restrict__ in, double2* __restrict__ out, const Acc* __restrict__ tab,
              const XBlock* __restrict__ blocks, const XTile* __restrict__ tiles, int ntiles, long long nrows,
              int rows_per_plane, int ncols, int trans, int store, int conj_out,
              const signed char* __restrict__ rowskip) {
-  constexpr int SA = sizeof(Tile<Acc, false, TM>) > sizeof(double2) * TN * (TM + 1)
-                         ? sizeof(Tile<Acc, false, TM>) : sizeof(double2) * TN * (TM + 1);
+  constexpr int S1 = sizeof(Tile<Acc, false, TM>), S2 = sizeof(SymTile<Acc, TM>);
+  constexpr int S3 = sizeof(double2) * 2 * TN * (TM + 1);      // transposed-store staging
+  constexpr int SA = S1 > S2 ? (S1 > S3 ? S1 : S3) : (S2 > S3 ? S2 : S3);
   __shared__ __align__(16) char smem[SA];
   // column tiles of one row tile are consecutive CTAs, so the row tile is read from
   // DRAM once and re-read from L2 by the other column tiles
@@ -196,7 +358,10 @@ xform_kernel(const double2* __restrict__ in, double2* __restrict__ out, const Ac
   const XBlock b = blocks[t.blk];
   const long long row0 = (cta / ntiles) * TM;
   const Acc* tb = tab + (sizeof(Acc) == 8 ? b.toff : b.toff32);
-  if (b.real)
+  if (b.sym)
+    run_tile_sym<Acc, TM>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out, rowskip,
+                          smem);
+  else if (b.real)
     run_tile<Acc, true, TM>(in, out, tb, b, t, nrows, rows_per_plane, ncols, row0, trans, store, conj_out,
                             rowskip, smem);
   else

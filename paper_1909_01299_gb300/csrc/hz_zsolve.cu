@@ -94,30 +94,39 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   }
 }
 
-constexpr int RT = 256, REPT = 2;      // right-hand-side kernels: threads, positions per thread
+constexpr int RT = 256, REPT = 4;      // right-hand-side kernels: threads, positions per thread
+
+// The right-hand-side kernels below first compute all REPT values of a thread and only
+// then store them: the interface arrays are reached through plain struct pointers, so the
+// compiler may not move the next position's loads above a store.
 
 // Step 6 boundary term, added in place to the block mode right-hand side:
 //   ft[r][k][i][j] += sigma_k (cxl[i] aX[r][k][gxl[i]][j] + cxr[i] aX[r][k][gxr[i]][j]
 //                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
-// REPT positions of a plane per thread (blockIdx.y = r * nz + k); interface positions skipped.
+// REPT positions of a plane per thread, RT * REPT consecutive positions per CTA
+// (blockIdx.y = r * nz + k); interface positions are skipped.
 // LO: the term is formed in FP32 (mixed path) and added to ft in FP64.
 template <bool LO>
 __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
-  // blockIdx.x: RT * REPT consecutive positions of the plane; blockIdx.y = plane r * nz + k
   const int rk = rk0 + blockIdx.y;
   const int k = rk % a.nz;
-  const long long plane = (long long)a.nx * a.ny;
+  const int plane = a.nx * a.ny;                           // < 2^31 (checked at plan creation)
+  const double s = a.sig ? a.sig[k] : 1.0;
+  const double2* __restrict__ axp = a.alphaX + (long long)rk * a.nIx * a.ny;
+  const double2* __restrict__ ayp = a.alphaY + (long long)rk * a.nIy * a.nx;
+  double2* __restrict__ ftp = ft + (long long)rk * plane;
+  double2 val[REPT];
+  bool ok[REPT];
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
-    const long long pos = ((long long)blockIdx.x * REPT + e) * RT + threadIdx.x;
-    if (pos >= plane) break;
-    const int i = (int)pos / a.ny, j = (int)pos - i * a.ny;          // nx * ny < 2^31
-    if (a.skip_i[i] | a.skip_j[j]) continue;
+    const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
+    const int i = pos / a.ny, j = pos - i * a.ny;
+    ok[e] = pos < plane && !(a.skip_i[i] | a.skip_j[j]);
+    if (!ok[e]) continue;
     const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
-    const double2* ax = a.alphaX + (long long)rk * a.nIx * a.ny + j;
-    const double2* ay = a.alphaY + (long long)rk * a.nIy * a.nx + i;
-    double2* p = ft + (long long)rk * plane + pos;
-    double2 v = *p;
+    const double2* ax = axp + j;
+    const double2* ay = ayp + i;
+    double2 v = ftp[pos];
     if (LO) {
       float2 g = make_float2(0.f, 0.f);
       if (pl >= 0) g = cfma32(a.cxl32[i], to_c64(ax[(long long)pl * a.ny]), g);
@@ -125,31 +134,27 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
       if (ql >= 0) g = cfma32(a.cyl32[j], to_c64(ay[(long long)ql * a.nx]), g);
       if (qr >= 0) g = cfma32(a.cyr32[j], to_c64(ay[(long long)qr * a.nx]), g);
       const double2 gd = to_c128(g);
-      if (a.sig) {
-        const double s = a.sig[k];
-        v.x = fma(s, gd.x, v.x);
-        v.y = fma(s, gd.y, v.y);
-      } else {
-        v.x += gd.x;
-        v.y += gd.y;
-      }
-    } else if (a.sig) {
+      v.x = fma(s, gd.x, v.x);
+      v.y = fma(s, gd.y, v.y);
+    } else {
       double2 g = make_double2(0.0, 0.0);
       if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
       if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
       if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
       if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
-      const double s = a.sig[k];
-      v.x = fma(s, g.x, v.x);
-      v.y = fma(s, g.y, v.y);
-    } else {                                     // sigma = 1: accumulate straight into f~
-      if (pl >= 0) v = cfma(a.cxl[i], ax[(long long)pl * a.ny], v);
-      if (pr >= 0) v = cfma(a.cxr[i], ax[(long long)pr * a.ny], v);
-      if (ql >= 0) v = cfma(a.cyl[j], ay[(long long)ql * a.nx], v);
-      if (qr >= 0) v = cfma(a.cyr[j], ay[(long long)qr * a.nx], v);
+      if (a.sig) {
+        v.x = fma(s, g.x, v.x);
+        v.y = fma(s, g.y, v.y);
+      } else {
+        v.x += g.x;
+        v.y += g.y;
+      }
     }
-    *p = v;
+    val[e] = v;
   }
+#pragma unroll
+  for (int e = 0; e < REPT; ++e)
+    if (ok[e]) ftp[((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x] = val[e];
 }
 
 // Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
@@ -159,26 +164,34 @@ template <bool LO>
 __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
                                                         int rk0) {
   const int rk = rk0 + blockIdx.y;
-  const long long plane = (long long)a.nx * a.ny;
+  const int plane = a.nx * a.ny;
+  const double2* __restrict__ axp = a.aX + (long long)rk * a.nIx * a.ny;
+  const double2* __restrict__ byp = a.bY + (long long)rk * a.nIy * a.nx;
+  double2* __restrict__ op = out + (long long)rk * plane;
+  double2 val[REPT];
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
-    const long long pos = ((long long)blockIdx.x * REPT + e) * RT + threadIdx.x;
-    if (pos >= plane) break;
-    const int i = (int)pos / a.ny, j = (int)pos - i * a.ny;          // nx * ny < 2^31
-    const double2* ax = a.aX + (long long)rk * a.nIx * a.ny + j;
-    const double2* by = a.bY + (long long)rk * a.nIy * a.nx + i;
-    double2 b;
+    const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
+    if (pos >= plane) continue;
+    const int i = pos / a.ny, j = pos - i * a.ny;
+    const double2* ax = axp + j;
+    const double2* by = byp + i;
     if (LO) {
       float2 g = make_float2(0.f, 0.f);
       for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64(ax[(long long)p * a.ny]), g);
       for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64(by[(long long)q * a.nx]), g);
-      b = to_c128(g);
+      val[e] = to_c128(g);
     } else {
-      b = make_double2(0.0, 0.0);
+      double2 b = make_double2(0.0, 0.0);
       for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
       for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+      val[e] = b;
     }
-    out[(long long)rk * plane + pos] = b;
+  }
+#pragma unroll
+  for (int e = 0; e < REPT; ++e) {
+    const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
+    if (pos < plane) op[pos] = val[e];
   }
 }
 
@@ -201,16 +214,22 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
   for (int k = 0; k < nz; ++k) {
     double2 d = tzd[k];
     const double2 sk = cmul(s, szs[k]);
+    // magnitude of the terms summed into the pivot: a pivot at their rounding level is
+    // numerically zero (the elimination would amplify rounding errors by 1 / eps)
+    double scale = hypot(d.x, d.y) + hypot(sk.x, sk.y);
     d.x += sk.x;
     d.y += sk.y;
     if (k > 0) {
       const double2 c = coff[k];
-      d = csub_mul(d, cmul(c, c), e_prev);
+      const double2 cc = cmul(c, c);
+      const double2 ce = cmul(cc, e_prev);
+      scale += hypot(ce.x, ce.y);
+      d = make_double2(d.x - ce.x, d.y - ce.y);
       Q[(long long)(k - 1) * plane + pos] = cmul(c, e_prev);
     }
     const double den = d.x * d.x + d.y * d.y;
     const double mag = sqrt(den);
-    if (!(mag > 0.0) || !isfinite(mag)) bad = true;
+    if (!(mag > 64.0 * 2.220446049250313e-16 * scale) || !isfinite(mag)) bad = true;
     minpiv = fmin(minpiv, mag);
     const double inv = 1.0 / den;
     const double2 e = make_double2(d.x * inv, -d.y * inv);

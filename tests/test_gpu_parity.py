@@ -305,3 +305,39 @@ def test_nonfinite_input_is_reported(hz, torch_cuda):
     with pytest.raises(hz.HzError) as e:
         plan.residual(fd, u)
     assert e.value.code == 4
+
+
+def _uniform_mix_workload(nrhs=2):
+    # x uniform in three blocks of 17, 18, 17 nodes (all take the closed-form sine pairs and
+    # the folded transforms, odd and even widths); y = 4 rim nodes | 35 uniform core nodes |
+    # 4 rim nodes, so one transform set mixes folded and dense complex blocks
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 54, 45, 9
+    hx = W.uniform_steps(nx, 1.0)
+    hy = W.rim_axis(ny - 8, rim_nodes=4, ratio=1.3, pml_nodes=2)
+    k2 = np.array([0.2 + 0.01j, 0.35 + 0.02j])
+    return W.Workload("uniform-mix", hx, hy, W.ramp_z(nz), np.array([0, 4, nz], np.int32), k2,
+                      np.array([17, 36], np.int32), np.array([4, 40], np.int32),
+                      rng.standard_normal((nrhs, nz, ny, nx)) + 1j * rng.standard_normal((nrhs, nz, ny, nx)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uniform_blocks_sine_path(hz, torch_cuda, precision):
+    w = _uniform_mix_workload()
+    P = O.Problem.from_workload(w)
+    ref = O.solve(P, w.f)
+    plan, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
+    assert plan.info()["eig_max_residual"] < 1e-12
+
+
+def test_uniform_blocks_mixed_adjoint(hz, torch_cuda):
+    # the conjugating transforms run on CUDA cores in FP32: the folded path with conj_out
+    torch = torch_cuda
+    w = _uniform_mix_workload()
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal(w.f.shape) + 1j * rng.standard_normal(w.f.shape)
+    lam_o = O.adjoint_solve(O.Problem.from_workload(w), g, method="lu")
+    plan = hz.Plan.from_workload(w, precision="mixed")
+    lam = plan.solve_adjoint(torch.from_numpy(g).cuda()).cpu().numpy()
+    assert rel(lam, lam_o) < TOLMIX
