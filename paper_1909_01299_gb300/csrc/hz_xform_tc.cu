@@ -23,8 +23,8 @@
 // The epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM lanes
 // 32(w%4)..+31 = tile rows, column chunks w/4, w/4+2, ...), converts to FP64 and
 // stores: transposed outputs straight from registers (a warp's 32 rows are
-// consecutive addresses), row-contiguous outputs through a shared-memory staging
-// tile written out row by row; optionally adding to the old values.
+// consecutive addresses), row-contiguous outputs through an FP32 staging tile in
+// shared memory written out row by row; optionally adding to the old values.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <algorithm>
@@ -148,8 +148,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 8 KB each), 64B-swizzled
 //   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled
 //   bars     : MMA-completion mbarriers of the two operand stages, TMEM address slot
-// The chunk pipeline: the FP64 rows of chunk c+2 and the table rows of chunk c+1 are in
-// flight (cp.async) while chunk c is converted and its MMAs run.
+// The chunk pipeline: while chunk c is converted, the MMAs of chunk c-1 run and the table
+// rows of chunk c and the FP64 rows of chunk c+1 are in flight (cp.async).
 constexpr int RAW_ROWB = KCH * 8;        // FP64 bytes of a data row in a chunk (KCH / 2 complex)
 constexpr int RAW_BYTES = TC_M * RAW_ROWB;
 
@@ -228,23 +228,17 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   bool ok = true;
   int issued = 0;
 
-  // Iteration kc: (1) once the MMAs of chunk kc-1 are done, start the table rows of chunk
-  // kc+1 (their stage is free) -- they then have a whole iteration to arrive; (2) wait for
-  // A(kc), B(kc); (3) convert; (4) issue the MMAs of kc; (5) start the data rows of kc+2.
-  // cp.async groups are committed in the order A0 B0 A1 | B1 A2 | B2 A3 | ..., so at step
-  // (2) everything but the newest two groups {A(kc+1), B(kc+1)} must be complete.
+  // Iteration kc: (1) wait for this thread's data rows of chunk kc; (2) convert them into
+  // the operand stage kc & 1 (free: the MMAs of kc-2 were waited for in iteration kc-1);
+  // (3) wait for the MMAs of kc-1 -- they ran while we converted -- and the table rows of
+  // kc; (4) one thread issues the MMAs of kc; (5) start the table rows of kc+1 (their stage
+  // was read by kc-1) and the data rows of kc+2 (their buffer was converted in (2)).
+  // cp.async groups are committed in the order A0 B0 A1 | B1 A2 | B2 A3 | ..., so at (1)
+  // all but the newest two {B(kc), A(kc+1)} are complete, at (3) all but A(kc+1).
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
-    if (kc >= 1) {
-      const int w = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
-      if (!__syncthreads_and(w)) { ok = false; break; }
-    }
-    if (kc + 1 < nk) load_b(kc + 1);
-    cp_async_commit();
-    cp_async_wait<2>();                                     // raw A(kc) and B(kc) have landed
+    cp_async_wait<2>();                                     // raw A(kc) has landed
     __syncthreads();
-    // convert raw[s] -> TF32 hi/lo operand planes of stage s (free: MMA(kc-2) finished
-    // before the wait on MMA(kc-1) above)
     {
       const uint32_t rsrc = raw0 + s * RAW_BYTES;
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
@@ -267,8 +261,11 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
         st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
     }
+    int w = 1;
+    if (kc >= 1) w = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
+    cp_async_wait<1>();                                     // table rows B(kc) have landed
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();                                        // raw[s] free, operands of kc ready
+    if (!__syncthreads_and(w)) { ok = false; break; }       // operands of kc ready, MMA(kc-1) done
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
@@ -286,6 +283,8 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       mma_commit(&bars[s]);
     }
     issued = kc + 1;
+    if (kc + 1 < nk) load_b(kc + 1);
+    cp_async_commit();
     if (kc + 2 < nk) load_raw(kc + 2);
     cp_async_commit();
   }
@@ -338,52 +337,61 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
           if (p[e]) *p[e] = val[e];
       }
     } else {
-      // Rows are contiguous in memory: stage the FP64 result in the (now idle) pipeline
-      // buffers, at most 80 real columns per pass, row stride padded by 16 bytes so that the
-      // row-per-lane writes are conflict-free; then each warp writes whole rows with
-      // consecutive lanes on consecutive columns.  A pass needs 1024 * pw + 2048 bytes; the
-      // buffers hold 2 * RAW_BYTES + 4 * A_BYTES + 256 * nt = 65536 + 256 * nt, which covers
-      // pw = nt for nt <= 80 and pw = 80 for nt >= 72.
-      const int PW = min(nt, 80);
-      const int sstride = PW * 8 + 16;
-      for (int p0 = 0; p0 < nt; p0 += PW) {
-        const int pw = min(PW, nt - p0);
-        for (int c16 = p0 + 16 * cgrp; c16 < p0 + pw; c16 += 16 * NGRP) {
-          float v[16];
-          tmem_ld16(tl + c16, v);
-          double2* dst = reinterpret_cast<double2*>(smem + (size_t)r * sstride) + (c16 - p0) / 2;
+      // Rows are contiguous in memory: stage the FP32 accumulator tile in the (now idle)
+      // pipeline buffers -- 128 rows x nt floats, row stride padded by 16 bytes so that the
+      // row-per-lane writes are conflict-free; nt * 512 + 2048 bytes fit in the
+      // 65536 + 256 * nt bytes of the buffers for every nt <= 252 -- then each warp writes
+      // whole rows, consecutive lanes on consecutive complex columns, converting to FP64.
+      const int sstride = nt * 4 + 16;
+      for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
+        float v[16];
+        tmem_ld16(tl + c16, v);
+        const uint32_t dst = s_base + (uint32_t)(r * sstride + c16 * 4);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) dst[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
+        for (int q = 0; q < 4; ++q)
+          st_shared_v4(dst + 16 * q, __float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
+                       __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]));
+      }
+      __syncthreads();
+      const int cbase = t.n0 / 2;                           // first complex column of the tile in the block
+      const int ccount = min(nt / 2, n - cbase);
+      for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
+        const long long g = row0 + rr;
+        if (g >= nrows) break;
+        if (rowskip) {
+          const long long pl = g / rows_per_plane;
+          if (rowskip[g - pl * rows_per_plane]) continue;
         }
-        __syncthreads();
-        const int cbase = (t.n0 + p0) / 2;                   // first complex column of the pass in the block
-        const int ccount = min(pw / 2, n - cbase);
-        for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
-          const long long g = row0 + rr;
-          if (g >= nrows) break;
-          if (rowskip) {
-            const long long pl = g / rows_per_plane;
-            if (rowskip[g - pl * rows_per_plane]) continue;
-          }
-          const double2* src = reinterpret_cast<const double2*>(smem + (size_t)rr * sstride);
-          double2* dg = out + g * (long long)ncols + b.start + cbase;
-          if (store == XS_ACCUM) {
-            for (int c = lane; c < ccount; c += 64) {       // two old values in flight per lane
-              const bool two = c + 32 < ccount;
-              const double2 o0 = dg[c];
-              const double2 o1 = two ? dg[c + 32] : make_double2(0.0, 0.0);
-              const double2 v0 = src[c];
-              dg[c] = make_double2(v0.x + o0.x, v0.y + o0.y);
-              if (two) {
-                const double2 v1 = src[c + 32];
-                dg[c + 32] = make_double2(v1.x + o1.x, v1.y + o1.y);
-              }
-            }
-          } else {
-            for (int c = lane; c < ccount; c += 32) dg[c] = src[c];
+        const float2* src = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
+        double2* dg = out + g * (long long)ncols + b.start + cbase;
+        constexpr int CPL = kTcMaxN / 2 / 32 + 1;           // complex columns per lane (<= 3)
+        double2 val[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const int c = lane + 32 * q;
+          if (c < ccount) {
+            const float2 f = src[c];
+            val[q] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
           }
         }
-        __syncthreads();
+        if (store == XS_ACCUM) {                           // every old value in flight at once
+          double2 o[CPL];
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const int c = lane + 32 * q;
+            if (c < ccount) o[q] = dg[c];
+          }
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const int c = lane + 32 * q;
+            if (c < ccount) { val[q].x += o[q].x; val[q].y += o[q].y; }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const int c = lane + 32 * q;
+          if (c < ccount) dg[c] = val[q];
+        }
       }
     }
   } else if (tid == 0) {
