@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pml160",
-                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48"],
+                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48", "scaling"],
                     help="pml160 is the benchmark workload; the others are extra measurements")
     return ap.parse_args()
 
@@ -380,6 +380,30 @@ def run_extra(args):
     B.build()
     from paper_1909_01299_gb300 import hz, workloads as W
     out = {"workload": args.workload}
+    if args.workload == "scaling":
+        # the two regimes of the cost estimate in Sec. 2, FP64 path: one block per axis (dense
+        # N x N transforms, work per unknown ~ N) against the automatic ~sqrt(N) partition
+        # (work per unknown ~ sqrt(N)); survey-type axes (uniform core + 16-node rim), nz = 64
+        rows = []
+        for n in (64, 96, 128, 192, 256, 320, 384):
+            hx = W.rim_axis(n - 32, rim_nodes=16, ratio=1.3, pml_nodes=8)
+            hzz = W.ramp_z(64)
+            rng = np.random.default_rng(n)
+            f = torch.from_numpy(rng.standard_normal((2, 64, n, n)) + 1j * rng.standard_normal((2, 64, n, n))).cuda()
+            u = torch.empty_like(f)
+            row = {"n": n, "unknowns_x_rhs": n * n * 64 * 2}
+            for label, nb in (("one_block", 1), ("auto", 0)):
+                plan = hz.Plan(hx, hx, hzz, [0, 32, 64], [0.2 + 0.004j, 0.35 + 0.007j], nbx=nb, nby=nb,
+                               precision="fp64")
+                ms, launches, st, clk = time_path(torch, hz, plan, f, u, args.steps, args.warmup, None, 1, 0)
+                row[label] = {"blocks": plan.info()["nbx"], "ms": ms, "value": n * n * 64 * 2 / (ms * 1e-3),
+                              "ns_per_unknown": ms * 1e6 / (n * n * 64 * 2),
+                              "rel_residual_max": float(np.max(plan.residual(f, u)))}
+                plan.close()
+            rows.append(row)
+        out.update({"path": "fp64", "sweep": rows, "unit": UNIT})
+        print(json.dumps(out), flush=True)
+        return
     if args.workload == "batch48":
         items = W.batched_models(48)
         plans, fs, us, nrhs = [], [], [], []
@@ -426,21 +450,27 @@ def run_extra(args):
                          "stages_ms_per_step": {k: v[0] / args.steps for k, v in st.items() if v[1]},
                          "clocks": clk}
         if args.workload == "adjoint192":
+            # misfit gradient: forward solves, adjoint solves and the layer reduction
             rec = torch.from_numpy(w.extra["rec_flat"]).cuda()
-            plan.set_options(precision="fp64")
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(args.steps):
+            def grad_step():
                 uu = plan.solve(f)
                 flat = uu.reshape(w.nrhs, -1)
                 g = torch.zeros_like(flat)
                 g[:, rec] = flat[:, rec]
                 lam = plan.solve_adjoint(g.reshape(uu.shape))
-                G = plan.grad_layers(uu, lam)
-            e1.record()
-            torch.cuda.synchronize()
-            out["gradient_ms"] = e0.elapsed_time(e1) / args.steps
+                return plan.grad_layers(uu, lam)
+
+            for prec in ("fp64", "mixed"):
+                plan.set_options(precision=prec, rtol=RTOL)
+                grad_step()                                  # warm-up (buffers, allocator)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.steps):
+                    grad_step()
+                e1.record()
+                torch.cuda.synchronize()
+                out[prec]["gradient_ms"] = e0.elapsed_time(e1) / args.steps
         out["unit"] = UNIT
         if not args.no_cpu_baseline:
             # the oracle on the machine's host cores, one right-hand side of the same workload

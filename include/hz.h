@@ -47,7 +47,7 @@ typedef enum {
   HZ_ERR_ARG = 1,            /* bad size, pointer or option                            */
   HZ_ERR_EIG = 2,            /* a 1D eigen-decomposition failed its identity checks    */
   HZ_ERR_SINGULAR = 3,       /* singular pivot in a z tridiagonal: zero, non-finite, or
-                                |d| <= 64 eps (sum of the magnitudes that formed d)     */
+                                |d| <= 64 eps x (sum of the 1-norms of the terms of d)  */
   HZ_ERR_NONFINITE = 4,      /* non-finite value in the input or the result            */
   HZ_ERR_NOT_CONVERGED = 5,  /* mixed path: refinement did not reach rtol              */
   HZ_ERR_OOM = 6,            /* device allocation failed                               */
@@ -79,7 +79,13 @@ typedef struct {
  * indices (strictly increasing, each block keeps >= 1 node); NULL selects the
  * default p_b = floor(b (nx+1) / nbx) - 1, b = 1..nbx-1.  Same for y.  The
  * interface nodes belong to no block (Sec. 2, "the projection operators to
- * interior nodes"). */
+ * interior nodes").  nbx = HZ_BLOCKS_AUTO (x_iface NULL) lets the plan choose the
+ * count: the FP64 path balances the dense block transforms (cost ~ N / B per unknown)
+ * against the interface steps (cost ~ B), B ~ sqrt(N) as in the cost estimate of Sec. 2,
+ * with blocks at least 16 nodes wide; the mixed path, whose block transforms run on
+ * tensor cores at memory speed, takes blocks about 80 nodes wide.  hz_get_info reports
+ * the counts chosen. */
+#define HZ_BLOCKS_AUTO 0
 typedef struct {
   int nbx, nby;
   const int *x_iface, *y_iface;
@@ -107,6 +113,7 @@ typedef struct {
   double eig_max_residual;   /* largest relative eigen-identity residual of the plan    */
   long long device_bytes;    /* device memory owned by the plan                         */
   long long kernel_launches; /* kernels launched by this plan's solves so far           */
+  int nbx, nby;              /* block partition in use                                  */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's

@@ -215,6 +215,20 @@ bool finite(cd z) { return std::isfinite(z.real()) && std::isfinite(z.imag()); }
 // ---------------------------------------------------------------------------
 // Plan construction
 // ---------------------------------------------------------------------------
+// Automatic block count for an axis of n nodes.  FP64 operations per unknown and solve,
+// per axis: the dense block transforms of steps 1 and 7 cost about 12 n / B (two
+// transforms, 3 FMA per complex multiply-add, blocks n / B wide); the interface steps
+// (short whole-axis transforms, the rank-|I| right-hand sides and contractions of steps
+// 5 and 6) about 28 (B - 1).  The minimum is at B = sqrt(3 n / 7) ~ 0.65 sqrt(n), the
+// sqrt(N) partition of the cost estimate in Sec. 2; blocks stay at least 16 nodes wide
+// (one transform column tile).  The mixed path runs the block transforms on tensor cores
+// at memory speed, so there fewer, wider blocks win: about 80 nodes each.
+int auto_blocks(int n, bool mixed) {
+  int b = mixed ? (int)std::lround(n / 80.0) : (int)std::lround(std::sqrt(3.0 * n / 7.0));
+  b = std::min(b, n / 16);
+  return std::max(b, 1);
+}
+
 // True when the sz + 1 steps h[s .. s + sz] that touch the nodes s .. s + sz - 1 are all
 // equal, real and positive: that block's pencil has the closed-form sine pairs.
 bool uniform_steps(const std::vector<cd>& h, int s, int sz, double* hu) {
@@ -938,6 +952,44 @@ void release(hz_plan_t p) {
 // ---------------------------------------------------------------------------
 // Batches: many (plan, nrhs) solves replayed as one CUDA graph
 // ---------------------------------------------------------------------------
+namespace {
+
+// Time the plan's kernel variants (z-sweep RHS per thread 1 or 2; on the mixed path tensor-core
+// or CUDA-core bulk transforms) with three solves each on workspace w and stream st, keep the
+// fastest; returns rb + 10 * tc of the choice.  f and out are device buffers of nrhs RHS.
+int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* out, int nrhs) {
+  const bool mixed = p->opts.precision == HZ_MIXED;
+  const bool timing = p->timing;
+  p->timing = false;
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_rb = p->zs_rb;
+  bool best_tc = p->use_tc;
+  for (int rb = 1; rb <= 2; ++rb)
+    for (int tc = mixed ? 0 : 1; tc <= 1; ++tc) {
+      p->zs_rb = rb;
+      p->use_tc = tc != 0;
+      solve_core(p, w, st, f, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up
+      ck(cudaEventRecord(e0, st));
+      for (int rep = 0; rep < 3; ++rep) solve_core(p, w, st, f, out, nrhs, mixed, hz::XS_STORE, 0);
+      ck(cudaEventRecord(e1, st));
+      ck(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->zs_rb = best_rb;
+  p->use_tc = best_tc;
+  p->timing = timing;
+  return best_rb + (best_tc ? 10 : 0);
+}
+
+}  // namespace
+
 struct hz_batch_s {
   std::vector<hz_plan_t> plans;
   std::vector<int> nrhs;
@@ -1179,10 +1231,19 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
     if (!std::isfinite(layers->k2[L].re) || !std::isfinite(layers->k2[L].im)) return HZ_ERR_ARG;
     if (layers->sigma && !(layers->sigma[L] > 0.0 && std::isfinite(layers->sigma[L]))) return HZ_ERR_ARG;
   }
-  const int nbx = blocks ? blocks->nbx : 1, nby = blocks ? blocks->nby : 1;
+  if (opts && (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED)) return HZ_ERR_ARG;
+  const bool mixed = opts && opts->precision == HZ_MIXED;
+  int nbx = blocks ? blocks->nbx : 1, nby = blocks ? blocks->nby : 1;
+  if (blocks && nbx == HZ_BLOCKS_AUTO) {
+    if (blocks->x_iface) return HZ_ERR_ARG;
+    nbx = auto_blocks(grid->nx, mixed);
+  }
+  if (blocks && nby == HZ_BLOCKS_AUTO) {
+    if (blocks->y_iface) return HZ_ERR_ARG;
+    nby = auto_blocks(grid->ny, mixed);
+  }
   if (nbx < 1 || nby < 1 || nbx > grid->nx || nby > grid->ny) return HZ_ERR_ARG;
   if ((long long)grid->nx * grid->ny >= (1LL << 31)) return HZ_ERR_ARG;      // in-plane indices are 32-bit
-  if (opts && (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED)) return HZ_ERR_ARG;
 
   hz_plan_t p = new (std::nothrow) hz_plan_s();
   if (!p) return HZ_ERR_OOM;
@@ -1203,6 +1264,8 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   for (int L = 0; L < nl; ++L) p->k2base[L] = cd(layers->k2[L].re, layers->k2[L].im);
   if (layers->sigma) p->sig_layer.assign(layers->sigma, layers->sigma + nl);
 
+  p->info.nbx = nbx;
+  p->info.nby = nby;
   hz_status s = build_axis(p->ax, grid->nx, grid->hx, nbx, blocks ? blocks->x_iface : nullptr);
   if (s == HZ_OK) s = build_axis(p->ay, grid->ny, grid->hy, nby, blocks ? blocks->y_iface : nullptr);
   p->need_global = (nbx > 1 || nby > 1);
@@ -1405,34 +1468,8 @@ hz_status hz_plan_autotune(hz_plan_t p, int nrhs, int* choice_out) {
     double2* buf = ensure_extra(p, p->ws.F2, p->ws.f2_cap, nrhs);
     double2* out = ensure_extra(p, p->ws.HU, p->ws.hu_cap, nrhs);
     ck(cudaMemsetAsync(buf, 0, sizeof(double2) * (size_t)p->nx * p->ny * p->nz * nrhs, p->st));
-    const bool mixed = p->opts.precision == HZ_MIXED;
-    const bool timing = p->timing;
-    p->timing = false;
-    cudaEvent_t e0, e1;
-    ck(cudaEventCreate(&e0));
-    ck(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_rb = p->zs_rb;
-    bool best_tc = p->use_tc;
-    for (int rb = 1; rb <= 2; ++rb)
-      for (int tc = mixed ? 0 : 1; tc <= 1; ++tc) {
-        p->zs_rb = rb;
-        p->use_tc = tc != 0;
-        solve_core(p, p->ws, p->st, buf, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up
-        ck(cudaEventRecord(e0, p->st));
-        for (int rep = 0; rep < 3; ++rep) solve_core(p, p->ws, p->st, buf, out, nrhs, mixed, hz::XS_STORE, 0);
-        ck(cudaEventRecord(e1, p->st));
-        ck(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        ck(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; }
-      }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->zs_rb = best_rb;
-    p->use_tc = best_tc;
-    p->timing = timing;
-    if (choice_out) *choice_out = best_rb + (best_tc ? 10 : 0);
+    const int c = tune_plan(p, p->ws, p->st, buf, out, nrhs);
+    if (choice_out) *choice_out = c;
   } catch (const Fail& e) {
     return e.s;
   }
@@ -1480,10 +1517,12 @@ hz_status hz_batch_autotune(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* 
   if (!b || !f_dev || !u_dev) return HZ_ERR_ARG;
   try {
     const int n = (int)b->plans.size();
-    for (int i = 0; i < n; ++i) {
-      const hz_status st = hz_plan_autotune(b->plans[i], b->nrhs[i], nullptr);
-      if (st != HZ_OK) throw Fail{st};
-    }
+    // tune every plan on the batch's own lane workspace (one lane: sized for the largest
+    // item) and the caller's buffers, so that no plan allocates a workspace of its own
+    batch_setup(b, 1);
+    for (int i = 0; i < n; ++i)
+      tune_plan(b->plans[i], b->ws[0], b->s0, reinterpret_cast<const double2*>(f_dev[i]),
+                reinterpret_cast<double2*>(u_dev[i]), b->nrhs[i]);
     int best_l = b->nlanes;
     double best_ms = 1e300;
     for (int l : {1, 2, 4, 8}) {

@@ -216,14 +216,14 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
     const double2 sk = cmul(s, szs[k]);
     // magnitude of the terms summed into the pivot: a pivot at their rounding level is
     // numerically zero (the elimination would amplify rounding errors by 1 / eps)
-    double scale = hypot(d.x, d.y) + hypot(sk.x, sk.y);
+    double scale = fabs(d.x) + fabs(d.y) + fabs(sk.x) + fabs(sk.y);   // (1-norms bound the moduli)
     d.x += sk.x;
     d.y += sk.y;
     if (k > 0) {
       const double2 c = coff[k];
       const double2 cc = cmul(c, c);
       const double2 ce = cmul(cc, e_prev);
-      scale += hypot(ce.x, ce.y);
+      scale += fabs(ce.x) + fabs(ce.y);
       d = make_double2(d.x - ce.x, d.y - ce.y);
       Q[(long long)(k - 1) * plane + pos] = cmul(c, e_prev);
     }

@@ -341,3 +341,17 @@ def test_uniform_blocks_mixed_adjoint(hz, torch_cuda):
     plan = hz.Plan.from_workload(w, precision="mixed")
     lam = plan.solve_adjoint(torch.from_numpy(g).cuda()).cpu().numpy()
     assert rel(lam, lam_o) < TOLMIX
+
+
+def test_auto_partition_matches_lu(hz, torch_cuda):
+    # HZ_BLOCKS_AUTO: the FP64 plan picks round(sqrt(3 N / 7)) blocks of >= 16 nodes per axis,
+    # the mixed plan blocks about 80 nodes wide
+    torch = torch_cuda
+    w = W.tiny_pml(96, 66, 8, 1, 1, rim=8, pml=3, nrhs=1)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    for precision, tol, counts in (("fp64", TOL64, (6, 4)), ("mixed", TOLMIX, (1, 1))):
+        plan = hz.Plan(w.hx, w.hy, w.hz, w.z_begin, w.k2, w.sigma, nbx=0, nby=0, precision=precision)
+        u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+        info = plan.info()
+        assert (info["nbx"], info["nby"]) == counts
+        assert rel(u, ref) < tol
