@@ -383,3 +383,34 @@ def misfit_gradient(P: Problem, f, rec_flat, d_obs, method="blk"):
     J, g = misfit(u, rec_flat, d_obs)
     lam = adjoint_solve(P, g, A, method)
     return J, layer_gradient(P, u, lam), u, lam
+
+
+# ---------------------------------------------------------------------------
+# Layered medium with a local perturbation (Sec. 1: the layered solve as a fast
+# preconditioner for media with embedded inhomogeneities)
+# ---------------------------------------------------------------------------
+
+def solve_perturbed(P: Problem, f, dk2, A=None):
+    """u of -div(sigma grad u) - (k^2(z) + dk2(x, y, z)) u = f by sparse LU.
+
+    dk2 is node-based, shape (Nz, Ny, Nx).  The perturbation adds -dk2 to the k^2 term of
+    every node, i.e. subtracts diag(M dk2) from A (the k^2 term of Eq. (fdmtr) is
+    -k^2 times the control-volume weight):  (A - diag(M dk2)) u = M f.
+    """
+    if A is None:
+        A, mdiag = assemble(P)
+    else:
+        mdiag = np.kron(dual_lengths(P.hz), np.kron(dual_lengths(P.hy), dual_lengths(P.hx)))
+    Ap = (A - sp.diags(mdiag * np.asarray(dk2, dtype=np.complex128).ravel())).tocsc()
+    return solve_direct(P, weighted_rhs(P, f), Ap)
+
+
+def residual_perturbed(P: Problem, u, f, dk2, A=None):
+    """Per-RHS ||M f - (A - diag(M dk2)) u|| / ||M f||."""
+    if A is None:
+        A, _ = assemble(P)
+    b = weighted_rhs(P, f)
+    r = b - apply_A(P, u, A) + weighted_rhs(P, dk2[None] * u)
+    R = u.shape[0]
+    return (np.linalg.norm(r.reshape(R, -1), axis=1) / np.linalg.norm(b.reshape(R, -1), axis=1))
+

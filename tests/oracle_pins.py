@@ -185,3 +185,52 @@ def adjoint_error(w):
     R = g.shape[0]
     ref = spla.spsolve(AH, g.reshape(R, -1).T).T.reshape(g.shape)
     return np.linalg.norm(lam - ref) / np.linalg.norm(ref)
+
+
+def perturbation(P: O.Problem, amp=0.15, seed=3):
+    """A local complex perturbation of k^2 on a box in the middle of the grid (zero elsewhere)."""
+    nz, ny, nx = P.shape
+    rng = np.random.default_rng(seed)
+    d = np.zeros((nz, ny, nx), dtype=np.complex128)
+    kz, jy, ix = slice(nz // 4, 3 * nz // 4 + 1), slice(ny // 4, 3 * ny // 4 + 1), slice(nx // 4, 3 * nx // 4 + 1)
+    shape = d[kz, jy, ix].shape
+    d[kz, jy, ix] = amp * (rng.uniform(0.5, 1.0, shape) + 0.1j * rng.uniform(0.0, 1.0, shape))
+    return d
+
+
+def perturbed_bruteforce_error(w, amp=0.15):
+    """Perturbed operator assembled node by node from the stencil (Eq. (fd) with k^2 -> k^2 + dk2
+    at each node) and solved densely, against the oracle's perturbed solve."""
+    P = O.Problem.from_workload(w)
+    dk2 = perturbation(P, amp)
+    Ad = stencil_matrix_loops(P)
+    nz, ny, nx = P.shape
+    hhx = [(P.hx[i] + P.hx[i + 1]) / 2 for i in range(nx)]
+    hhy = [(P.hy[j] + P.hy[j + 1]) / 2 for j in range(ny)]
+    hhz = [(P.hz[k] + P.hz[k + 1]) / 2 for k in range(nz)]
+    b = np.zeros((w.f.shape[0], nz * ny * nx), dtype=np.complex128)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                row = (k * ny + j) * nx + i
+                vol = hhx[i] * hhy[j] * hhz[k]
+                Ad[row, row] -= dk2[k, j, i] * vol
+                b[:, row] = w.f[:, k, j, i] * vol
+    ref = np.linalg.solve(Ad, b.T).T.reshape(w.f.shape)
+    u = O.solve_perturbed(P, w.f, dk2)
+    return np.linalg.norm(u - ref) / np.linalg.norm(ref)
+
+
+def perturbed_born_series_error(w, amp=0.02, terms=40):
+    """For a weak perturbation the solution is the Born (Neumann) series
+    u = sum_n (S dk2)^n S f with S the layered solve; only layered solves are used."""
+    P = O.Problem.from_workload(w)
+    dk2 = perturbation(P, amp)
+    A, _ = O.assemble(P)
+    term = O.solve(P, w.f, A)
+    u = term.copy()
+    for _ in range(terms):
+        term = O.solve(P, dk2[None] * term, A)
+        u += term
+    ref = O.solve_perturbed(P, w.f, dk2, A)
+    return np.linalg.norm(u - ref) / np.linalg.norm(ref)

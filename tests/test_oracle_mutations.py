@@ -140,3 +140,24 @@ def test_gradient_without_conjugation_is_caught(monkeypatch):
     e[0] = eps
     fd = (J_at(w.k2 + e) - J_at(w.k2 - e)) / (2 * eps)
     assert abs(G[0].real - fd) > 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("mistake", ["sign", "no_weight", "transposed"])
+def test_perturbed_solve_mistakes_are_caught(mistake, monkeypatch):
+    # plausible slips in the perturbed operator: the perturbation added with the wrong
+    # sign, without the control-volume weight, or laid out transposed
+    orig = O.solve_perturbed
+
+    def bad(P, f, dk2, A=None):
+        d = np.asarray(dk2)
+        if mistake == "sign":
+            d = -d
+        elif mistake == "no_weight":
+            mdiag = np.kron(O.dual_lengths(P.hz), np.kron(O.dual_lengths(P.hy), O.dual_lengths(P.hx)))
+            d = d / mdiag.reshape(d.shape)
+        else:
+            d = np.ascontiguousarray(np.swapaxes(d, 1, 2)).reshape(d.shape)
+        return orig(P, f, d, A)
+    monkeypatch.setattr(O, "solve_perturbed", bad)
+    w = W.tiny_pml(9, 8, 6, 2, 2, rim=2, pml=1, nrhs=2)
+    assert pins.perturbed_bruteforce_error(w) > 1e-8

@@ -162,3 +162,23 @@ def test_workload_shapes():
     assert list(w3.x_iface) == [79, 159, 239]
     w5 = W.adjoint_192x192x128(nsrc=2)
     assert len(w5.hx) == 193 and list(w5.x_iface) == [95]
+
+
+def test_perturbed_solve_bruteforce():
+    # dense node-by-node assembly with the perturbed k^2 (tiny grid, 2x2 blocks irrelevant here)
+    w = W.tiny_pml(9, 8, 6, 2, 2, rim=2, pml=1, nrhs=2)
+    assert pins.perturbed_bruteforce_error(w) < 1e-12
+
+
+def test_perturbed_solve_born_series():
+    w = W.tiny_pml(16, 14, 10, 2, 2, rim=3, pml=2, nrhs=2)
+    assert pins.perturbed_born_series_error(w) < 1e-11
+
+
+def test_perturbed_solve_zero_perturbation():
+    w = W.tiny_pml(13, 11, 9, 2, 2, nrhs=1)
+    P = O.Problem.from_workload(w)
+    u0 = O.solve(P, w.f)
+    u1 = O.solve_perturbed(P, w.f, np.zeros(P.shape, dtype=np.complex128))
+    assert np.linalg.norm(u1 - u0) <= 1e-14 * np.linalg.norm(u0)
+    assert np.all(O.residual_perturbed(P, u1, w.f, np.zeros(P.shape)) < 1e-12)
