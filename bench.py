@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pml160",
-                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48", "scaling"],
+                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48", "scaling", "perturbed160"],
                     help="pml160 is the benchmark workload; the others are extra measurements")
     return ap.parse_args()
 
@@ -402,6 +402,32 @@ def run_extra(args):
                 plan.close()
             rows.append(row)
         out.update({"path": "fp64", "sweep": rows, "unit": UNIT})
+        print(json.dumps(out), flush=True)
+        return
+    if args.workload == "perturbed160":
+        # pml-160 with a local inhomogeneity: dk2 on a 64 x 64 x 48 box in the survey core,
+        # 0.3 x the mean layer k^2 (the layered solve as the operator of GMRES)
+        w = W.pml_160x160x128()
+        rng = np.random.default_rng(1909)
+        dk2 = np.zeros((w.nz, w.ny, w.nx), np.complex128)
+        amp = 0.3 * float(np.mean(np.real(w.k2)))
+        dk2[40:88, 48:112, 48:112] = amp * (rng.uniform(0.5, 1.0, (48, 64, 64)) + 0.1j * rng.uniform(0, 1, (48, 64, 64)))
+        d = torch.from_numpy(dk2).cuda()
+        f = torch.from_numpy(w.f).cuda()
+        out["workload"] = "pml-160x160x128-2x2blocks-4rhs + 64x64x48 perturbation box"
+        for prec in ("fp64", "mixed"):
+            plan = hz.Plan.from_workload(w, precision=prec)
+            u, iters, rel = plan.solve_perturbed(d, f, rtol=1e-8, max_iter=300, restart=20)   # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                u, iters, rel = plan.solve_perturbed(d, f, rtol=1e-8, max_iter=300, restart=20)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / args.steps
+            out[prec] = {"ms_per_step": dt * 1e3, "iterations": iters, "value": w.unknowns * w.nrhs / dt,
+                         "rel_residual_max": float(np.max(rel)), "ms_per_iteration": dt * 1e3 / max(iters, 1)}
+            plan.close()
+        out["unit"] = UNIT
         print(json.dumps(out), flush=True)
         return
     if args.workload == "batch48":

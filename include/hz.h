@@ -178,6 +178,23 @@ hz_status hz_solve_host(hz_plan_t plan, const hz_c128 *f_host, hz_c128 *u_host, 
  * applied to it). */
 hz_status hz_solve_adjoint(hz_plan_t plan, const hz_c128 *g_dev, hz_c128 *lam_dev, int nrhs);
 
+/* Layered medium with a local perturbation of k^2 -- the paper's motivating use of the
+ * layered solver as a fast preconditioner for media with embedded inhomogeneities (Sec. 1):
+ *     -div(sigma grad u) - (k^2(z) + dk2(x, y, z)) u = f,  i.e.  (A - M diag(dk2)) u = M f.
+ * Solved by restarted GMRES(restart) on the second-kind form u - S(dk2 u) = S f, where S is
+ * this plan's layered solve (FP64 or mixed, per the plan's options; the Born term S f is the
+ * initial guess).  dk2_dev: device complex [Nz][Ny][Nx], node-based, the same for every RHS;
+ * f_dev, u_dev: as hz_solve (distinct buffers).  Stops when every RHS's GMRES residual is
+ * <= rtol ||S f||; each iteration is one layered solve of all RHS.  iters_out (may be NULL):
+ * iterations used; relres_out (may be NULL, else nrhs doubles): the true relative residual
+ * ||M f - (A - M diag(dk2)) u|| / ||M f|| per RHS (FP64 stencil).  The Krylov basis,
+ * (restart + 1) volumes of nrhs RHS (restart <= 0: 20), is allocated for the call and freed.
+ * Errors: HZ_ERR_ARG; HZ_ERR_NOT_CONVERGED after max_iter iterations (u holds the last
+ * iterate); errors of the inner solves. */
+hz_status hz_solve_perturbed(hz_plan_t plan, const hz_c128 *dk2_dev, const hz_c128 *f_dev, hz_c128 *u_dev,
+                             int nrhs, double rtol, int max_iter, int restart, int *iters_out,
+                             double *relres_out);
+
 /* Layer gradient G_L = sum_rhs sum_{k in L} hhat^z_k sum_ij conj(lam_ijk) hhat^x_i hhat^y_j u_ijk
  * for L = 0..nlayers-1, written to G_host (nlayers entries).  For a real misfit J whose
  * adjoint source is g = dJ/du* the result gives dJ/dRe k^2_L = Re G_L and

@@ -200,6 +200,30 @@ void contract_rows(const double2* V, double2* out, const float2* coef, const int
 void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Locally perturbed medium: vector kernels of the GMRES around the layered solve.
+// Vectors are [r][n] complex (R right-hand sides of n values); a basis is [i][r][n]
+// with vstride = R * n between its vectors.
+// ---------------------------------------------------------------------------
+constexpr int kMaxVec = 16;     // basis vectors handled per multi_dot / multi_axpy pass
+// out[r][n] = d[n] v[r][n]
+void pert_mul(const double2* d, const double2* v, double2* out, long long n, int R, cudaStream_t st);
+// out = a - b + c (b or c may be NULL), total elements
+void vec_lin3(const double2* a, const double2* b, const double2* c, double2* out, long long total,
+              cudaStream_t st);
+// s[r] = 1 / sqrt(Re d[r]), or 0 where Re d[r] <= 0
+void vec_inv_norm(const double2* d, double2* s, int R, cudaStream_t st);
+// out[r][n] = s[r] w[r][n]
+void vec_scale(const double2* s, const double2* w, double2* out, long long n, int R, cudaStream_t st);
+// out[r * cnt + i] = <V_i[r], w[r]> = sum conj(V_i[r][n]) w[r][n], cnt <= kMaxVec; partial needs
+// R * multi_dot_parts(n) * cnt entries.  Fixed summation order.
+int multi_dot_parts(long long n);
+void multi_dot(const double2* V, long long vstride, int cnt, const double2* w, long long n, int R,
+               double2* partial, double2* out, cudaStream_t st);
+// w[r][n] -= sum_{i < cnt} c[r * cnt + i] V_i[r][n], cnt <= kMaxVec
+void multi_axpy(const double2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
+                cudaStream_t st);
+
 struct IfaceArgs {
   int nx = 0, ny = 0, nz = 0, nrhs = 0, nIx = 0, nIy = 0;
   const int* xif = nullptr; const int* yif = nullptr;          // interface node indices

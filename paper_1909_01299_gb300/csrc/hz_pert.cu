@@ -1,0 +1,205 @@
+// Vector kernels of the restarted GMRES that solves a locally perturbed layered medium
+// with the layered solve as its operator (Sec. 1: the fast layered solver as a
+// preconditioner for media with embedded inhomogeneities).
+//
+// Vectors are the solver's volumes: nrhs right-hand sides of n complex values each,
+// [r][n]; a Krylov basis is a run of such volumes, [i][r][n].  Everything is FP64 and
+// bound by HBM: each kernel streams its vectors once (grid-stride, coalesced), the
+// multi-vector dot products and updates take up to kMaxVec basis vectors per pass so that
+// the vector they are applied to is read once per pass, and the dot products reduce in a
+// fixed order (per-CTA partial sums, then one ordered sum per output).
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+unsigned grid_for(long long n) {
+  const long long g = (n + NT - 1) / NT;
+  return (unsigned)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+// per-RHS kernels: grid (x, R), blockIdx.y = RHS, grid-stride over its n values
+dim3 grid_rhs(long long n, int R) {
+  const long long g = (n + NT - 1) / NT;
+  return dim3((unsigned)(g < 1024 ? (g > 0 ? g : 1) : 1024), (unsigned)R);
+}
+
+// out[r][n] = d[n] * v[r][n]
+__global__ void pert_mul_kernel(const double2* __restrict__ d, const double2* __restrict__ v,
+                                double2* __restrict__ out, long long n) {
+  const long long off = (long long)blockIdx.y * n;
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT)
+    out[off + t] = cmul(d[t], v[off + t]);
+}
+
+// out = a - b + c (b or c may be NULL)
+__global__ void lin3_kernel(const double2* __restrict__ a, const double2* __restrict__ b,
+                            const double2* __restrict__ c, double2* __restrict__ out, long long total) {
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < total; t += (long long)gridDim.x * NT) {
+    double2 x = a[t];
+    if (b) {
+      const double2 y = b[t];
+      x.x -= y.x;
+      x.y -= y.y;
+    }
+    if (c) {
+      const double2 z = c[t];
+      x.x += z.x;
+      x.y += z.y;
+    }
+    out[t] = x;
+  }
+}
+
+// out[r][n] = s[r] * w[r][n]
+__global__ void scale_kernel(const double2* __restrict__ s, const double2* __restrict__ w,
+                             double2* __restrict__ out, long long n) {
+  const long long off = (long long)blockIdx.y * n;
+  const double2 sr = s[blockIdx.y];
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT)
+    out[off + t] = cmul(sr, w[off + t]);
+}
+
+// partial[(blockIdx.y * gridDim.x + blockIdx.x) * cnt + i] = sum over this CTA's slice of
+// conj(V_i[r][.]) w[r][.], r = blockIdx.y, V_i = V + i * vstride
+__global__ void __launch_bounds__(NT) multi_dot_kernel(const double2* __restrict__ V, long long vstride, int cnt,
+                                                       const double2* __restrict__ w, long long n,
+                                                       double2* __restrict__ partial) {
+  __shared__ double2 sh[NT / 32][kMaxVec];
+  const int r = blockIdx.y;
+  const double2* __restrict__ wr = w + (long long)r * n;
+  double2 acc[kMaxVec];
+#pragma unroll
+  for (int i = 0; i < kMaxVec; ++i) acc[i] = make_double2(0.0, 0.0);
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
+    const double2 x = wr[t];
+#pragma unroll
+    for (int i = 0; i < kMaxVec; ++i) {
+      if (i < cnt) {
+        const double2 v = V[i * vstride + (long long)r * n + t];
+        acc[i].x = fma(v.x, x.x, fma(v.y, x.y, acc[i].x));       // conj(v) * x
+        acc[i].y = fma(v.x, x.y, fma(-v.y, x.x, acc[i].y));
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kMaxVec; ++i) {
+    if (i < cnt) {
+      double2 a = acc[i];
+      for (int o = 16; o > 0; o >>= 1) {
+        a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+        a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+      }
+      if (lane == 0) sh[wid][i] = a;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < NT / 32; ++q) {
+      s.x += sh[q][threadIdx.x].x;
+      s.y += sh[q][threadIdx.x].y;
+    }
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * cnt + threadIdx.x] = s;
+  }
+}
+
+// out[r * cnt + i] = sum_p partial[(r * parts + p) * cnt + i]: one warp per output, lane l
+// sums p = l, l + 32, ..., then a shuffle tree (fixed order)
+__global__ void dot_finish_kernel(const double2* __restrict__ partial, int parts, int cnt,
+                                  double2* __restrict__ out) {
+  const int t = blockIdx.x;                                 // = r * cnt + i
+  const int r = t / cnt, i = t - r * cnt;
+  const int lane = threadIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  for (int p = lane; p < parts; p += 32) {
+    const double2 v = partial[((long long)r * parts + p) * cnt + i];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) out[t] = s;
+}
+
+// w[r][n] -= sum_{i < cnt} c[r * cnt + i] V_i[r][n]
+__global__ void __launch_bounds__(NT) multi_axpy_kernel(const double2* __restrict__ V, long long vstride, int cnt,
+                                                        const double2* __restrict__ c, double2* __restrict__ w,
+                                                        long long n) {
+  const int r = blockIdx.y;
+  const long long off = (long long)r * n;
+  double2 cr[kMaxVec];
+#pragma unroll
+  for (int i = 0; i < kMaxVec; ++i) cr[i] = i < cnt ? c[r * cnt + i] : make_double2(0.0, 0.0);
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
+    double2 x = w[off + t];
+#pragma unroll
+    for (int i = 0; i < kMaxVec; ++i) {
+      if (i < cnt) {
+        const double2 v = V[i * vstride + off + t];
+        x.x -= cr[i].x * v.x - cr[i].y * v.y;
+        x.y -= cr[i].x * v.y + cr[i].y * v.x;
+      }
+    }
+    w[off + t] = x;
+  }
+}
+
+// s[r] = 1 / sqrt(Re d[r]) (0 where that is not positive): the scale that normalises a
+// vector from its <w, w>
+__global__ void inv_norm_kernel(const double2* __restrict__ d, double2* __restrict__ s, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R) s[r] = make_double2(d[r].x > 0.0 ? 1.0 / sqrt(d[r].x) : 0.0, 0.0);
+}
+
+}  // namespace
+
+void vec_inv_norm(const double2* d, double2* s, int R, cudaStream_t st) {
+  inv_norm_kernel<<<(R + 127) / 128, 128, 0, st>>>(d, s, R);
+  count_launch();
+}
+
+void pert_mul(const double2* d, const double2* v, double2* out, long long n, int R, cudaStream_t st) {
+  pert_mul_kernel<<<grid_rhs(n, R), NT, 0, st>>>(d, v, out, n);
+  count_launch();
+}
+
+void vec_lin3(const double2* a, const double2* b, const double2* c, double2* out, long long total,
+              cudaStream_t st) {
+  lin3_kernel<<<grid_for(total), NT, 0, st>>>(a, b, c, out, total);
+  count_launch();
+}
+
+void vec_scale(const double2* s, const double2* w, double2* out, long long n, int R, cudaStream_t st) {
+  scale_kernel<<<grid_rhs(n, R), NT, 0, st>>>(s, w, out, n);
+  count_launch();
+}
+
+int multi_dot_parts(long long n) {
+  const long long g = (n + NT - 1) / NT;
+  return (int)(g < 512 ? (g > 0 ? g : 1) : 512);
+}
+
+void multi_dot(const double2* V, long long vstride, int cnt, const double2* w, long long n, int R,
+               double2* partial, double2* out, cudaStream_t st) {
+  const int parts = multi_dot_parts(n);
+  multi_dot_kernel<<<dim3(parts, R), NT, 0, st>>>(V, vstride, cnt, w, n, partial);
+  dot_finish_kernel<<<R * cnt, 32, 0, st>>>(partial, parts, cnt, out);
+  count_launch(2);
+}
+
+void multi_axpy(const double2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
+                cudaStream_t st) {
+  multi_axpy_kernel<<<grid_rhs(n, R), NT, 0, st>>>(V, vstride, cnt, c, w, n);
+  count_launch();
+}
+
+}  // namespace hz

@@ -64,6 +64,8 @@ SIGNATURES = {
     "hz_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_grad_layers": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "hz_solve_perturbed": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, _P, _P]),
     "hz_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_residual_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_get_info": (ctypes.c_int, [_P, ctypes.POINTER(hz_info)]),
@@ -264,6 +266,23 @@ class Plan:
         lam = torch.empty_like(g) if out is None else out
         _check(_lib.hz_solve_adjoint(self._h, g.data_ptr(), lam.data_ptr(), R), "hz_solve_adjoint")
         return lam
+
+    def solve_perturbed(self, dk2, f, rtol: float = 1e-8, max_iter: int = 200, restart: int = 20, out=None):
+        """u of the layered medium with a local k^2 perturbation dk2 (device complex128 of shape
+        (Nz, Ny, Nx)), by GMRES around this plan's layered solve (hz_solve_perturbed).
+        Returns (u, iterations, per-RHS true relative residual)."""
+        import torch
+        R = self._check_tensor(f)
+        if tuple(dk2.shape) != (self.nz, self.ny, self.nx) or dk2.dtype != torch.complex128 or not dk2.is_cuda \
+                or not dk2.is_contiguous():
+            raise ValueError("dk2 must be a contiguous CUDA complex128 tensor of shape (nz, ny, nx)")
+        u = torch.empty_like(f) if out is None else out
+        it = ctypes.c_int()
+        rel = np.empty(R, np.float64)
+        code = _lib.hz_solve_perturbed(self._h, dk2.data_ptr(), f.data_ptr(), u.data_ptr(), R, rtol, max_iter,
+                                       restart, ctypes.byref(it), rel.ctypes.data)
+        _check(code, "hz_solve_perturbed")
+        return u, it.value, rel
 
     def grad_layers(self, u, lam) -> np.ndarray:
         R = self._check_tensor(u)
