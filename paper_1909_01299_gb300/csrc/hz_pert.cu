@@ -65,48 +65,47 @@ __global__ void scale_kernel(const double2* __restrict__ s, const double2* __res
     out[off + t] = cmul(sr, w[off + t]);
 }
 
-// partial[(blockIdx.y * gridDim.x + blockIdx.x) * cnt + i] = sum over this CTA's slice of
-// conj(V_i[r][.]) w[r][.], r = blockIdx.y, V_i = V + i * vstride
-__global__ void __launch_bounds__(NT) multi_dot_kernel(const double2* __restrict__ V, long long vstride, int cnt,
+// partial[(blockIdx.y * gridDim.x + blockIdx.x) * CNT + i] = sum over this CTA's slice of
+// conj(V_i[r][.]) w[r][.], r = blockIdx.y, V_i = V + i * vstride.  CNT is a compile-time
+// count: with a run-time count the predicated-off FP64 arithmetic of the unrolled loop
+// still issues, and FP64 is the bound here (4 FMA per complex element and vector).
+template <int CNT>
+__global__ void __launch_bounds__(NT) multi_dot_kernel(const double2* __restrict__ V, long long vstride,
                                                        const double2* __restrict__ w, long long n,
                                                        double2* __restrict__ partial) {
-  __shared__ double2 sh[NT / 32][kMaxVec];
+  __shared__ double2 sh[NT / 32][CNT];
   const int r = blockIdx.y;
-  const double2* __restrict__ wr = w + (long long)r * n;
-  double2 acc[kMaxVec];
+  const long long off = (long long)r * n;
+  double2 acc[CNT];
 #pragma unroll
-  for (int i = 0; i < kMaxVec; ++i) acc[i] = make_double2(0.0, 0.0);
+  for (int i = 0; i < CNT; ++i) acc[i] = make_double2(0.0, 0.0);
   for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
-    const double2 x = wr[t];
+    const double2 x = w[off + t];
 #pragma unroll
-    for (int i = 0; i < kMaxVec; ++i) {
-      if (i < cnt) {
-        const double2 v = V[i * vstride + (long long)r * n + t];
-        acc[i].x = fma(v.x, x.x, fma(v.y, x.y, acc[i].x));       // conj(v) * x
-        acc[i].y = fma(v.x, x.y, fma(-v.y, x.x, acc[i].y));
-      }
+    for (int i = 0; i < CNT; ++i) {
+      const double2 v = V[i * vstride + off + t];
+      acc[i].x = fma(v.x, x.x, fma(v.y, x.y, acc[i].x));       // conj(v) * x
+      acc[i].y = fma(v.x, x.y, fma(-v.y, x.x, acc[i].y));
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kMaxVec; ++i) {
-    if (i < cnt) {
-      double2 a = acc[i];
-      for (int o = 16; o > 0; o >>= 1) {
-        a.x += __shfl_down_sync(0xffffffffu, a.x, o);
-        a.y += __shfl_down_sync(0xffffffffu, a.y, o);
-      }
-      if (lane == 0) sh[wid][i] = a;
+  for (int i = 0; i < CNT; ++i) {
+    double2 a = acc[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_down_sync(0xffffffffu, a.y, o);
     }
+    if (lane == 0) sh[wid][i] = a;
   }
   __syncthreads();
-  if (threadIdx.x < cnt) {
+  if (threadIdx.x < CNT) {
     double2 s = make_double2(0.0, 0.0);
     for (int q = 0; q < NT / 32; ++q) {
       s.x += sh[q][threadIdx.x].x;
       s.y += sh[q][threadIdx.x].y;
     }
-    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * cnt + threadIdx.x] = s;
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * CNT + threadIdx.x] = s;
   }
 }
 
@@ -130,24 +129,23 @@ __global__ void dot_finish_kernel(const double2* __restrict__ partial, int parts
   if (lane == 0) out[t] = s;
 }
 
-// w[r][n] -= sum_{i < cnt} c[r * cnt + i] V_i[r][n]
-__global__ void __launch_bounds__(NT) multi_axpy_kernel(const double2* __restrict__ V, long long vstride, int cnt,
+// w[r][n] -= sum_{i < CNT} c[r * CNT + i] V_i[r][n]  (compile-time CNT, as multi_dot)
+template <int CNT>
+__global__ void __launch_bounds__(NT) multi_axpy_kernel(const double2* __restrict__ V, long long vstride,
                                                         const double2* __restrict__ c, double2* __restrict__ w,
                                                         long long n) {
   const int r = blockIdx.y;
   const long long off = (long long)r * n;
-  double2 cr[kMaxVec];
+  double2 cr[CNT];
 #pragma unroll
-  for (int i = 0; i < kMaxVec; ++i) cr[i] = i < cnt ? c[r * cnt + i] : make_double2(0.0, 0.0);
+  for (int i = 0; i < CNT; ++i) cr[i] = c[r * CNT + i];
   for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
     double2 x = w[off + t];
 #pragma unroll
-    for (int i = 0; i < kMaxVec; ++i) {
-      if (i < cnt) {
-        const double2 v = V[i * vstride + off + t];
-        x.x -= cr[i].x * v.x - cr[i].y * v.y;
-        x.y -= cr[i].x * v.y + cr[i].y * v.x;
-      }
+    for (int i = 0; i < CNT; ++i) {
+      const double2 v = V[i * vstride + off + t];
+      x.x = fma(-cr[i].x, v.x, fma(cr[i].y, v.y, x.x));
+      x.y = fma(-cr[i].x, v.y, fma(-cr[i].y, v.x, x.y));
     }
     w[off + t] = x;
   }
@@ -188,18 +186,60 @@ int multi_dot_parts(long long n) {
   return (int)(g < 512 ? (g > 0 ? g : 1) : 512);
 }
 
+template <int CNT>
+void multi_dot_t(const double2* V, long long vstride, const double2* w, long long n, int R, double2* partial,
+                 double2* out, cudaStream_t st) {
+  const int parts = multi_dot_parts(n);
+  multi_dot_kernel<CNT><<<dim3(parts, R), NT, 0, st>>>(V, vstride, w, n, partial);
+  dot_finish_kernel<<<R * CNT, 32, 0, st>>>(partial, parts, CNT, out);
+  count_launch(2);
+}
+template <int CNT>
+void multi_axpy_t(const double2* V, long long vstride, const double2* c, double2* w, long long n, int R,
+                  cudaStream_t st) {
+  multi_axpy_kernel<CNT><<<grid_rhs(n, R), NT, 0, st>>>(V, vstride, c, w, n);
+  count_launch();
+}
+
+// run-time count -> the compile-time instantiation
+template <template <int> class Op, int C = 1>
+struct CountDispatch {
+  template <typename... A>
+  static void run(int cnt, A... a) {
+    if (cnt == C) Op<C>::go(a...);
+    else CountDispatch<Op, C + 1>::run(cnt, a...);
+  }
+};
+template <template <int> class Op>
+struct CountDispatch<Op, kMaxVec + 1> {
+  template <typename... A>
+  static void run(int, A...) {}
+};
+template <int C>
+struct DotOp {
+  static void go(const double2* V, long long vs, const double2* w, long long n, int R, double2* p, double2* o,
+                 cudaStream_t st) {
+    multi_dot_t<C>(V, vs, w, n, R, p, o, st);
+  }
+};
+template <int C>
+struct AxpyOp {
+  static void go(const double2* V, long long vs, const double2* c, double2* w, long long n, int R,
+                 cudaStream_t st) {
+    multi_axpy_t<C>(V, vs, c, w, n, R, st);
+  }
+};
+
 void multi_dot(const double2* V, long long vstride, int cnt, const double2* w, long long n, int R,
                double2* partial, double2* out, cudaStream_t st) {
-  const int parts = multi_dot_parts(n);
-  multi_dot_kernel<<<dim3(parts, R), NT, 0, st>>>(V, vstride, cnt, w, n, partial);
-  dot_finish_kernel<<<R * cnt, 32, 0, st>>>(partial, parts, cnt, out);
-  count_launch(2);
+  if (cnt < 1 || cnt > kMaxVec) return;
+  CountDispatch<DotOp>::run(cnt, V, vstride, w, n, R, partial, out, st);
 }
 
 void multi_axpy(const double2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
                 cudaStream_t st) {
-  multi_axpy_kernel<<<grid_rhs(n, R), NT, 0, st>>>(V, vstride, cnt, c, w, n);
-  count_launch();
+  if (cnt < 1 || cnt > kMaxVec) return;
+  CountDispatch<AxpyOp>::run(cnt, V, vstride, c, w, n, R, st);
 }
 
 }  // namespace hz
