@@ -92,34 +92,34 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
 
 // Step 5 on the mixed path with several interfaces per axis: every slot contracts the
 // whole row or column (the whole-axis eigenvector rows), so one pass over V accumulates all
-// nslots sums (nslots <= kMultiSlots) in FP32 instead of reading V once per slot.
-constexpr int kMultiSlots = 8;
+// nslots sums (2 <= nslots <= 8, a compile-time count) in FP32 instead of reading V once
+// per slot.
 
+template <int NS>
 __global__ void contract_rows_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
-                                           const float2* __restrict__ coef, int nrows, int ncols, int nslots,
+                                           const float2* __restrict__ coef, int nrows, int ncols,
                                            long long nplanes) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nplanes * (long long)ncols) return;
   const int j = (int)(t % ncols);
   const long long plane = t / ncols;
   const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
-  float2 acc[kMultiSlots];
+  float2 acc[NS];
 #pragma unroll
-  for (int q = 0; q < kMultiSlots; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
   for (int i = 0; i < nrows; ++i) {
     const float2 x = to_c64(v[(long long)i * ncols]);
 #pragma unroll
-    for (int q = 0; q < kMultiSlots; ++q)
-      if (q < nslots) acc[q] = cfma32(coef[(long long)q * nrows + i], x, acc[q]);
+    for (int q = 0; q < NS; ++q) acc[q] = cfma32(coef[(long long)q * nrows + i], x, acc[q]);
   }
 #pragma unroll
-  for (int q = 0; q < kMultiSlots; ++q)
-    if (q < nslots) out[(plane * nslots + q) * (long long)ncols + j] = to_c128(acc[q]);
+  for (int q = 0; q < NS; ++q) out[(plane * NS + q) * (long long)ncols + j] = to_c128(acc[q]);
 }
 
 // One warp per (plane, row i): lanes stride over the row, then a shuffle reduction per slot.
+template <int NS>
 __global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
-                                           const float2* __restrict__ coef, int nrows, int ncols, int nslots,
+                                           const float2* __restrict__ coef, int nrows, int ncols,
                                            long long nplanes) {
   const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -127,24 +127,21 @@ __global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double
   const int i = (int)(t % nrows);
   const long long plane = t / nrows;
   const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
-  float2 acc[kMultiSlots];
+  float2 acc[NS];
 #pragma unroll
-  for (int q = 0; q < kMultiSlots; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
   for (int j = lane; j < ncols; j += 32) {
     const float2 x = to_c64(v[j]);
 #pragma unroll
-    for (int q = 0; q < kMultiSlots; ++q)
-      if (q < nslots) acc[q] = cfma32(coef[(long long)q * ncols + j], x, acc[q]);
+    for (int q = 0; q < NS; ++q) acc[q] = cfma32(coef[(long long)q * ncols + j], x, acc[q]);
   }
 #pragma unroll
-  for (int q = 0; q < kMultiSlots; ++q) {
-    if (q < nslots) {
-      for (int o = 16; o > 0; o >>= 1) {
-        acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
-        acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
-      }
-      if (lane == 0) out[(plane * nslots + q) * (long long)nrows + i] = to_c128(acc[q]);
+  for (int q = 0; q < NS; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+      acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
     }
+    if (lane == 0) out[(plane * NS + q) * (long long)nrows + i] = to_c128(acc[q]);
   }
 }
 
@@ -444,21 +441,33 @@ void contract_cols_t(const double2* V, double2* out, const C* coef, const int2* 
   count_launch();
 }
 
-bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
-                  int nslots, long long nplanes, cudaStream_t st) {
-  if (nslots < 2 || nslots > kMultiSlots) return false;
+template <int NS>
+void contract_all_t(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+                    long long nplanes, cudaStream_t st) {
   if (rows) {
     const long long n = nplanes * (long long)ncols;
-    if (n == 0) return true;
-    contract_rows_multi_kernel<<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, nrows, ncols, nslots, nplanes);
+    if (n == 0) return;
+    contract_rows_multi_kernel<NS><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, nrows, ncols, nplanes);
   } else {
     const long long n = nplanes * (long long)nrows;
-    if (n == 0) return true;
-    contract_cols_multi_kernel<<<blocks_for(n * 32, 256), 256, 0, st>>>(V, out, coef, nrows, ncols, nslots,
-                                                                       nplanes);
+    if (n == 0) return;
+    contract_cols_multi_kernel<NS><<<blocks_for(n * 32, 256), 256, 0, st>>>(V, out, coef, nrows, ncols, nplanes);
   }
   count_launch();
-  return true;
+}
+
+bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st) {
+  switch (nslots) {        // the slot count is a compile-time constant of the kernels
+    case 2: contract_all_t<2>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 3: contract_all_t<3>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 4: contract_all_t<4>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 5: contract_all_t<5>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 6: contract_all_t<6>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 7: contract_all_t<7>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    case 8: contract_all_t<8>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
+    default: return false;
+  }
 }
 
 void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
