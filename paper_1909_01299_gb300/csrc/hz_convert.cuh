@@ -25,6 +25,19 @@ __device__ __forceinline__ float f64_to_f32(double x) {
   return __uint_as_float(sign | (uint32_t)(full >> 29));       // a rounding carry moves into the exponent
 }
 
+// FP64 -> FP32 by truncation, with fewer operations, for splitting data into TF32 hi / lo
+// parts: the sign, the exponent rebiased (for exponents 897..1150 the low 8 bits of the FP64
+// exponent with the top bit flipped are the FP32 exponent) and the top 23 mantissa bits
+// (a funnel shift).  |x| below the FP32 normal range -> signed 0; |x| must stay below
+// 2^128 (non-finite or larger inputs give finite garbage; the refinement's FP64 residual,
+// computed from the FP64 data, still reports a non-finite input).
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  uint32_t u = (__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u;
+  u = ((hi & 0x7ff00000u) < 0x38100000u) ? 0u : u;
+  return __uint_as_float(u | (hi & 0x80000000u));
+}
+
 // FP32 -> FP64 (exact for normal numbers; FP32 denormals -> signed 0).
 __device__ __forceinline__ double f32_to_f64(float v) {
   const uint32_t u = __float_as_uint(v);

@@ -249,7 +249,8 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
         double x0, x1, x2, x3;
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * RAW_ROWB + c * 32));
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * RAW_ROWB + c * 32 + 16));
-        const float f[4] = {f64_to_f32(x0), f64_to_f32(x1), f64_to_f32(x2), f64_to_f32(x3)};
+        const float f[4] = {f64_to_f32_trunc(x0), f64_to_f32_trunc(x1), f64_to_f32_trunc(x2),
+                            f64_to_f32_trunc(x3)};
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
