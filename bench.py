@@ -201,6 +201,26 @@ def oracle_sample(budget_s: float = 12.0, max_runs: int = 3, w=None, of: str = "
                       f"cores, per-mode z solves single-threaded"}, best, w.unknowns
 
 
+def oracle_single_thread(workload: str, timeout_s: float = 90.0):
+    """The same oracle sample with one BLAS thread, in a child process (thread counts are
+    fixed when numpy loads); None if it does not finish in time."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench\n"
+            "from paper_1909_01299_gb300 import workloads as W\n"
+            f"w = W.NAMED[{workload!r}]()\n"
+            "r = bench.oracle_sample(budget_s=30.0, max_runs=1, w=type(w)(**{**w.__dict__, 'f': w.f[:1]}), "
+            "of=str(w.nrhs))[0]\n"
+            "r['cores'] = 1\n"
+            "print(json.dumps(r))\n")
+    try:
+        res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=timeout_s)
+        return json.loads(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -334,6 +354,9 @@ def run_hz(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _ = oracle_sample()
+        one = oracle_single_thread("pml160")
+        if one:
+            cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
