@@ -177,7 +177,7 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
   const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
 
-  // issue the FP64 rows of chunk c (16 complex per row) into raw[c & 1]
+  // issue the FP64 rows of chunk c (8 complex per row) into raw[c & 1]
   auto load_raw = [&](int c) {
     const uint32_t dst = raw0 + (c & 1) * RAW_BYTES;
 #pragma unroll
@@ -191,7 +191,7 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       cp_async16(dst + r * RAW_ROWB + cc * 16, src, ok);
     }
   };
-  // issue the table rows (hi and lo) of chunk c into bop[c & 1], 128B-swizzled
+  // issue the table rows (hi and lo) of chunk c into bop[c & 1], 64B-swizzled
   auto load_b = [&](int c) {
     const uint32_t bh = bop0 + (c & 1) * BSTAGE, bl = bh + B_BYTES;
     for (int task = tid; task < nt * (ROWB / 16); task += TC_THREADS) {
