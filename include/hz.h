@@ -169,7 +169,9 @@ hz_status hz_plan_set_options(hz_plan_t plan, const hz_options *opts);
 hz_status hz_solve(hz_plan_t plan, const hz_c128 *f_dev, hz_c128 *u_dev, int nrhs);
 
 /* The same solve with HOST arrays f_host, u_host (pageable or pinned): the call
- * copies f to the device, solves and copies u back. */
+ * copies f to the device, solves and copies u back.  With nrhs >= 2 the RHS are solved in
+ * two halves, the second half's upload and the first half's download overlapping the
+ * solves (pinned buffers make the copies asynchronous). */
 hz_status hz_solve_host(hz_plan_t plan, const hz_c128 *f_host, hz_c128 *u_host, int nrhs);
 
 /* lam = A^{-H} g.  A is complex symmetric (Eq. (fdmtr) with symmetric K_d and

@@ -90,6 +90,8 @@ struct hz_plan_s {
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cst = nullptr;                  // host <-> device copies overlapped with solves
+  cudaEvent_t ev_in = nullptr;
   int real_cm = 1;
   AxisDev dx, dy;
   // z tables
@@ -963,8 +965,12 @@ void release(hz_plan_t p) {
   if (p->side) cudaStreamDestroy(p->side);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->cst) cudaStreamDestroy(p->cst);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
   p->side = nullptr;
   p->ev_fork = p->ev_join = nullptr;
+  p->cst = nullptr;
+  p->ev_in = nullptr;
 }
 
 }  // namespace
@@ -1389,14 +1395,42 @@ hz_status hz_solve_host(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
   if (!p || !f || !u || nrhs < 1) return HZ_ERR_ARG;
   try {
     ensure_ws(p, nrhs);
-    const size_t bytes = sizeof(double2) * (size_t)p->nx * p->ny * p->nz * nrhs;
+    const size_t per = (size_t)p->nx * p->ny * p->nz;          // complex values per RHS
     double2* fd = ensure_extra(p, p->ws.F2, p->ws.f2_cap, nrhs);
     double2* ud = ensure_extra(p, p->ws.HU, p->ws.hu_cap, nrhs);
-    ck(cudaMemcpyAsync(fd, f, bytes, cudaMemcpyHostToDevice, p->st));
-    solve_full(p, fd, ud, nrhs, 0);
-    ck(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, p->st));
-    ck(cudaStreamSynchronize(p->st));
+    const double2* fh = reinterpret_cast<const double2*>(f);
+    double2* uh = reinterpret_cast<double2*>(u);
+    if (nrhs < 2) {
+      ck(cudaMemcpyAsync(fd, fh, sizeof(double2) * per * nrhs, cudaMemcpyHostToDevice, p->st));
+      solve_full(p, fd, ud, nrhs, 0);
+      ck(cudaMemcpyAsync(uh, ud, sizeof(double2) * per * nrhs, cudaMemcpyDeviceToHost, p->st));
+      ck(cudaStreamSynchronize(p->st));
+    } else {
+      // two halves: the second half's input arrives and the first half's result leaves on a
+      // copy stream while the other half is solved
+      if (!p->cst) {
+        ck(cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
+        ck(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+      }
+      const int R0 = (nrhs + 1) / 2, R1 = nrhs - R0;
+      const size_t b0 = sizeof(double2) * per * R0, b1 = sizeof(double2) * per * R1;
+      ck(cudaMemcpyAsync(fd, fh, b0, cudaMemcpyHostToDevice, p->st));
+      ck(cudaMemcpyAsync(fd + per * R0, fh + per * R0, b1, cudaMemcpyHostToDevice, p->cst));
+      ck(cudaEventRecord(p->ev_in, p->cst));
+      solve_full(p, fd, ud, R0, 0);                               // returns with the solve done
+      const int ref0 = p->info.refinements;
+      const double rel0 = p->info.rel_residual;
+      ck(cudaMemcpyAsync(uh, ud, b0, cudaMemcpyDeviceToHost, p->cst));
+      ck(cudaStreamWaitEvent(p->st, p->ev_in, 0));
+      solve_full(p, fd + per * R0, ud + per * R0, R1, 0);
+      ck(cudaMemcpyAsync(uh + per * R0, ud + per * R0, b1, cudaMemcpyDeviceToHost, p->st));
+      ck(cudaStreamSynchronize(p->st));
+      ck(cudaStreamSynchronize(p->cst));
+      p->info.refinements = std::max(ref0, p->info.refinements);
+      p->info.rel_residual = std::max(rel0, p->info.rel_residual);
+    }
   } catch (const Fail& e) {
+    if (p->cst) cudaStreamSynchronize(p->cst);             // no copy may touch the caller's buffers later
     return e.s;
   }
   return HZ_OK;
