@@ -92,10 +92,13 @@ typedef struct {
 } hz_blocks;
 
 /* Options.  precision: HZ_FP64 (all arithmetic FP64) or HZ_MIXED (x/y
- * eigen-transforms on FP32 tensor cores; z solves, interface solves and the
- * residual in FP64; FP64 iterative refinement until the relative residual
- * ||M f - A u|| / ||M f|| <= rtol for every RHS, at most max_refine
- * corrections).  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+ * eigen-transforms in FP32, the bulk ones on the tensor cores; z solves, the interface
+ * residual and the refinement residual in FP64; FP64 iterative refinement until the
+ * relative residual ||M f - A u|| / ||M f|| <= rtol for every RHS, at most max_refine
+ * corrections; HZ_ERR_NOT_CONVERGED otherwise).  The mixed path carries transformed data
+ * in FP32: values below about 1e-30 or above 1e30 lose precision there (the refinement
+ * then reports non-convergence rather than a wrong answer), so scale such right-hand
+ * sides.  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
 typedef struct {
   int precision;
   double rtol;
