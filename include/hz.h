@@ -188,7 +188,8 @@ hz_status hz_solve_adjoint(hz_plan_t plan, const hz_c128 *g_dev, hz_c128 *lam_de
  *     -div(sigma grad u) - (k^2(z) + dk2(x, y, z)) u = f,  i.e.  (A - M diag(dk2)) u = M f.
  * Solved by restarted GMRES(restart) on the second-kind form u - S(dk2 u) = S f, where S is
  * this plan's layered solve (FP64 or mixed, per the plan's options; the Born term S f is the
- * initial guess).  dk2_dev: device complex [Nz][Ny][Nx], node-based, the same for every RHS;
+ * initial guess; mixed plans keep the Krylov basis in complex64, combined in FP32 against
+ * FP64 vectors, while the restart residuals and the iterate stay FP64).  dk2_dev: device complex [Nz][Ny][Nx], node-based, the same for every RHS;
  * f_dev, u_dev: as hz_solve (distinct buffers).  Stops when every RHS's GMRES residual is
  * <= rtol ||S f||; each iteration is one layered solve of all RHS.  iters_out (may be NULL):
  * iterations used; relres_out (may be NULL, else nrhs doubles): the true relative residual

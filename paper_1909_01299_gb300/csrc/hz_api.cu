@@ -1450,10 +1450,17 @@ hz_status hz_solve_adjoint(hz_plan_t p, const hz_c128* g, hz_c128* lam, int nrhs
   return HZ_OK;
 }
 
-hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128* f_dev, hz_c128* u_dev, int nrhs,
-                             double rtol, int max_iter, int restart, int* iters_out, double* relres_out) {
-  if (!p || !dk2_dev || !f_dev || !u_dev || nrhs < 1 || !(rtol > 0.0) || max_iter < 1) return HZ_ERR_ARG;
-  if (static_cast<const void*>(f_dev) == static_cast<const void*>(u_dev)) return HZ_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// The GMRES of hz_solve_perturbed with a Krylov basis of element type VT: double2 (FP64
+// plans) or float2 (mixed plans: the basis in complex64, combined in FP32 against FP64
+// vectors; the restart residuals, the solves and the iterate stay FP64, so the restarts
+// correct what the FP32 basis loses).
+template <typename VT>
+hz_status perturbed_impl(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128* f_dev, hz_c128* u_dev, int nrhs,
+                         double rtol, int max_iter, int restart, int* iters_out, double* relres_out) {
   using cplx = std::complex<double>;
   const int m = restart < 1 ? 20 : std::min(restart, 200);
   const int R = nrhs;
@@ -1473,7 +1480,8 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
     const double2* d = reinterpret_cast<const double2*>(dk2_dev);
     const double2* f = reinterpret_cast<const double2*>(f_dev);
     double2* X = reinterpret_cast<double2*>(u_dev);
-    double2* V = local((size_t)(m + 1) * vol);              // Krylov basis [i][r][n]
+    VT* V = dalloc<VT>(p, (size_t)(m + 1) * vol);            // Krylov basis [i][r][n]
+    mine.push_back(V);
     double2* B = local(vol);                                // S f
     double2* T = local(vol);
     double2* Wv = local(vol);
@@ -1492,7 +1500,7 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
       for (int q = 0; q < R * cnt; ++q) out[q] = cplx(hbuf[q].x, hbuf[q].y);
       return out;
     };
-    auto axpy_host = [&](const double2* Vb, int cnt, const std::vector<cplx>& c, double2* w) {   // w -= V c
+    auto axpy_host = [&](const VT* Vb, int cnt, const std::vector<cplx>& c, double2* w) {   // w -= V c
       for (int q = 0; q < R * cnt; ++q) hbuf[q] = make_double2(c[q].real(), c[q].imag());
       ck(cudaMemcpyAsync(coef, hbuf.data(), sizeof(double2) * R * cnt, cudaMemcpyHostToDevice, st));
       hz::multi_axpy(Vb, vol, cnt, coef, w, n, R, st);
@@ -1503,7 +1511,7 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
       for (int r = 0; r < R; ++r) o[r] = std::sqrt(std::max(q[r].real(), 0.0));
       return o;
     };
-    auto scale_into = [&](const std::vector<double>& s, const double2* w, double2* out) {
+    auto scale_into = [&](const std::vector<double>& s, const double2* w, VT* out) {
       for (int r = 0; r < R; ++r) hbuf[r] = make_double2(s[r], 0.0);
       ck(cudaMemcpyAsync(coef, hbuf.data(), sizeof(double2) * R, cudaMemcpyHostToDevice, st));
       hz::vec_scale(coef, w, out, n, R, st);
@@ -1519,14 +1527,14 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
       // r0 = B - L(X) = B - X + S(dk2 X)
       hz::pert_mul(d, X, T, n, R, st);
       solve_full(p, T, Wv, R, 0);
-      hz::vec_lin3(B, X, Wv, V, vol, st);
-      const std::vector<double> beta = norms(V);
+      hz::vec_lin3(B, X, Wv, T, vol, st);
+      const std::vector<double> beta = norms(T);
       conv = true;
       for (int r = 0; r < R; ++r) conv = conv && beta[r] <= rtol * bnorm[r];
       if (conv) break;
       std::vector<double> inv(R);
       for (int r = 0; r < R; ++r) inv[r] = beta[r] > 0.0 ? 1.0 / beta[r] : 0.0;
-      scale_into(inv, V, V);
+      scale_into(inv, T, V);
       std::fill(H.begin(), H.end(), cplx(0));
       std::fill(g.begin(), g.end(), cplx(0));
       for (int r = 0; r < R; ++r) g[(size_t)r * (m + 1)] = beta[r];
@@ -1535,7 +1543,7 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
         // Arnoldi on K = S dk2 (L = I - K has the same Krylov space; its Hessenberg matrix is
         // I - H_K): K v_j carries no large component along v_j, so one Gram-Schmidt pass is
         // usually enough
-        double2* Vj = V + (size_t)j * vol;
+        VT* Vj = V + (size_t)j * vol;
         hz::pert_mul(d, Vj, T, n, R, st);
         solve_full(p, T, Wv, R, 0);
         ++iters;
@@ -1640,6 +1648,20 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
   if (iters_out) *iters_out = iters;
   return status;
 }
+
+}  // namespace
+
+extern "C" {
+
+hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128* f_dev, hz_c128* u_dev, int nrhs,
+                             double rtol, int max_iter, int restart, int* iters_out, double* relres_out) {
+  if (!p || !dk2_dev || !f_dev || !u_dev || nrhs < 1 || !(rtol > 0.0) || max_iter < 1) return HZ_ERR_ARG;
+  if (static_cast<const void*>(f_dev) == static_cast<const void*>(u_dev)) return HZ_ERR_ARG;
+  if (p->opts.precision == HZ_MIXED)
+    return perturbed_impl<float2>(p, dk2_dev, f_dev, u_dev, nrhs, rtol, max_iter, restart, iters_out, relres_out);
+  return perturbed_impl<double2>(p, dk2_dev, f_dev, u_dev, nrhs, rtol, max_iter, restart, iters_out, relres_out);
+}
+
 
 hz_status hz_grad_layers(hz_plan_t p, const hz_c128* u, const hz_c128* lam, int nrhs, hz_c128* G_host) {
   if (!p || !u || !lam || !G_host || nrhs < 1) return HZ_ERR_ARG;

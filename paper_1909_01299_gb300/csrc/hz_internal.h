@@ -223,6 +223,13 @@ void multi_dot(const double2* V, long long vstride, int cnt, const double2* w, l
 // w[r][n] -= sum_{i < cnt} c[r * cnt + i] V_i[r][n], cnt <= kMaxVec
 void multi_axpy(const double2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
                 cudaStream_t st);
+// FP32-basis forms (mixed plans): the basis V is complex64, the other vector stays FP64
+void pert_mul(const double2* d, const float2* v, double2* out, long long n, int R, cudaStream_t st);
+void vec_scale(const double2* s, const double2* w, float2* out, long long n, int R, cudaStream_t st);
+void multi_dot(const float2* V, long long vstride, int cnt, const double2* w, long long n, int R,
+               double2* partial, double2* out, cudaStream_t st);
+void multi_axpy(const float2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
+                cudaStream_t st);
 
 struct IfaceArgs {
   int nx = 0, ny = 0, nz = 0, nrhs = 0, nIx = 0, nIy = 0;

@@ -8,6 +8,7 @@
 // multi-vector dot products and updates take up to kMaxVec basis vectors per pass so that
 // the vector they are applied to is read once per pass, and the dot products reduce in a
 // fixed order (per-CTA partial sums, then one ordered sum per output).
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
@@ -151,6 +152,94 @@ __global__ void __launch_bounds__(NT) multi_axpy_kernel(const double2* __restric
   }
 }
 
+// ---- FP32 Krylov basis (mixed plans): the basis is stored and combined in FP32, the
+// vector it is applied to stays FP64 (converted with integer operations, no FP64 work) ----
+
+// out[r][n] = d[n] * v[r][n], v FP32
+__global__ void pert_mul32_kernel(const double2* __restrict__ d, const float2* __restrict__ v,
+                                  double2* __restrict__ out, long long n) {
+  const long long off = (long long)blockIdx.y * n;
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT)
+    out[off + t] = cmul(d[t], to_c128(v[off + t]));
+}
+
+// out32[r][n] = s[r] * w[r][n] rounded to FP32
+__global__ void scale32_kernel(const double2* __restrict__ s, const double2* __restrict__ w,
+                               float2* __restrict__ out, long long n) {
+  const long long off = (long long)blockIdx.y * n;
+  const float2 sr = to_c64(s[blockIdx.y]);
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
+    const float2 x = to_c64(w[off + t]);
+    out[off + t] = make_float2(fmaf(sr.x, x.x, -sr.y * x.y), fmaf(sr.x, x.y, sr.y * x.x));
+  }
+}
+
+template <int CNT>
+__global__ void __launch_bounds__(NT) multi_dot32_kernel(const float2* __restrict__ V, long long vstride,
+                                                         const double2* __restrict__ w, long long n,
+                                                         double2* __restrict__ partial) {
+  __shared__ double2 sh[NT / 32][CNT];
+  const int r = blockIdx.y;
+  const long long off = (long long)r * n;
+  float2 acc[CNT];
+#pragma unroll
+  for (int i = 0; i < CNT; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
+    const float2 x = to_c64(w[off + t]);
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const float2 v = V[i * vstride + off + t];
+      acc[i].x = fmaf(v.x, x.x, fmaf(v.y, x.y, acc[i].x));       // conj(v) * x
+      acc[i].y = fmaf(v.x, x.y, fmaf(-v.y, x.x, acc[i].y));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < CNT; ++i) {
+    double2 a = to_c128(acc[i]);                           // the reduction across threads in FP64
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+    }
+    if (lane == 0) sh[wid][i] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < CNT) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < NT / 32; ++q) {
+      s.x += sh[q][threadIdx.x].x;
+      s.y += sh[q][threadIdx.x].y;
+    }
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * CNT + threadIdx.x] = s;
+  }
+}
+
+// w[r][n] -= sum_{i < CNT} c[r * CNT + i] V_i[r][n]: the sum in FP32, the update in FP64
+template <int CNT>
+__global__ void __launch_bounds__(NT) multi_axpy32_kernel(const float2* __restrict__ V, long long vstride,
+                                                          const double2* __restrict__ c, double2* __restrict__ w,
+                                                          long long n) {
+  const int r = blockIdx.y;
+  const long long off = (long long)r * n;
+  float2 cr[CNT];
+#pragma unroll
+  for (int i = 0; i < CNT; ++i) cr[i] = to_c64(c[r * CNT + i]);
+  for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
+    float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const float2 v = V[i * vstride + off + t];
+      sum.x = fmaf(cr[i].x, v.x, fmaf(-cr[i].y, v.y, sum.x));
+      sum.y = fmaf(cr[i].x, v.y, fmaf(cr[i].y, v.x, sum.y));
+    }
+    const double2 sd = to_c128(sum);
+    double2 x = w[off + t];
+    x.x -= sd.x;
+    x.y -= sd.y;
+    w[off + t] = x;
+  }
+}
+
 // s[r] = 1 / sqrt(Re d[r]) (0 where that is not positive): the scale that normalises a
 // vector from its <w, w>
 __global__ void inv_norm_kernel(const double2* __restrict__ d, double2* __restrict__ s, int R) {
@@ -186,6 +275,16 @@ int multi_dot_parts(long long n) {
   return (int)(g < 512 ? (g > 0 ? g : 1) : 512);
 }
 
+void pert_mul(const double2* d, const float2* v, double2* out, long long n, int R, cudaStream_t st) {
+  pert_mul32_kernel<<<grid_rhs(n, R), NT, 0, st>>>(d, v, out, n);
+  count_launch();
+}
+
+void vec_scale(const double2* s, const double2* w, float2* out, long long n, int R, cudaStream_t st) {
+  scale32_kernel<<<grid_rhs(n, R), NT, 0, st>>>(s, w, out, n);
+  count_launch();
+}
+
 template <int CNT>
 void multi_dot_t(const double2* V, long long vstride, const double2* w, long long n, int R, double2* partial,
                  double2* out, cudaStream_t st) {
@@ -215,6 +314,35 @@ struct CountDispatch<Op, kMaxVec + 1> {
   template <typename... A>
   static void run(int, A...) {}
 };
+template <int CNT>
+void multi_dot32_t(const float2* V, long long vstride, const double2* w, long long n, int R, double2* partial,
+                   double2* out, cudaStream_t st) {
+  const int parts = multi_dot_parts(n);
+  multi_dot32_kernel<CNT><<<dim3(parts, R), NT, 0, st>>>(V, vstride, w, n, partial);
+  dot_finish_kernel<<<R * CNT, 32, 0, st>>>(partial, parts, CNT, out);
+  count_launch(2);
+}
+template <int CNT>
+void multi_axpy32_t(const float2* V, long long vstride, const double2* c, double2* w, long long n, int R,
+                    cudaStream_t st) {
+  multi_axpy32_kernel<CNT><<<grid_rhs(n, R), NT, 0, st>>>(V, vstride, c, w, n);
+  count_launch();
+}
+template <int C>
+struct Dot32Op {
+  static void go(const float2* V, long long vs, const double2* w, long long n, int R, double2* p, double2* o,
+                 cudaStream_t st) {
+    multi_dot32_t<C>(V, vs, w, n, R, p, o, st);
+  }
+};
+template <int C>
+struct Axpy32Op {
+  static void go(const float2* V, long long vs, const double2* c, double2* w, long long n, int R,
+                 cudaStream_t st) {
+    multi_axpy32_t<C>(V, vs, c, w, n, R, st);
+  }
+};
+
 template <int C>
 struct DotOp {
   static void go(const double2* V, long long vs, const double2* w, long long n, int R, double2* p, double2* o,
@@ -240,6 +368,18 @@ void multi_axpy(const double2* V, long long vstride, int cnt, const double2* c, 
                 cudaStream_t st) {
   if (cnt < 1 || cnt > kMaxVec) return;
   CountDispatch<AxpyOp>::run(cnt, V, vstride, c, w, n, R, st);
+}
+
+void multi_dot(const float2* V, long long vstride, int cnt, const double2* w, long long n, int R,
+               double2* partial, double2* out, cudaStream_t st) {
+  if (cnt < 1 || cnt > kMaxVec) return;
+  CountDispatch<Dot32Op>::run(cnt, V, vstride, w, n, R, partial, out, st);
+}
+
+void multi_axpy(const float2* V, long long vstride, int cnt, const double2* c, double2* w, long long n, int R,
+                cudaStream_t st) {
+  if (cnt < 1 || cnt > kMaxVec) return;
+  CountDispatch<Axpy32Op>::run(cnt, V, vstride, c, w, n, R, st);
 }
 
 }  // namespace hz
