@@ -1,5 +1,7 @@
 // C ABI of the hz library: plan creation (1D operators, eigen-decompositions,
-// device tables, z factors) and the solve orchestration of steps 1-7 of Sec. 2.
+// device tables, z factors), the solve orchestration of steps 1-7 of Sec. 2, the
+// mixed-precision refinement, adjoint and layer gradient, batched graph launches, the
+// autotuners and the GMRES of the locally perturbed medium.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

@@ -14,8 +14,10 @@
 // and table entry c + i d the table stores (c, d - c, c + d) and
 //   Re = sum c (ar + ai) - sum (c + d) ai,   Im = sum c (ar + ai) + sum (d - c) ar,
 // three DFMA per complex multiply-add instead of four.  Real tables (blocks whose
-// steps are all real) take two DFMA.  FP32 variant (mixed path): the same tiling in
-// FFMA with the four-product form on an FP32 copy of the tables.
+// steps are all real) take two DFMA; uniform blocks (sine eigenvectors) fold or unfold
+// the data around the block centre and contract over half the block (run_tile_sym).
+// FP32 variant (mixed path): the same tiling in FFMA with the four-product form on an
+// FP32 copy of the tables.
 #include "hz_convert.cuh"
 #include "hz_internal.h"
 
