@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="right-hand sides of an extra workload (default: the workload's own count)")
     ap.add_argument("--workload", default="pml160",
                     choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48", "scaling", "perturbed160"],
                     help="pml160 is the benchmark workload; the others are extra measurements")
@@ -483,10 +485,26 @@ def run_extra(args):
                     "graph_replay_ms": batch.info()["last_ms"], "launches_per_replay":
                     batch.info()["launches_per_replay"], "rel_residual_max": float(np.max(rel)),
                     "plan_seconds": plan_s})
+        if not args.no_cpu_baseline:
+            # the oracle on a 4-model subset (first 4 models, omega = 1, 1 RHS each), extrapolated
+            # to the batch at the subset's unknowns/s
+            from oracle import hz_oracle as O
+            done, secs = 0, 0.0
+            for w, _ in items[:4]:
+                P = O.Problem.from_workload(w)
+                A, _ = O.assemble(P)
+                t1 = time.perf_counter()
+                O.block_solve(P, w.f[:1], A)
+                secs += time.perf_counter() - t1
+                done += w.unknowns
+            out["cpu_baseline"] = {"value": done / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"4-model subset of the batch ({done} unknowns, 1 RHS each, omega = 1), "
+                                             f"{secs:.1f} s; extrapolated to the batch: "
+                                             f"{unknowns / (done / secs):.0f} s per batch"}
     else:
         gen = {"uniform320": W.uniform_320x320x200, "adjoint192": W.adjoint_192x192x128,
                "uniform32": W.single_block_32, "pml160": W.pml_160x160x128}[args.workload]
-        w = gen()
+        w = gen(args.nrhs) if args.nrhs else gen()
         f = torch.from_numpy(w.f).cuda()
         u = torch.empty_like(f)
         plan = hz.Plan.from_workload(w, precision="fp64")
