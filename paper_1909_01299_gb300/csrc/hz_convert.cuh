@@ -38,6 +38,12 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(u | (hi & 0x80000000u));
 }
 
+// complex FP64 -> FP32 by the truncating conversion (the FP32 kernels of the mixed path are
+// bound by instruction issue; the refinement absorbs the last bit)
+__device__ __forceinline__ float2 to_c64t(double2 v) {
+  return make_float2(f64_to_f32_trunc(v.x), f64_to_f32_trunc(v.y));
+}
+
 // FP32 -> FP64 (exact for normal numbers; FP32 denormals -> signed 0).
 __device__ __forceinline__ double f32_to_f64(float v) {
   const uint32_t u = __float_as_uint(v);

@@ -50,7 +50,7 @@ __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __r
     out[t] = acc;
   } else {
     float2 acc = make_float2(0.f, 0.f);
-    for (int i = rg.x; i < rg.y; ++i) acc = cfma32(c[i], to_c64(v[(long long)i * ncols]), acc);
+    for (int i = rg.x; i < rg.y; ++i) acc = cfma32(c[i], to_c64t(v[(long long)i * ncols]), acc);
     out[t] = to_c128(acc);
   }
 }
@@ -81,7 +81,7 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
     out[t] = acc;
   } else {
     float2 a32 = make_float2(0.f, 0.f);
-    for (int j = rg.x + lane; j < rg.y; j += 32) a32 = cfma32(c[j], to_c64(v[j]), a32);
+    for (int j = rg.x + lane; j < rg.y; j += 32) a32 = cfma32(c[j], to_c64t(v[j]), a32);
     for (int o = 16; o > 0; o >>= 1) {
       a32.x += __shfl_down_sync(0xffffffffu, a32.x, o);
       a32.y += __shfl_down_sync(0xffffffffu, a32.y, o);
@@ -108,7 +108,7 @@ __global__ void contract_rows_multi_kernel(const double2* __restrict__ V, double
 #pragma unroll
   for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
   for (int i = 0; i < nrows; ++i) {
-    const float2 x = to_c64(v[(long long)i * ncols]);
+    const float2 x = to_c64t(v[(long long)i * ncols]);
 #pragma unroll
     for (int q = 0; q < NS; ++q) acc[q] = cfma32(coef[(long long)q * nrows + i], x, acc[q]);
   }
@@ -131,7 +131,7 @@ __global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double
 #pragma unroll
   for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
   for (int j = lane; j < ncols; j += 32) {
-    const float2 x = to_c64(v[j]);
+    const float2 x = to_c64t(v[j]);
 #pragma unroll
     for (int q = 0; q < NS; ++q) acc[q] = cfma32(coef[(long long)q * ncols + j], x, acc[q]);
   }

@@ -167,9 +167,9 @@ __global__ void pert_mul32_kernel(const double2* __restrict__ d, const float2* _
 __global__ void scale32_kernel(const double2* __restrict__ s, const double2* __restrict__ w,
                                float2* __restrict__ out, long long n) {
   const long long off = (long long)blockIdx.y * n;
-  const float2 sr = to_c64(s[blockIdx.y]);
+  const float2 sr = to_c64t(s[blockIdx.y]);
   for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
-    const float2 x = to_c64(w[off + t]);
+    const float2 x = to_c64t(w[off + t]);
     out[off + t] = make_float2(fmaf(sr.x, x.x, -sr.y * x.y), fmaf(sr.x, x.y, sr.y * x.x));
   }
 }
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(NT) multi_dot32_kernel(const float2* __restric
 #pragma unroll
   for (int i = 0; i < CNT; ++i) acc[i] = make_float2(0.f, 0.f);
   for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
-    const float2 x = to_c64(w[off + t]);
+    const float2 x = to_c64t(w[off + t]);
 #pragma unroll
     for (int i = 0; i < CNT; ++i) {
       const float2 v = V[i * vstride + off + t];
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(NT) multi_axpy32_kernel(const float2* __restri
   const long long off = (long long)r * n;
   float2 cr[CNT];
 #pragma unroll
-  for (int i = 0; i < CNT; ++i) cr[i] = to_c64(c[r * CNT + i]);
+  for (int i = 0; i < CNT; ++i) cr[i] = to_c64t(c[r * CNT + i]);
   for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < n; t += (long long)gridDim.x * NT) {
     float2 sum = make_float2(0.f, 0.f);
 #pragma unroll

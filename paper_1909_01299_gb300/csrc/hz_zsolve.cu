@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
     double2 v = ftp[pos];
     if (LO) {
       float2 g = make_float2(0.f, 0.f);
-      if (pl >= 0) g = cfma32(a.cxl32[i], to_c64(ax[(long long)pl * a.ny]), g);
-      if (pr >= 0) g = cfma32(a.cxr32[i], to_c64(ax[(long long)pr * a.ny]), g);
-      if (ql >= 0) g = cfma32(a.cyl32[j], to_c64(ay[(long long)ql * a.nx]), g);
-      if (qr >= 0) g = cfma32(a.cyr32[j], to_c64(ay[(long long)qr * a.nx]), g);
+      if (pl >= 0) g = cfma32(a.cxl32[i], to_c64t(ax[(long long)pl * a.ny]), g);
+      if (pr >= 0) g = cfma32(a.cxr32[i], to_c64t(ax[(long long)pr * a.ny]), g);
+      if (ql >= 0) g = cfma32(a.cyl32[j], to_c64t(ay[(long long)ql * a.nx]), g);
+      if (qr >= 0) g = cfma32(a.cyr32[j], to_c64t(ay[(long long)qr * a.nx]), g);
       const double2 gd = to_c128(g);
       v.x = fma(s, gd.x, v.x);
       v.y = fma(s, gd.y, v.y);
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, d
     const double2* by = byp + i;
     if (LO) {
       float2 g = make_float2(0.f, 0.f);
-      for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64(ax[(long long)p * a.ny]), g);
-      for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64(by[(long long)q * a.nx]), g);
+      for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64t(ax[(long long)p * a.ny]), g);
+      for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64t(by[(long long)q * a.nx]), g);
       val[e] = to_c128(g);
     } else {
       double2 b = make_double2(0.0, 0.0);
