@@ -340,10 +340,16 @@ def run_hz(args):
     achieved = flops_per_launch / (t_launch * 1e-3) / 1e12
     peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
     total_ms = sum(v[0] for v in st64.values())
-    # mixed path: the tensor-core bulk transform (HBM-bound: it reads and writes one volume)
+    # mixed path: the tensor-core bulk transform (HBM-bound: it reads and writes one volume).
+    # Algorithmic bytes per transformed value: forward x reads complex128 f and writes
+    # complex64 (24 B), forward y and inverse y complex64 both ways (16 B), inverse x reads
+    # complex64 and writes complex128 u (24 B), or also reads u when it accumulates a
+    # correction (40 B); averaged over the 4 (1 + refinements) launches of a step.
     hbm_peak, hbm_src = measured_peaks()
     tc_launch_ms = (stmx["fwd"][0] + stmx["inv"][0]) / max(1, stmx["fwd"][1] + stmx["inv"][1])
-    tc_bytes = 2 * 16 * w.unknowns * R
+    nref = int(infomx.get("refinements", 0))
+    tc_values = (w.nx - len(w.x_iface)) * (w.ny - len(w.y_iface)) * w.nz * R
+    tc_bytes = tc_values * (80 + 96 * nref) / (4 * (1 + nref))
     roof_tc = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
                "achieved": tc_bytes / (tc_launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                "frac": tc_bytes / (tc_launch_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,

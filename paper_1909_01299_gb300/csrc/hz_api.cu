@@ -708,15 +708,28 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const long long planes = (long long)R * nz;
   const int nIx = (int)p->ax.iface.size(), nIy = (int)p->ay.iface.size();
+  // Mixed path with tensor-core transforms: the mode-space volumes (the transformed right-hand
+  // side f~, the half-transformed planes in G and the z-sweep results) are complex64, since
+  // the transforms that produce them accumulate in FP32 and the ones that consume them split
+  // FP32 values into TF32 parts; the z eliminations keep FP64 forward values in V's buffer.
+  // FT's buffer holds f~ (first half) and the z-sweep results (second half).
+  const bool c64 = lo && p->use_tc && !conj_out;
+  float2* const FT32 = reinterpret_cast<float2*>(w.FT);
+  float2* const V32 = FT32 + planes * nx * ny;
+  float2* const G32 = reinterpret_cast<float2*>(w.G);
   // bulk transforms: FP64 DFMA, or (mixed path) 3xTF32 on the tensor cores
-  auto bulk = [&](const hz::XformSet& xs, const hz::TCSet& ts, const double2* in, double2* out, int rpp,
-                  int trans, int store_mode, int conj, const signed char* skip) {
-    if (!lo)
-      hz::xform_f64(xs, in, out, rpp, planes, trans, store_mode, conj, skip, st);
-    else if (p->use_tc && !conj)
-      hz::xform_tc(ts, in, out, rpp, planes, trans, store_mode, skip, p->status, st);
-    else
-      hz::xform_f32(xs, in, out, rpp, planes, trans, store_mode, conj, skip, st);
+  auto bulk = [&](const hz::XformSet& xs, const hz::TCSet& ts, const void* in, int in32, void* out, int out32,
+                  int rpp, int trans, int store_mode, int conj, const signed char* skip) {
+    if (in32 || out32 || (lo && p->use_tc && !conj)) {
+      if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st))
+        throw Fail{HZ_ERR_ARG};
+    } else if (!lo) {
+      hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
+                    store_mode, conj, skip, st);
+    } else {
+      hz::xform_f32(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
+                    store_mode, conj, skip, st);
+    }
   };
   // The interface-row transforms below are non-transposed, so their rows are
   // flattened across planes (one launch row tile covers 32 rows of any planes).
@@ -728,25 +741,41 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     if (lo) hz::xform_f32(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
     else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
   };
-  auto crows = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
+  // contractions of the current z-sweep result (complex64 in V32, or complex128 in V)
+  auto crows = [&](const AxisDev& d, double2* out, bool edge, int nslots, cudaStream_t s) {
     const int2* rng = edge ? d.edge_rng : d.grng;
+    if (c64) {
+      if (!edge && hz::contract_all(true, V32, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
+      hz::contract_rows(V32, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+      return;
+    }
     // FP32: one pass over V for all slots; FP64 stays per slot (bound by the FP64 pipe, where
     // one pass saves no work but gives fewer threads)
-    if (!edge && lo && hz::contract_all(true, V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
-    if (lo) hz::contract_rows(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
-    else hz::contract_rows(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+    if (!edge && lo && hz::contract_all(true, w.V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
+    if (lo) hz::contract_rows(w.V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+    else hz::contract_rows(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
   };
-  auto ccols = [&](const AxisDev& d, const double2* V, double2* out, bool edge, int nslots, cudaStream_t s) {
+  auto ccols = [&](const AxisDev& d, double2* out, bool edge, int nslots, cudaStream_t s) {
     const int2* rng = edge ? d.edge_rng : d.grng;
-    if (!edge && lo && hz::contract_all(false, V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
-    if (lo) hz::contract_cols(V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
-    else hz::contract_cols(V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+    if (c64) {
+      if (!edge && hz::contract_all(false, V32, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
+      hz::contract_cols(V32, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+      return;
+    }
+    if (!edge && lo && hz::contract_all(false, w.V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
+    if (lo) hz::contract_cols(w.V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
+    else hz::contract_cols(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
   };
   // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
   {
     Stage t(p, st, HZ_STAGE_FWD);
-    bulk(p->dx.fwd, p->dx.tfwd, f, w.G, ny, 1, hz::XS_STORE, 0, p->dy.skip);
-    bulk(p->dy.fwd, p->dy.tfwd, w.G, w.FT, nx, 0, hz::XS_STORE, 0, p->dx.skip);
+    if (c64) {
+      bulk(p->dx.fwd, p->dx.tfwd, f, 0, G32, 1, ny, 1, hz::XS_STORE, 0, p->dy.skip);
+      bulk(p->dy.fwd, p->dy.tfwd, G32, 1, FT32, 1, nx, 0, hz::XS_STORE, 0, p->dx.skip);
+    } else {
+      bulk(p->dx.fwd, p->dx.tfwd, f, 0, w.G, 0, ny, 1, hz::XS_STORE, 0, p->dy.skip);
+      bulk(p->dy.fwd, p->dy.tfwd, w.G, 0, w.FT, 0, nx, 0, hz::XS_STORE, 0, p->dx.skip);
+    }
   }
 
   hz::ZSolveArgs za;
@@ -756,6 +785,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   za.rhs = w.FT; za.out = w.V;
   za.P = p->Pb; za.Q = p->Qb; za.cm = p->cm_b;
   za.rhs_per_thread = p->zs_rb;
+  if (c64) { za.rhs32 = FT32; za.out32 = V32; za.scratch = w.V; }
   // Step 2: mode-wise z solves of every block (pass A)
   {
     Stage t(p, st, HZ_STAGE_PASS_A);
@@ -768,11 +798,11 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     const cudaStream_t sy = p->side;
     fork(p, st);
     if (nIx) {
-      crows(p->dx, w.V, w.cX, true, 2 * nIx, st);
+      crows(p->dx, w.cX, true, 2 * nIx, st);
       rowx(p->dy.inv, w.cX, w.vX, 2 * nIx * planes, st);
     }
     if (nIy) {
-      ccols(p->dy, w.V, w.cY, true, 2 * nIy, sy);
+      ccols(p->dy, w.cY, true, 2 * nIy, sy);
       rowx(p->dx.inv, w.cY, w.vY, 2 * nIy * planes, sy);
     }
     join(p, st);
@@ -797,17 +827,19 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     zg.skip_i = nullptr; zg.skip_j = nullptr;
     zg.rhs = w.G; zg.out = w.V;                     // w~ (v~ in V is no longer needed)
     zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
-    hz::global_rhs(ga, w.G, st);                    // r~ (G is free until step 7)
+    if (c64) zg.rhs32 = G32;
+    if (c64) hz::global_rhs(ga, G32, st);           // r~ (G is free until step 7)
+    else hz::global_rhs(ga, w.G, st);
     hz::zsolve(zg, st);
     fork(p, st);
     if (nIx) {
-      crows(p->dx, w.V, w.cg, false, nIx, st);
+      crows(p->dx, w.cg, false, nIx, st);
       rowx(p->dy.ginv, w.cg, w.wX, nIx * planes, st);
       // Step 6 (x interfaces): forward y-transform of w on the interface rows
       rowx(p->dy.fwd, w.wX, w.alX, nIx * planes, st);
     }
     if (nIy) {
-      ccols(p->dy, w.V, w.dg, false, nIy, sy);
+      ccols(p->dy, w.dg, false, nIy, sy);
       rowx(p->dx.ginv, w.dg, w.wY, nIy * planes, sy);
       rowx(p->dx.fwd, w.wY, w.alY, nIy * planes, sy);
     }
@@ -822,14 +854,20 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     ba.gxl = p->dx.gl; ba.gxr = p->dx.gr; ba.gyl = p->dy.gl; ba.gyr = p->dy.gr;
     ba.cxl = p->dx.cl; ba.cxr = p->dx.cr; ba.cyl = p->dy.cl; ba.cyr = p->dy.cr;
     if (lo) { ba.cxl32 = p->dx.cl32; ba.cxr32 = p->dx.cr32; ba.cyl32 = p->dy.cl32; ba.cyr32 = p->dy.cr32; }
-    hz::boundary_rhs(ba, w.FT, st);                 // f~ + g~ / M_z, in place
+    if (c64) hz::boundary_rhs(ba, FT32, st);        // f~ + g~ / M_z, in place
+    else hz::boundary_rhs(ba, w.FT, st);
     hz::zsolve(za, st);
   }
   // Step 7: u = W_x (x) W_y u~ in the blocks; u = w on the interfaces
   {
     Stage t(p, st, HZ_STAGE_INV);
-    bulk(p->dy.inv, p->dy.tinv, w.V, w.G, nx, 1, hz::XS_STORE, 0, p->dx.skip);
-    bulk(p->dx.inv, p->dx.tinv, w.G, u, ny, 0, store, conj_out, p->dy.skip);
+    if (c64) {
+      bulk(p->dy.inv, p->dy.tinv, V32, 1, G32, 1, nx, 1, hz::XS_STORE, 0, p->dx.skip);
+      bulk(p->dx.inv, p->dx.tinv, G32, 1, u, 0, ny, 0, store, conj_out, p->dy.skip);
+    } else {
+      bulk(p->dy.inv, p->dy.tinv, w.V, 0, w.G, 0, nx, 1, hz::XS_STORE, 0, p->dx.skip);
+      bulk(p->dx.inv, p->dx.tinv, w.G, 0, u, 0, ny, 0, store, conj_out, p->dy.skip);
+    }
   }
   if (nIx + nIy > 0) {
     Stage t(p, st, HZ_STAGE_IFACE_OUT);

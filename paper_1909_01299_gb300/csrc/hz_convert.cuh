@@ -57,6 +57,15 @@ __device__ __forceinline__ double f32_to_f64(float v) {
 __device__ __forceinline__ float2 to_c64(double2 v) { return make_float2(f64_to_f32(v.x), f64_to_f32(v.y)); }
 __device__ __forceinline__ double2 to_c128(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
 
+// Identity forms, so that kernels templated on the storage type (the mixed path keeps its
+// mode-space volumes as complex64, the FP64 path as complex128) read either through one
+// call: to_c64t gives FP32 operands, to_c128 FP64 operands.
+__device__ __forceinline__ float2 to_c64t(float2 v) { return v; }
+__device__ __forceinline__ double2 to_c128(double2 v) { return v; }
+// Store a value computed in FP64 into either storage type (complex64: truncated).
+__device__ __forceinline__ void store_c(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void store_c(float2* p, double2 v) { *p = to_c64t(v); }
+
 // acc + c * y in FP32
 __device__ __forceinline__ float2 cfma32(float2 c, float2 y, float2 acc) {
   return make_float2(fmaf(c.x, y.x, fmaf(-c.y, y.y, acc.x)), fmaf(c.x, y.y, fmaf(c.y, y.x, acc.y)));

@@ -29,9 +29,10 @@ __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// C = double2: FP64 arithmetic; C = float2: FP32 arithmetic on FP64 data (mixed path).
-template <typename C>
-__global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+// C = double2: FP64 arithmetic; C = float2: FP32 arithmetic (mixed path) on complex128 or
+// complex64 data (TV).
+template <typename C, typename TV>
+__global__ void contract_rows_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                      const C* __restrict__ coef, const int2* __restrict__ range,
                                      int nrows, int ncols, int nslots, long long nplanes) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -42,7 +43,7 @@ __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __r
   const int s = (int)(ps % nslots);
   const long long plane = ps / nslots;
   const int2 rg = range[s];
-  const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
+  const TV* __restrict__ v = V + plane * (long long)nrows * ncols + j;
   const C* __restrict__ c = coef + (long long)s * nrows;
   if constexpr (sizeof(C) == sizeof(double2)) {
     double2 acc = make_double2(0.0, 0.0);
@@ -58,8 +59,8 @@ __global__ void contract_rows_kernel(const double2* __restrict__ V, double2* __r
 // FP64: one thread per output (plane, slot, row i) walking its row (the loads of a warp hit
 // 32 rows; every line is reused from L1 by the next iterations).  FP32: one warp per
 // output, lanes reading the row's range coalesced, then a shuffle reduction in fixed order.
-template <typename C>
-__global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+template <typename C, typename TV>
+__global__ void contract_cols_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                      const C* __restrict__ coef, const int2* __restrict__ range,
                                      int nrows, int ncols, int nslots, long long nplanes) {
   constexpr bool F64 = sizeof(C) == sizeof(double2);
@@ -73,7 +74,7 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
   const int s = (int)(ps % nslots);
   const long long plane = ps / nslots;
   const int2 rg = range[s];
-  const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
+  const TV* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
   const C* __restrict__ c = coef + (long long)s * ncols;
   if constexpr (F64) {
     double2 acc = make_double2(0.0, 0.0);
@@ -95,15 +96,15 @@ __global__ void contract_cols_kernel(const double2* __restrict__ V, double2* __r
 // nslots sums (2 <= nslots <= 8, a compile-time count) in FP32 instead of reading V once
 // per slot.
 
-template <int NS>
-__global__ void contract_rows_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+template <int NS, typename TV>
+__global__ void contract_rows_multi_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                            const float2* __restrict__ coef, int nrows, int ncols,
                                            long long nplanes) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nplanes * (long long)ncols) return;
   const int j = (int)(t % ncols);
   const long long plane = t / ncols;
-  const double2* __restrict__ v = V + plane * (long long)nrows * ncols + j;
+  const TV* __restrict__ v = V + plane * (long long)nrows * ncols + j;
   float2 acc[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -117,8 +118,8 @@ __global__ void contract_rows_multi_kernel(const double2* __restrict__ V, double
 }
 
 // One warp per (plane, row i): lanes stride over the row, then a shuffle reduction per slot.
-template <int NS>
-__global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double2* __restrict__ out,
+template <int NS, typename TV>
+__global__ void contract_cols_multi_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                            const float2* __restrict__ coef, int nrows, int ncols,
                                            long long nplanes) {
   const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -126,7 +127,7 @@ __global__ void contract_cols_multi_kernel(const double2* __restrict__ V, double
   if (t >= nplanes * (long long)nrows) return;             // warp-uniform
   const int i = (int)(t % nrows);
   const long long plane = t / nrows;
-  const double2* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
+  const TV* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
   float2 acc[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -421,43 +422,46 @@ unsigned blocks_for(long long n, int T) { return (unsigned)((n + T - 1) / T); }
 
 }  // namespace
 
-template <typename C>
-void contract_rows_t(const double2* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
+template <typename C, typename TV>
+void contract_rows_t(const TV* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
                      int nslots, long long nplanes, cudaStream_t st) {
   const long long n = nplanes * nslots * (long long)ncols;
   if (n == 0) return;
-  contract_rows_kernel<C><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots, nplanes);
+  contract_rows_kernel<C, TV><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots,
+                                                                 nplanes);
   count_launch();
 }
 
-template <typename C>
-void contract_cols_t(const double2* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
+template <typename C, typename TV>
+void contract_cols_t(const TV* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
                      int nslots, long long nplanes, cudaStream_t st) {
   const long long n = nplanes * nslots * (long long)nrows;
   if (n == 0) return;
   const long long threads = sizeof(C) == sizeof(double2) ? n : n * 32;   // FP32: one warp per output
-  contract_cols_kernel<C><<<blocks_for(threads, 256), 256, 0, st>>>(V, out, coef, range, nrows, ncols, nslots,
-                                                                   nplanes);
+  contract_cols_kernel<C, TV><<<blocks_for(threads, 256), 256, 0, st>>>(V, out, coef, range, nrows, ncols,
+                                                                       nslots, nplanes);
   count_launch();
 }
 
-template <int NS>
-void contract_all_t(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+template <int NS, typename TV>
+void contract_all_t(bool rows, const TV* V, double2* out, const float2* coef, int nrows, int ncols,
                     long long nplanes, cudaStream_t st) {
   if (rows) {
     const long long n = nplanes * (long long)ncols;
     if (n == 0) return;
-    contract_rows_multi_kernel<NS><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, nrows, ncols, nplanes);
+    contract_rows_multi_kernel<NS, TV><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, nrows, ncols, nplanes);
   } else {
     const long long n = nplanes * (long long)nrows;
     if (n == 0) return;
-    contract_cols_multi_kernel<NS><<<blocks_for(n * 32, 256), 256, 0, st>>>(V, out, coef, nrows, ncols, nplanes);
+    contract_cols_multi_kernel<NS, TV><<<blocks_for(n * 32, 256), 256, 0, st>>>(V, out, coef, nrows, ncols,
+                                                                              nplanes);
   }
   count_launch();
 }
 
-bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
-                  int nslots, long long nplanes, cudaStream_t st) {
+template <typename TV>
+bool contract_all_any(bool rows, const TV* V, double2* out, const float2* coef, int nrows, int ncols,
+                      int nslots, long long nplanes, cudaStream_t st) {
   switch (nslots) {        // the slot count is a compile-time constant of the kernels
     case 2: contract_all_t<2>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
     case 3: contract_all_t<3>(rows, V, out, coef, nrows, ncols, nplanes, st); return true;
@@ -470,6 +474,15 @@ bool contract_all(bool rows, const double2* V, double2* out, const float2* coef,
   }
 }
 
+bool contract_all(bool rows, const double2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st) {
+  return contract_all_any(rows, V, out, coef, nrows, ncols, nslots, nplanes, st);
+}
+bool contract_all(bool rows, const float2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st) {
+  return contract_all_any(rows, V, out, coef, nrows, ncols, nslots, nplanes, st);
+}
+
 void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {
   contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
@@ -478,11 +491,19 @@ void contract_rows(const double2* V, double2* out, const float2* coef, const int
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {
   contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
 }
+void contract_rows(const float2* V, double2* out, const float2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+}
 void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {
   contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
 }
 void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range, int nrows,
+                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
+  contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+}
+void contract_cols(const float2* V, double2* out, const float2* coef, const int2* range, int nrows,
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {
   contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
 }

@@ -101,8 +101,11 @@ void xform_tc_prepare();
 void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
                    std::vector<TCTile>& tiles, int blk_index);
 // err: device status word (set to HZ_ERR_TIMEOUT if a bounded wait gives up).
-void xform_tc(const TCSet& ts, const double2* in, double2* out, int rows_per_plane, long long nplanes,
-              int trans, int store, const signed char* rowskip, int* err, cudaStream_t st);
+// in32 / out32: the input / output are complex64 (float2) instead of complex128 (double2).
+// Returns false (nothing launched) for XS_ACCUM with a complex64 output.
+bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
+              long long nplanes, int trans, int store, const signed char* rowskip, int* err,
+              cudaStream_t st);
 
 // FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
 // trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out
@@ -138,6 +141,12 @@ struct ZSolveArgs {
   int nx = 0, ny = 0, nz = 0, nrhs = 0;
   int real_cm = 0;
   int rhs_per_thread = 0;                // 1 or 2; 0 = chosen from the launch size
+  // complex64 storage (mixed path): when rhs32 is set, the right-hand side is read from
+  // rhs32, the result written to out32 (truncated to FP32) and the FP64 forward-sweep
+  // values kept in scratch (same layout); the elimination itself stays FP64
+  const float2* rhs32 = nullptr;
+  float2* out32 = nullptr;
+  double2* scratch = nullptr;
 };
 void zsolve(const ZSolveArgs& a, cudaStream_t st);
 
@@ -159,6 +168,9 @@ struct BoundaryArgs {
   const float2* cyl32 = nullptr; const float2* cyr32 = nullptr;
 };
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st);
+// complex64 f~ (mixed path, needs the FP32 coefficient copies): the sum is formed in FP64
+// and stored truncated to FP32
+void boundary_rhs(const BoundaryArgs& a, float2* ft, cudaStream_t st);
 
 // Step 5 global right-hand side: out = sum_p WgxI[p][i] aX[r][k][p][j] + sum_q WgyI[q][j] bY[r][k][q][i].
 struct GlobalRhsArgs {
@@ -171,6 +183,8 @@ struct GlobalRhsArgs {
   const float2* WgyI32 = nullptr;
 };
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
+// complex64 output (mixed path, needs the FP32 coefficient copies)
+void global_rhs(const GlobalRhsArgs& a, float2* out, cudaStream_t st);
 
 
 // Elimination factors of (Tz + s_ij S_z) for every (i, j) with s_ij = lamx[i] + lamy[j]
@@ -198,6 +212,13 @@ bool contract_all(bool rows, const double2* V, double2* out, const float2* coef,
 void contract_rows(const double2* V, double2* out, const float2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
 void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+// The FP32 contractions on complex64 V (the mixed path's mode-space storage).
+bool contract_all(bool rows, const float2* V, double2* out, const float2* coef, int nrows, int ncols,
+                  int nslots, long long nplanes, cudaStream_t st);
+void contract_rows(const float2* V, double2* out, const float2* coef, const int2* range,
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+void contract_cols(const float2* V, double2* out, const float2* coef, const int2* range,
                    int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

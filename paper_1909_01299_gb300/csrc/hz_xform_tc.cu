@@ -16,13 +16,14 @@
 // 16) of one block; two CTAs share an SM (about 105 KB of shared memory and 256 TMEM
 // columns each), so that one CTA's loads overlap the other's prologue and epilogue.
 // The contraction runs in chunks of 16 real K (64 bytes per operand row): all
-// threads convert the FP64 data rows to TF32 hi/lo and store them, with the tables'
-// hi/lo rows, in shared memory in the K-major 64-byte-swizzled layout; one thread
+// threads convert the data rows (complex128, or complex64 for the mixed path's
+// mode-space volumes, which carry FP32 accuracy only) to TF32 hi/lo and store them,
+// with the tables' hi/lo rows, in shared memory in the K-major 64-byte-swizzled layout; one thread
 // issues the 6 MMAs of the chunk and commits them to the chunk's mbarrier; two chunk
 // buffers alternate, so the conversion of chunk c+1 overlaps the MMAs of chunk c.
 // The epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM lanes
-// 32(w%4)..+31 = tile rows, column chunks w/4, w/4+2, ...), converts to FP64 and
-// stores: transposed outputs straight from registers (a warp's 32 rows are
+// 32(w%4)..+31 = tile rows, column chunks w/4, w/4+2, ...) and stores it as complex128
+// (exact) or complex64: transposed outputs straight from registers (a warp's 32 rows are
 // consecutive addresses), row-contiguous outputs through an FP32 staging tile in
 // shared memory written out row by row; optionally adding to the old values.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
@@ -139,12 +140,19 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool v
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
+  // 8-byte copy (one complex64 value: a block may start at an odd column, so pairs of
+  // complex64 values are not 16-byte aligned in general)
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory plan of one CTA (offsets from a 1024-byte aligned base):
-//   raw[2]   : FP64 data chunks as loaded, 128 rows x 8 complex (16 KB each)
+//   raw[2]   : data chunks as loaded, 128 rows x 8 complex (16 KB each; complex64 data use
+//              the first half)
 //   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 8 KB each), 64B-swizzled
 //   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled
 //   bars     : MMA-completion mbarriers of the two operand stages, TMEM address slot
@@ -153,8 +161,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int RAW_ROWB = KCH * 8;        // FP64 bytes of a data row in a chunk (KCH / 2 complex)
 constexpr int RAW_BYTES = TC_M * RAW_ROWB;
 
+// TI / TO: double2 (complex128) or float2 (complex64) input / output elements.
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM)
-xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const float* __restrict__ tabs,
+xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __restrict__ tabs,
                 const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, int ntiles,
                 long long nrows, int rows_per_plane, int ncols, int trans, int store,
                 const signed char* __restrict__ rowskip, int* __restrict__ err) {
@@ -177,7 +187,9 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
   const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
   const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
 
-  // issue the FP64 rows of chunk c (8 complex per row) into raw[c & 1]
+  constexpr bool IN32 = sizeof(TI) == 8, OUT32 = sizeof(TO) == 8;
+  constexpr int RROWB = (int)sizeof(TI) * (KCH / 2);       // bytes of a data row in a chunk
+  // issue the data rows of chunk c (8 complex per row) into raw[c & 1]
   auto load_raw = [&](int c) {
     const uint32_t dst = raw0 + (c & 1) * RAW_BYTES;
 #pragma unroll
@@ -187,8 +199,9 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       const long long grow = row0 + r;
       const int col = c * (KCH / 2) + cc;
       const bool ok = grow < nrows && col < n;
-      const double2* src = ok ? in + grow * (long long)ncols + b.start + col : in;
-      cp_async16(dst + r * RAW_ROWB + cc * 16, src, ok);
+      const TI* src = ok ? in + grow * (long long)ncols + b.start + col : in;
+      if constexpr (IN32) cp_async8(dst + r * RROWB + cc * 8, src, ok);
+      else cp_async16(dst + r * RROWB + cc * 16, src, ok);
     }
   };
   // issue the table rows (hi and lo) of chunk c into bop[c & 1], 64B-swizzled
@@ -246,11 +259,20 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
       for (int q = 0; q < TC_M * (ROWB / 16) / TC_THREADS; ++q) {
         const int task = tid + TC_THREADS * q;             // row = task / 4, 16-byte unit = task % 4
         const int r = task >> 2, c = task & 3;
-        double x0, x1, x2, x3;
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * RAW_ROWB + c * 32));
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * RAW_ROWB + c * 32 + 16));
-        const float f[4] = {f64_to_f32_trunc(x0), f64_to_f32_trunc(x1), f64_to_f32_trunc(x2),
-                            f64_to_f32_trunc(x3)};
+        float f[4];
+        if constexpr (IN32) {
+          asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                       : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3])
+                       : "r"(rsrc + r * RROWB + c * 16));
+        } else {
+          double x0, x1, x2, x3;
+          asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * RROWB + c * 32));
+          asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * RROWB + c * 32 + 16));
+          f[0] = f64_to_f32_trunc(x0);
+          f[1] = f64_to_f32_trunc(x1);
+          f[2] = f64_to_f32_trunc(x2);
+          f[3] = f64_to_f32_trunc(x3);
+        }
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -316,22 +338,25 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
         float v[16];
         tmem_ld16(tl + c16, v);
         if (!row_ok) continue;
-        double2* p[8];
-        double2 val[8];
+        TO* p[8];
+        TO val[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int ccol = (t.n0 + c16) / 2 + e;             // complex column within the block
           p[e] = ccol < n ? out + plane * (long long)ncols * rows_per_plane +
                                 (long long)(b.start + ccol) * rows_per_plane + rip
                           : nullptr;
-          val[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
+          if constexpr (OUT32) val[e] = make_float2(v[2 * e], v[2 * e + 1]);
+          else val[e] = make_double2(f32_to_f64(v[2 * e]), f32_to_f64(v[2 * e + 1]));
         }
-        if (store == XS_ACCUM) {                           // all old values in flight at once
-          double2 o[8];
+        if constexpr (!OUT32) {
+          if (store == XS_ACCUM) {                         // all old values in flight at once
+            double2 o[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) o[e] = p[e] ? *p[e] : make_double2(0.0, 0.0);
+            for (int e = 0; e < 8; ++e) o[e] = p[e] ? *p[e] : make_double2(0.0, 0.0);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) { val[e].x += o[e].x; val[e].y += o[e].y; }
+            for (int e = 0; e < 8; ++e) { val[e].x += o[e].x; val[e].y += o[e].y; }
+          }
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e)
@@ -364,28 +389,31 @@ xform_tc_kernel(const double2* __restrict__ in, double2* __restrict__ out, const
           if (rowskip[g - pl * rows_per_plane]) continue;
         }
         const float2* src = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
-        double2* dg = out + g * (long long)ncols + b.start + cbase;
+        TO* dg = out + g * (long long)ncols + b.start + cbase;
         constexpr int CPL = kTcMaxN / 2 / 32 + 1;           // complex columns per lane (<= 3)
-        double2 val[CPL];
+        TO val[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
           const int c = lane + 32 * q;
           if (c < ccount) {
             const float2 f = src[c];
-            val[q] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
+            if constexpr (OUT32) val[q] = f;
+            else val[q] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
           }
         }
-        if (store == XS_ACCUM) {                           // every old value in flight at once
-          double2 o[CPL];
+        if constexpr (!OUT32) {
+          if (store == XS_ACCUM) {                         // every old value in flight at once
+            double2 o[CPL];
 #pragma unroll
-          for (int q = 0; q < CPL; ++q) {
-            const int c = lane + 32 * q;
-            if (c < ccount) o[q] = dg[c];
-          }
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (c < ccount) o[q] = dg[c];
+            }
 #pragma unroll
-          for (int q = 0; q < CPL; ++q) {
-            const int c = lane + 32 * q;
-            if (c < ccount) { val[q].x += o[q].x; val[q].y += o[q].y; }
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (c < ccount) { val[q].x += o[q].x; val[q].y += o[q].y; }
+            }
           }
         }
 #pragma unroll
@@ -457,28 +485,46 @@ size_t xform_tc_smem(int nt_max) {
 
 uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }
 
+template <typename TI, typename TO>
+void set_smem_attr() {
+  cudaFuncSetAttribute(xform_tc_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)xform_tc_smem(kTcMaxN));
+}
+
 void xform_tc_prepare() {
   int dev = 0;
   cudaGetDevice(&dev);
   static bool attr_set[64] = {};
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
     // the largest tile any plan uses, so every launch fits
-    cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)xform_tc_smem(kTcMaxN));
+    set_smem_attr<double2, double2>();
+    set_smem_attr<double2, float2>();
+    set_smem_attr<float2, float2>();
+    set_smem_attr<float2, double2>();
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
 }
 
-void xform_tc(const TCSet& ts, const double2* in, double2* out, int rows_per_plane, long long nplanes,
-              int trans, int store, const signed char* rowskip, int* err, cudaStream_t st) {
+bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
+              long long nplanes, int trans, int store, const signed char* rowskip, int* err,
+              cudaStream_t st) {
+  if (out32 && store != XS_STORE) return false;          // accumulation needs a complex128 output
   const long long nrows = nplanes * (long long)rows_per_plane;
-  if (nrows <= 0 || ts.ntiles == 0) return;
+  if (nrows <= 0 || ts.ntiles == 0) return true;
   xform_tc_prepare();
   const long long ctas = ((nrows + TC_M - 1) / TC_M) * ts.ntiles;
-  xform_tc_kernel<<<(unsigned)ctas, TC_THREADS, xform_tc_smem(ts.nt_max), st>>>(
-      in, out, ts.d_tab, ts.d_blocks, ts.d_tiles, ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store,
-      rowskip, err);
+  const size_t smem = xform_tc_smem(ts.nt_max);
+#define HZ_TC_LAUNCH(TI, TO)                                                                          \
+  xform_tc_kernel<TI, TO><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                                 \
+      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_tab, ts.d_blocks, ts.d_tiles, ts.ntiles, \
+      nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
+  if (in32 && out32) HZ_TC_LAUNCH(float2, float2);
+  else if (in32) HZ_TC_LAUNCH(float2, double2);
+  else if (out32) HZ_TC_LAUNCH(double2, float2);
+  else HZ_TC_LAUNCH(double2, double2);
+#undef HZ_TC_LAUNCH
   count_launch();
+  return true;
 }
 
 }  // namespace hz

@@ -17,7 +17,10 @@
 //   forward  y_k = (rhs_k - cm_k y_{k-1}) P_k,   back  x_k = y_k - Q_k x_{k+1},
 // with P_k = fold_k / d_k, Q_k = c_{k+1} / d_k, cm_k = c_k / fold_k, d_k the
 // pivots.  The forward results are kept in the output array and overwritten by
-// the back sweep.  FP64 throughout.
+// the back sweep.  The elimination is FP64 throughout; on the mixed path the
+// right-hand side and the result are stored as complex64 (they carry the FP32
+// accuracy of the tensor-core transforms that produce and consume them) and the
+// forward values go to an FP64 scratch array instead.
 #include <algorithm>
 
 #include "hz_convert.cuh"
@@ -39,8 +42,9 @@ __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
 }
 
 // RB right-hand sides per thread share each factor load and give the sweep RB independent
-// dependency chains.
-template <bool REALCM, int RB>
+// dependency chains.  C64: complex64 right-hand side and result (mixed path); the forward
+// values y_k are kept in FP64 in the scratch array, so only the stored result is rounded.
+template <bool REALCM, int RB, bool C64>
 __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const long long plane = (long long)a.nx * a.ny;
   const int ngrp = (a.nrhs + RB - 1) / RB;
@@ -53,8 +57,9 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const long long rs = plane * a.nz;
   const int r0 = grp * RB;
   const int nr = min(RB, a.nrhs - r0);
-  const double2* __restrict__ rhs = a.rhs + r0 * rs + pos;
-  double2* __restrict__ out = a.out + r0 * rs + pos;
+  const long long base = r0 * rs + pos;
+  // FP64 forward values: the result array itself, or the scratch array for complex64 results
+  double2* __restrict__ fw = (C64 ? a.scratch : a.out) + base;
   const double2* __restrict__ P = a.P + pos;
   const double2* __restrict__ Q = a.Q + pos;
   const double2* __restrict__ cm = a.cm;
@@ -69,16 +74,23 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
 #pragma unroll
     for (int q = 0; q < RB; ++q) {
       if (q < nr) {
-        const double2 b = rhs[q * rs + k * plane];
+        double2 b;
+        if constexpr (C64) b = to_c128(a.rhs32[base + q * rs + k * plane]);
+        else b = a.rhs[base + q * rs + k * plane];
         double2 t;
         if (REALCM)
           t = make_double2(fma(-c.x, y[q].x, b.x), fma(-c.x, y[q].y, b.y));
         else
           t = csub_mul(b, c, y[q]);
         y[q] = cmul(t, pk);
-        out[q * rs + k * plane] = y[q];
+        fw[q * rs + k * plane] = y[q];
       }
     }
+  }
+  if constexpr (C64) {
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (q < nr) a.out32[base + q * rs + (long long)(a.nz - 1) * plane] = to_c64t(y[q]);
   }
 #pragma unroll 2
   for (int k = a.nz - 2; k >= 0; --k) {
@@ -86,9 +98,10 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
 #pragma unroll
     for (int q = 0; q < RB; ++q) {
       if (q < nr) {
-        const double2 yk = out[q * rs + k * plane];
+        const double2 yk = fw[q * rs + k * plane];
         y[q] = csub_mul(yk, qk, y[q]);
-        out[q * rs + k * plane] = y[q];
+        if constexpr (C64) a.out32[base + q * rs + k * plane] = to_c64t(y[q]);
+        else fw[q * rs + k * plane] = y[q];
       }
     }
   }
@@ -105,16 +118,17 @@ constexpr int RT = 256, REPT = 4;      // right-hand-side kernels: threads, posi
 //                              + cyl[j] aY[r][k][gyl[j]][i] + cyr[j] aY[r][k][gyr[j]][i]).
 // REPT positions of a plane per thread, RT * REPT consecutive positions per CTA
 // (blockIdx.y = r * nz + k); interface positions are skipped.
-// LO: the term is formed in FP32 (mixed path) and added to ft in FP64.
-template <bool LO>
-__global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, double2* __restrict__ ft, int rk0) {
+// LO: the term is formed in FP32 (mixed path) and added to ft in FP64; FT = float2: ft is
+// complex64 (the sum is stored truncated).
+template <bool LO, typename FT>
+__global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, FT* __restrict__ ft, int rk0) {
   const int rk = rk0 + blockIdx.y;
   const int k = rk % a.nz;
   const int plane = a.nx * a.ny;                           // < 2^31 (checked at plan creation)
   const double s = a.sig ? a.sig[k] : 1.0;
   const double2* __restrict__ axp = a.alphaX + (long long)rk * a.nIx * a.ny;
   const double2* __restrict__ ayp = a.alphaY + (long long)rk * a.nIy * a.nx;
-  double2* __restrict__ ftp = ft + (long long)rk * plane;
+  FT* __restrict__ ftp = ft + (long long)rk * plane;
   double2 val[REPT];
   bool ok[REPT];
 #pragma unroll
@@ -126,7 +140,7 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
     const int pl = a.gxl[i], pr = a.gxr[i], ql = a.gyl[j], qr = a.gyr[j];
     const double2* ax = axp + j;
     const double2* ay = ayp + i;
-    double2 v = ftp[pos];
+    double2 v = to_c128(ftp[pos]);
     if (LO) {
       float2 g = make_float2(0.f, 0.f);
       if (pl >= 0) g = cfma32(a.cxl32[i], to_c64t(ax[(long long)pl * a.ny]), g);
@@ -154,20 +168,20 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
   }
 #pragma unroll
   for (int e = 0; e < REPT; ++e)
-    if (ok[e]) ftp[((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x] = val[e];
+    if (ok[e]) store_c(ftp + ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x, val[e]);
 }
 
 // Step 5 global right-hand side r~[r][k][l][m] = sum_p Wgx[p][l] aX[r][k][p][m]
 //                                              + sum_q Wgy[q][m] bY[r][k][q][l].
-// LO: FP32 arithmetic on the FP64 data (mixed path).
-template <bool LO>
-__global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, double2* __restrict__ out,
+// LO: FP32 arithmetic on the FP64 data (mixed path); OT = float2: complex64 output.
+template <bool LO, typename OT>
+__global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, OT* __restrict__ out,
                                                         int rk0) {
   const int rk = rk0 + blockIdx.y;
   const int plane = a.nx * a.ny;
   const double2* __restrict__ axp = a.aX + (long long)rk * a.nIx * a.ny;
   const double2* __restrict__ byp = a.bY + (long long)rk * a.nIy * a.nx;
-  double2* __restrict__ op = out + (long long)rk * plane;
+  OT* __restrict__ op = out + (long long)rk * plane;
   double2 val[REPT];
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, d
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
     const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
-    if (pos < plane) op[pos] = val[e];
+    if (pos < plane) store_c(op + pos, val[e]);
   }
 }
 
@@ -251,37 +265,47 @@ void zsolve(const ZSolveArgs& a, cudaStream_t st) {
   const int rb = (a.rhs_per_thread == 2) ? 2 : 1;
   const long long n = (long long)a.nx * a.ny * ((a.nrhs + rb - 1) / rb);
   const unsigned grid = (unsigned)((n + T - 1) / T);
-  if (rb == 2) {
-    if (a.real_cm) zsolve_kernel<true, 2><<<grid, T, 0, st>>>(a);
-    else zsolve_kernel<false, 2><<<grid, T, 0, st>>>(a);
-  } else {
-    if (a.real_cm) zsolve_kernel<true, 1><<<grid, T, 0, st>>>(a);
-    else zsolve_kernel<false, 1><<<grid, T, 0, st>>>(a);
+  const int v = (a.rhs32 ? 4 : 0) + (rb == 2 ? 2 : 0) + (a.real_cm ? 1 : 0);
+  switch (v) {
+    case 0: zsolve_kernel<false, 1, false><<<grid, T, 0, st>>>(a); break;
+    case 1: zsolve_kernel<true, 1, false><<<grid, T, 0, st>>>(a); break;
+    case 2: zsolve_kernel<false, 2, false><<<grid, T, 0, st>>>(a); break;
+    case 3: zsolve_kernel<true, 2, false><<<grid, T, 0, st>>>(a); break;
+    case 4: zsolve_kernel<false, 1, true><<<grid, T, 0, st>>>(a); break;
+    case 5: zsolve_kernel<true, 1, true><<<grid, T, 0, st>>>(a); break;
+    case 6: zsolve_kernel<false, 2, true><<<grid, T, 0, st>>>(a); break;
+    default: zsolve_kernel<true, 2, true><<<grid, T, 0, st>>>(a); break;
   }
   count_launch();
 }
 
-void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) {
+template <typename FT>
+void boundary_rhs_t(const BoundaryArgs& a, FT* ft, cudaStream_t st) {
   const int planes = a.nrhs * a.nz;
   const unsigned gx = (unsigned)(((long long)a.nx * a.ny + RT * REPT - 1) / (RT * REPT));
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    if (a.cxl32) boundary_rhs_kernel<true><<<grid, RT, 0, st>>>(a, ft, rk0);
-    else boundary_rhs_kernel<false><<<grid, RT, 0, st>>>(a, ft, rk0);
+    if (a.cxl32) boundary_rhs_kernel<true, FT><<<grid, RT, 0, st>>>(a, ft, rk0);
+    else boundary_rhs_kernel<false, FT><<<grid, RT, 0, st>>>(a, ft, rk0);
     count_launch();
   }
 }
+void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st) { boundary_rhs_t(a, ft, st); }
+void boundary_rhs(const BoundaryArgs& a, float2* ft, cudaStream_t st) { boundary_rhs_t(a, ft, st); }
 
-void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) {
+template <typename OT>
+void global_rhs_t(const GlobalRhsArgs& a, OT* out, cudaStream_t st) {
   const int planes = a.nrhs * a.nz;
   const unsigned gx = (unsigned)(((long long)a.nx * a.ny + RT * REPT - 1) / (RT * REPT));
   for (int rk0 = 0; rk0 < planes; rk0 += 65535) {
     dim3 grid(gx, std::min(65535, planes - rk0));
-    if (a.WgxI32) global_rhs_kernel<true><<<grid, RT, 0, st>>>(a, out, rk0);
-    else global_rhs_kernel<false><<<grid, RT, 0, st>>>(a, out, rk0);
+    if (a.WgxI32) global_rhs_kernel<true, OT><<<grid, RT, 0, st>>>(a, out, rk0);
+    else global_rhs_kernel<false, OT><<<grid, RT, 0, st>>>(a, out, rk0);
     count_launch();
   }
 }
+void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) { global_rhs_t(a, out, st); }
+void global_rhs(const GlobalRhsArgs& a, float2* out, cudaStream_t st) { global_rhs_t(a, out, st); }
 
 void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,
              const signed char* skip_i, const signed char* skip_j, const double2* tzd,
