@@ -88,6 +88,7 @@ struct hz_plan_s {
   double omega = 1.0;
   bool need_global = false;
   bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
+  bool tc_ok = true;                 // the tensor-core tables have their TMA tensor maps
   int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
@@ -401,6 +402,9 @@ void make_tc(hz_plan_t p, hz::TCSet& ts, int ncols, const std::vector<int>& star
   ts.d_blocks = upload(p, blocks);
   ts.d_tiles = upload(p, tiles);
   ts.d_tab = upload(p, tab);
+  std::vector<unsigned char> maps;
+  if (hz::tc_encode_tmaps(ts.d_tab, blocks, tiles, maps)) ts.d_tmaps = upload(p, maps);
+  else p->use_tc = p->tc_ok = false;   // no tensor maps: the mixed path runs the SIMT FP32 transforms
 }
 
 void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global) {
@@ -1034,7 +1038,7 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   int best_rb = p->zs_rb;
   bool best_tc = p->use_tc;
   for (int rb = 1; rb <= 2; ++rb)
-    for (int tc = mixed ? 0 : 1; tc <= 1; ++tc) {
+    for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
       p->zs_rb = rb;
       p->use_tc = tc != 0;
       solve_core(p, w, st, f, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up

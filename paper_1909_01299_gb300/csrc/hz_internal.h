@@ -92,8 +92,13 @@ struct TCSet {
   TCBlock* d_blocks = nullptr;
   TCTile* d_tiles = nullptr;
   float* d_tab = nullptr;
+  unsigned char* d_tmaps = nullptr;   // one 128-byte TMA tensor map per tile (its table rows)
 };
-size_t xform_tc_smem(int nt_max);
+// Encode the TMA tensor maps of the tiles (tables already on the device at d_tab) into
+// 128-byte records; false if the driver offers no encoder or rejects a map.
+bool tc_encode_tmaps(const float* d_tab, const std::vector<TCBlock>& blocks, const std::vector<TCTile>& tiles,
+                     std::vector<unsigned char>& bytes);
+size_t xform_tc_smem(int nt_max, bool in32);
 // Set the tensor-core kernel's shared-memory limit on the current device (before any capture).
 void xform_tc_prepare();
 // Host: append the TF32 hi/lo K-major tables of one block (complex table B, n x n row-major,

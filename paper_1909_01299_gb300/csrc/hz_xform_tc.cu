@@ -33,6 +33,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its enums; the encoder is fetched from the driver at run time
+
 #include "hz_convert.cuh"
 #include "hz_internal.h"
 
@@ -111,6 +113,21 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Arrive on the barrier (this thread) and add bytes to its expected transaction count.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// 3-D tiled TMA load (tensor map in global memory) completing on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
@@ -151,47 +168,58 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory plan of one CTA (offsets from a 1024-byte aligned base):
-//   raw[2]   : data chunks as loaded, 128 rows x 8 complex (16 KB each; complex64 data use
-//              the first half)
+//   raw[2]   : data chunks as loaded, 128 rows x 8 complex (16 KB each for complex128 data,
+//              8 KB for complex64)
 //   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 8 KB each), 64B-swizzled
-//   bop[2]   : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled
-//   bars     : MMA-completion mbarriers of the two operand stages, TMEM address slot
-// The chunk pipeline: while chunk c is converted, the MMAs of chunk c-1 run and the table
-// rows of chunk c and the FP64 rows of chunk c+1 are in flight (cp.async).
+//   bop[NB]  : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled; three
+//              stages for complex64 data, two for complex128 (whose raw buffers are larger)
+//   bars     : MMA-completion mbarriers of the two operand stages, table-arrival mbarriers of
+//              the table stages, TMEM address slot
+// The chunk pipeline: while chunk c is converted, the MMAs of chunk c-1 run (those of chunk c
+// are queued behind them as soon as c is converted), the table rows of chunk c are in flight
+// (one TMA copy per chunk: a 16 x nt x 2 box of the tile's 3-D tensor map [plane][row][k]
+// with the 64-byte swizzle, which lands in exactly the operand layout above) and so are the
+// data rows of chunk c+1 (cp.async: a block may start at any column, so its rows have no
+// 16-byte alignment a TMA box would need).
 constexpr int RAW_ROWB = KCH * 8;        // FP64 bytes of a data row in a chunk (KCH / 2 complex)
 constexpr int RAW_BYTES = TC_M * RAW_ROWB;
+__host__ __device__ constexpr int nbstages(bool in32) { return in32 ? 3 : 2; }
+__host__ __device__ constexpr int raw_bytes(bool in32) { return in32 ? RAW_BYTES / 2 : RAW_BYTES; }
 
 // TI / TO: double2 (complex128) or float2 (complex64) input / output elements.
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM)
 xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __restrict__ tabs,
-                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles, int ntiles,
+                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles,
+                const unsigned char* __restrict__ tmaps, int ntiles,
                 long long nrows, int rows_per_plane, int ncols, int trans, int store,
                 const signed char* __restrict__ rowskip, int* __restrict__ err) {
   extern __shared__ uint8_t smem_dyn[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   // column tiles of one row tile are consecutive CTAs (the data rows come from L2 the second time)
-  const TCTile t = tiles[blockIdx.x % ntiles];
+  const int tile = (int)(blockIdx.x % ntiles);
+  const TCTile t = tiles[tile];
+  const void* tmap = tmaps + (size_t)tile * 128;           // this tile's 128-byte tensor map
   const TCBlock b = blocks[t.blk];
   const long long row0 = (long long)(blockIdx.x / ntiles) * TC_M;
   const int nt = t.nt;
   const int B_BYTES = nt * ROWB;                           // one table plane of a chunk
+  constexpr bool IN32 = sizeof(TI) == 8, OUT32 = sizeof(TO) == 8;
+  constexpr int RROWB = (int)sizeof(TI) * (KCH / 2);       // bytes of a data row in a chunk
+  constexpr int RAWB = raw_bytes(IN32), NB = nbstages(IN32);
   const uint32_t s_base = smem_u32(smem);
-  const uint32_t raw0 = s_base, aop0 = raw0 + 2 * RAW_BYTES, bop0 = aop0 + 2 * 2 * A_BYTES;
+  const uint32_t raw0 = s_base, aop0 = raw0 + 2 * RAWB, bop0 = aop0 + 2 * 2 * A_BYTES;
   const uint32_t BSTAGE = 2 * B_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * RAW_BYTES + 4 * A_BYTES + 2 * BSTAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * RAWB + 4 * A_BYTES + NB * BSTAGE);
+  uint64_t* tbars = bars + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + NB);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = b.size;
   const int nk = b.kpad / KCH;
-  const float* __restrict__ thi = tabs + b.toff + (long long)t.n0 * b.kpad;
-  const float* __restrict__ tlo = thi + (long long)b.npad * b.kpad;
 
-  constexpr bool IN32 = sizeof(TI) == 8, OUT32 = sizeof(TO) == 8;
-  constexpr int RROWB = (int)sizeof(TI) * (KCH / 2);       // bytes of a data row in a chunk
   // issue the data rows of chunk c (8 complex per row) into raw[c & 1]
   auto load_raw = [&](int c) {
-    const uint32_t dst = raw0 + (c & 1) * RAW_BYTES;
+    const uint32_t dst = raw0 + (c & 1) * RAWB;
 #pragma unroll
     for (int q = 0; q < TC_M * (KCH / 2) / TC_THREADS; ++q) {
       const int task = tid + TC_THREADS * q;               // row = task / 8, complex = task % 8
@@ -204,16 +232,11 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
       else cp_async16(dst + r * RROWB + cc * 16, src, ok);
     }
   };
-  // issue the table rows (hi and lo) of chunk c into bop[c & 1], 64B-swizzled
+  // (thread 0) one TMA copy of the table rows (hi and lo planes) of chunk c into bop[c % NB]
   auto load_b = [&](int c) {
-    const uint32_t bh = bop0 + (c & 1) * BSTAGE, bl = bh + B_BYTES;
-    for (int task = tid; task < nt * (ROWB / 16); task += TC_THREADS) {
-      const int r = task >> 2, cc = task & 3;
-      const long long go = (long long)r * b.kpad + c * KCH + 4 * cc;
-      const uint32_t off = swz64(r, cc);
-      cp_async16(bh + off, thi + go, true);
-      cp_async16(bl + off, tlo + go, true);
-    }
+    uint64_t* tb = &tbars[c % NB];
+    mbar_expect_tx(tb, (uint32_t)(2 * B_BYTES));
+    tma_load_3d(bop0 + (c % NB) * BSTAGE, tmap, c * KCH, t.n0, 0, tb);
   };
 
   if (warp == 0) {
@@ -224,12 +247,12 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    for (int q = 0; q < NB; ++q) mbar_init(&tbars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_b(0);
   }
-  // prologue: groups {A0}, {B0}, {A1}
+  // prologue: cp.async groups {A0}, {A1}; table chunk 0 by TMA
   load_raw(0);
-  cp_async_commit();
-  load_b(0);
   cp_async_commit();
   if (nk > 1) load_raw(1);
   cp_async_commit();
@@ -241,19 +264,23 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
   bool ok = true;
   int issued = 0;
 
-  // Iteration kc: (1) wait for this thread's data rows of chunk kc; (2) convert them into
-  // the operand stage kc & 1 (free: the MMAs of kc-2 were waited for in iteration kc-1);
-  // (3) wait for the MMAs of kc-1 -- they ran while we converted -- and the table rows of
-  // kc; (4) one thread issues the MMAs of kc; (5) start the table rows of kc+1 (their stage
-  // was read by kc-1) and the data rows of kc+2 (their buffer was converted in (2)).
-  // cp.async groups are committed in the order A0 B0 A1 | B1 A2 | B2 A3 | ..., so at (1)
-  // all but the newest two {B(kc), A(kc+1)} are complete, at (3) all but A(kc+1).
+  // Iteration kc: (1) wait for this thread's data rows of chunk kc and for the MMAs of kc-2,
+  // the last reader of operand stage kc & 1; (2) convert the rows into that stage (the MMAs
+  // of kc-1 run meanwhile); (3) thread 0 waits for the table rows of kc, (4) queues the MMAs
+  // of kc behind those of kc-1 and (5) issues the TMA copy of the table rows of kc+1 into
+  // stage (kc+1) % NB, last read by the MMAs of kc+1-NB (with two stages: kc-1, which thread
+  // 0 waits for first); (6) all threads start the data rows of kc+2 (their buffer was
+  // converted in (2)).  cp.async groups are committed in the order A0 A1 | A2 | A3 | ...,
+  // so at (1) all but the newest group A(kc+1) are complete.
+  int tab_issued = (tid == 0) ? 1 : 0, tab_done = 0;        // (thread 0) table copies issued / arrived
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
-    cp_async_wait<2>();                                     // raw A(kc) has landed
-    __syncthreads();
+    cp_async_wait<1>();                                     // raw A(kc) has landed
+    int w = 1;
+    if (kc >= 2) w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
+    if (!__syncthreads_and(w)) { ok = false; break; }       // every thread's rows in; stage s free
     {
-      const uint32_t rsrc = raw0 + s * RAW_BYTES;
+      const uint32_t rsrc = raw0 + s * RAWB;
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
 #pragma unroll
       for (int q = 0; q < TC_M * (ROWB / 16) / TC_THREADS; ++q) {
@@ -284,15 +311,17 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
         st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
     }
-    int w = 1;
-    if (kc >= 1) w = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1) ? 1 : 0;
-    cp_async_wait<1>();                                     // table rows B(kc) have landed
+    int w2 = 1;
+    if (tid == 0) {
+      if (tab_done < tab_issued && mbar_wait(&tbars[kc % NB], (kc / NB) & 1)) tab_done = kc + 1;
+      if (tab_done != kc + 1) w2 = 0;                       // table rows of kc missing
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (!__syncthreads_and(w)) { ok = false; break; }       // operands of kc ready, MMA(kc-1) done
+    if (!__syncthreads_and(w2)) { ok = false; break; }      // operands of kc ready
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
-      const uint32_t b_hi = bop0 + s * BSTAGE, b_lo = b_hi + B_BYTES;
+      const uint32_t b_hi = bop0 + (kc % NB) * BSTAGE, b_lo = b_hi + B_BYTES;
 #pragma unroll
       for (int ks = 0; ks < KCH / 8; ++ks) {               // 8 tf32 = 32 bytes per MMA
         const uint32_t koff = ks * 32;
@@ -304,14 +333,25 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
         mma_tf32(tmem, dal, dbh, idesc, 1u);
       }
       mma_commit(&bars[s]);
+      if (kc + 1 < nk) {
+        // the stage of table chunk kc+1 was last read by the MMAs of kc+1-NB: with three
+        // stages those of kc-2, waited for in (1); with two those of kc-1
+        bool free_stage = true;
+        if (NB == 2 && kc >= 1) free_stage = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1);
+        if (free_stage) { load_b(kc + 1); tab_issued = kc + 2; }
+      }
     }
     issued = kc + 1;
-    if (kc + 1 < nk) load_b(kc + 1);
-    cp_async_commit();
     if (kc + 2 < nk) load_raw(kc + 2);
     cp_async_commit();
   }
   cp_async_wait<0>();                                       // no copy left in flight
+  // (thread 0) a table copy that has not arrived (no later one was issued): wait for it once
+  // more, bounded, before the shared memory is given up
+  if (tid == 0 && tab_done < tab_issued) {
+    const int c = tab_issued - 1;
+    mbar_wait(&tbars[c % NB], (c / NB) & 1);
+  }
   if (issued > 0) {
     const int last = issued - 1;
     if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) ok = false;
@@ -365,8 +405,9 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __
     } else {
       // Rows are contiguous in memory: stage the FP32 accumulator tile in the (now idle)
       // pipeline buffers -- 128 rows x nt floats, row stride padded by 16 bytes so that the
-      // row-per-lane writes are conflict-free; nt * 512 + 2048 bytes fit in the
-      // 65536 + 256 * nt bytes of the buffers for every nt <= 252 -- then each warp writes
+      // row-per-lane writes are conflict-free; nt * 512 + 2048 bytes fit in the buffers
+      // (65536 + 256 * nt bytes for complex128 input, 49152 + 384 * nt for complex64) for
+      // every nt <= 248 -- then each warp writes
       // whole rows, consecutive lanes on consecutive complex columns, converting to FP64.
       const int sstride = nt * 4 + 16;
       for (int c16 = 16 * cgrp; c16 < nt; c16 += 16 * NGRP) {
@@ -477,9 +518,45 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
   }
 }
 
-size_t xform_tc_smem(int nt_max) {
+bool tc_encode_tmaps(const float* d_tab, const std::vector<TCBlock>& blocks, const std::vector<TCTile>& tiles,
+                     std::vector<unsigned char>& bytes) {
+  using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<EncodeTiled>(fn);
+  }
+  std::vector<CUtensorMap> maps(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    const TCBlock& b = blocks[tiles[i].blk];
+    // [plane][row][k] view of the block's hi | lo tables; box = one chunk of K x the tile's rows
+    // x both planes, 64-byte swizzle (the K-major operand layout of the MMA descriptors)
+    const cuuint64_t dims[3] = {(cuuint64_t)b.kpad, (cuuint64_t)b.npad, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)b.kpad * 4, (cuuint64_t)b.npad * b.kpad * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)KCH, (cuuint32_t)tiles[i].nt, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d_tab + b.toff), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  static_assert(sizeof(CUtensorMap) == 128, "tensor maps are 128 bytes");
+  bytes.resize(maps.size() * sizeof(CUtensorMap));
+  if (!maps.empty()) std::memcpy(bytes.data(), maps.data(), bytes.size());
+  return true;
+}
+
+size_t xform_tc_smem(int nt_max, bool in32) {
   // at least 80 KB, so that no more than TC_CTAS_PER_SM CTAs (each holding TMEM_COLS) share an SM
-  const size_t need = 1024 + 2 * RAW_BYTES + 4 * A_BYTES + 4 * (size_t)nt_max * ROWB + 64;
+  const size_t need = 1024 + 2 * (size_t)raw_bytes(in32) + 4 * A_BYTES +
+                      (size_t)nbstages(in32) * 2 * nt_max * ROWB + 64;
   return std::max(need, (size_t)80 * 1024);
 }
 
@@ -488,7 +565,7 @@ uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }
 template <typename TI, typename TO>
 void set_smem_attr() {
   cudaFuncSetAttribute(xform_tc_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)xform_tc_smem(kTcMaxN));
+                       (int)xform_tc_smem(kTcMaxN, sizeof(TI) == 8));
 }
 
 void xform_tc_prepare() {
@@ -509,15 +586,16 @@ bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, i
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
               cudaStream_t st) {
   if (out32 && store != XS_STORE) return false;          // accumulation needs a complex128 output
+  if (!ts.d_tmaps) return false;
   const long long nrows = nplanes * (long long)rows_per_plane;
   if (nrows <= 0 || ts.ntiles == 0) return true;
   xform_tc_prepare();
   const long long ctas = ((nrows + TC_M - 1) / TC_M) * ts.ntiles;
-  const size_t smem = xform_tc_smem(ts.nt_max);
+  const size_t smem = xform_tc_smem(ts.nt_max, in32 != 0);
 #define HZ_TC_LAUNCH(TI, TO)                                                                          \
   xform_tc_kernel<TI, TO><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                                 \
-      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_tab, ts.d_blocks, ts.d_tiles, ts.ntiles, \
-      nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
+      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_tab, ts.d_blocks, ts.d_tiles, ts.d_tmaps,  \
+      ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
   if (in32 && out32) HZ_TC_LAUNCH(float2, float2);
   else if (in32) HZ_TC_LAUNCH(float2, double2);
   else if (out32) HZ_TC_LAUNCH(double2, float2);
