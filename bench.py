@@ -125,6 +125,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def tf32_peak():
+    """TF32 dense TFLOP/s: the measured bf16 burst figure x the nominal TF32 / bf16 ratio."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh).get("bf16_tflops", 1900.0))
+        src = "measured bf16 burst x 1.1/2.25 (nominal TF32/bf16)"
+    except (OSError, ValueError):
+        bf16, src = 1900.0, "fallback bf16 x 1.1/2.25 (nominal TF32/bf16)"
+    return bf16 * 1.1 / 2.25, src
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """The slowest rank's time: all-reduce(MAX) of a per-rank scalar (identity without dist)."""
     if dist is None:
@@ -355,6 +366,13 @@ def run_hz(args):
                "frac": tc_bytes / (tc_launch_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
                "bytes_per_launch": tc_bytes, "launch_ms": tc_launch_ms,
                "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
+    # the same launches against the tensor pipe: 3 TF32 products (3xTF32) of 8 real flops per
+    # complex multiply-add of the block transforms
+    tc_flops = sum(macs) / 4 * 8 * 3
+    tpk, tsrc = tf32_peak()
+    roof_tc["tensor"] = {"achieved": tc_flops / (tc_launch_ms * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                         "frac": tc_flops / (tc_launch_ms * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
+                         "flops_per_launch": tc_flops}
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -13,21 +13,22 @@
 // refinement of the solve removes the rest.
 //
 // One CTA (8 warps) computes a 128-row x Nt-column tile (Nt <= 160, a multiple of
-// 16) of one block; two CTAs share an SM (about 105 KB of shared memory and 256 TMEM
-// columns each), so that one CTA's loads overlap the other's prologue and epilogue.
-// The contraction runs in chunks of 16 real K (64 bytes per operand row): all
-// threads convert the data rows (complex128, or complex64 for the mixed path's
-// mode-space volumes, which carry FP32 accuracy only) to TF32 hi/lo and store them,
-// with the tables' hi/lo rows, in shared memory in the K-major 64-byte-swizzled layout; one thread
-// issues the 6 MMAs of the chunk and commits them to the chunk's mbarrier; two chunk
-// buffers alternate, so the conversion of chunk c+1 overlaps the MMAs of chunk c.
+// 16) of one block; two CTAs share an SM (108-112 KB of shared memory and 256 TMEM
+// columns each).  The contraction runs in chunks of 16 real K (64 bytes per operand
+// row): all threads convert the data rows (complex128, or complex64 for the mixed
+// path's mode-space volumes, which carry FP32 accuracy only) to TF32 hi/lo and store
+// them in shared memory in the K-major 64-byte-swizzled layout; the tables' hi/lo rows
+// arrive in the same layout by one TMA copy per chunk; one thread queues the 6 MMAs of
+// the chunk behind those of the previous chunk and commits them to the chunk's
+// mbarrier; two operand stages alternate, so the conversion of chunk c+1 overlaps the
+// MMAs of chunk c.
 // The epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM lanes
 // 32(w%4)..+31 = tile rows, column chunks w/4, w/4+2, ...) and stores it as complex128
 // (exact) or complex64: transposed outputs straight from registers (a warp's 32 rows are
 // consecutive addresses), row-contiguous outputs through an FP32 staging tile in
 // shared memory written out row by row; optionally adding to the old values.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
-// waits (bounded) for its own MMAs, frees its tensor memory and returns.
+// waits (bounded) for its own MMAs and copies, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
