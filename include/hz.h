@@ -117,6 +117,9 @@ typedef struct {
   long long device_bytes;    /* device memory owned by the plan                         */
   long long kernel_launches; /* kernels launched by this plan's solves so far           */
   int nbx, nby;              /* block partition in use                                  */
+  int tensor_cores;          /* 1: the mixed path's bulk transforms run on the tensor
+                                cores (tcgen05, 3xTF32) with complex64 mode-space data;
+                                0: FP32 CUDA-core transforms on complex128 data          */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's

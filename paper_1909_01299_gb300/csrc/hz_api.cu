@@ -1768,6 +1768,7 @@ hz_status hz_get_stage_times(hz_plan_t p, double* ms, long long* launches) {
 hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   if (!p || !out) return HZ_ERR_ARG;
   p->info.device_bytes = p->bytes;
+  p->info.tensor_cores = p->use_tc ? 1 : 0;
   *out = p->info;
   return HZ_OK;
 }

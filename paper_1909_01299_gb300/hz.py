@@ -47,7 +47,8 @@ class hz_info(ctypes.Structure):
     _fields_ = [("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("min_abs_pivot", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("eig_max_residual", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong), ("nbx", ctypes.c_int), ("nby", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_longlong), ("nbx", ctypes.c_int), ("nby", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 # Every symbol declared in include/hz.h, with its ctypes signature.

@@ -1,0 +1,63 @@
+"""Mixed path at the edges of its tiling and storage (needs a GB300).
+
+Blocks wider than one tensor-core column tile (the table rows of the later tiles start at a
+non-zero row of the block's tensor map), one and two z planes (the complex64 z sweep with
+no back-substitution step), odd block starts and odd right-hand-side counts; every result
+is compared with the oracle's sparse LU on the same seeded input.
+"""
+import numpy as np
+import pytest
+
+from oracle import hz_oracle as O
+from paper_1909_01299_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-8
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01299_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def hz(torch_cuda):
+    from paper_1909_01299_gb300 import hz as mod
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def solve_and_check(hz, torch, w, precision):
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan = hz.Plan.from_workload(w, precision=precision)
+    u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+    info = plan.info()
+    if precision == "mixed":
+        assert info["tensor_cores"] == 1
+        assert info["rel_residual"] <= 1e-8
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+# x block of 150 nodes: two column tiles of 144 and 160 real columns; y block of 170
+# nodes: three tiles of 112, 112 and 128
+@pytest.mark.parametrize("kw", [dict(nx=150, ny=20, nz=6, bx=1, by=2, rim=6, pml=3, nrhs=1),
+                                dict(nx=30, ny=170, nz=5, bx=2, by=1, rim=6, pml=3, nrhs=3)])
+def test_mixed_blocks_wider_than_one_tile(hz, torch_cuda, kw):
+    solve_and_check(hz, torch_cuda, W.tiny_pml(**kw), "mixed")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nz", [1, 2])
+def test_one_and_two_z_planes(hz, torch_cuda, nz, precision):
+    solve_and_check(hz, torch_cuda, W.tiny_pml(nx=23, ny=19, nz=nz, bx=2, by=3, rim=4, pml=2, nrhs=3),
+                    precision)
