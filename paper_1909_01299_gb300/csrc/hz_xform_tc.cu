@@ -190,9 +190,8 @@ __host__ __device__ constexpr int raw_bytes(bool in32) { return in32 ? RAW_BYTES
 // TI / TO: double2 (complex128) or float2 (complex64) input / output elements.
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM)
-xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const float* __restrict__ tabs,
-                const TCBlock* __restrict__ blocks, const TCTile* __restrict__ tiles,
-                const unsigned char* __restrict__ tmaps, int ntiles,
+xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* __restrict__ blocks,
+                const TCTile* __restrict__ tiles, const unsigned char* __restrict__ tmaps, int ntiles,
                 long long nrows, int rows_per_plane, int ncols, int trans, int store,
                 const signed char* __restrict__ rowskip, int* __restrict__ err) {
   extern __shared__ uint8_t smem_dyn[];
@@ -595,7 +594,7 @@ bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, i
   const size_t smem = xform_tc_smem(ts.nt_max, in32 != 0);
 #define HZ_TC_LAUNCH(TI, TO)                                                                          \
   xform_tc_kernel<TI, TO><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                                 \
-      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_tab, ts.d_blocks, ts.d_tiles, ts.d_tmaps,  \
+      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, ts.d_tiles, ts.d_tmaps,            \
       ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
   if (in32 && out32) HZ_TC_LAUNCH(float2, float2);
   else if (in32) HZ_TC_LAUNCH(float2, double2);
