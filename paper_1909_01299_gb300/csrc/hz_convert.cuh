@@ -54,7 +54,6 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   return __hiloint2double((int)(sign | (e64 << 20) | ((u & 0x7fffffu) >> 3)), (int)((u & 7u) << 29));
 }
 
-__device__ __forceinline__ float2 to_c64(double2 v) { return make_float2(f64_to_f32(v.x), f64_to_f32(v.y)); }
 __device__ __forceinline__ double2 to_c128(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
 
 // Identity forms, so that kernels templated on the storage type (the mixed path keeps its
