@@ -167,6 +167,17 @@ def bulk_macs(w, nrhs):
     return [per * rows_x * sx, per * rows_y * sy, per * rows_y * sy, per * rows_x * sx]
 
 
+def tc_bytes_per_launch(w, nrhs, nref):
+    """Algorithmic HBM bytes of a tensor-core transform launch, averaged over a mixed step.
+
+    A step is 1 + nref solves of 4 launches over the block values (interface rows and
+    columns excluded): forward x 24 B per value (complex128 in, complex64 out), forward y
+    and inverse y 16 B, inverse x 24 B, or 40 B when it accumulates a correction into u.
+    """
+    values = (w.nx - len(w.x_iface)) * (w.ny - len(w.y_iface)) * w.nz * nrhs
+    return values * (80 + 96 * nref) / (4 * (1 + nref))
+
+
 def kernel_source_hash(fname: str = "hz_xform.cu"):
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_1909_01299_gb300", "csrc", fname), "rb") as fh:
@@ -358,9 +369,7 @@ def run_hz(args):
     # correction (40 B); averaged over the 4 (1 + refinements) launches of a step.
     hbm_peak, hbm_src = measured_peaks()
     tc_launch_ms = (stmx["fwd"][0] + stmx["inv"][0]) / max(1, stmx["fwd"][1] + stmx["inv"][1])
-    nref = int(infomx.get("refinements", 0))
-    tc_values = (w.nx - len(w.x_iface)) * (w.ny - len(w.y_iface)) * w.nz * R
-    tc_bytes = tc_values * (80 + 96 * nref) / (4 * (1 + nref))
+    tc_bytes = tc_bytes_per_launch(w, R, int(infomx.get("refinements", 0)))
     roof_tc = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
                "achieved": tc_bytes / (tc_launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                "frac": tc_bytes / (tc_launch_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,

@@ -1,0 +1,52 @@
+"""The benchmark's work and byte accounting (CPU): the counts behind its roofline figures,
+checked against hand-computed values for the pml-160 workload (160 x 160 x 128, one
+interface per axis at node 79, so blocks of 79 and 80 nodes, 4 RHS)."""
+import json
+import os
+
+from paper_1909_01299_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_bulk_transform_multiply_adds():
+    import bench
+    w = W.pml_160x160x128()
+    # per launch: RHS x planes x rows outside the other axis' interface x sum of n^2 over blocks
+    per_launch = 4 * 128 * 159 * (79 * 79 + 80 * 80)
+    assert bench.bulk_macs(w, 4) == [per_launch] * 4
+
+
+def test_tensor_core_bytes_per_launch():
+    import bench
+    w = W.pml_160x160x128()
+    values = 159 * 159 * 128 * 4
+    # one solve: 24 + 16 + 16 + 24 B per value over 4 launches
+    assert bench.tc_bytes_per_launch(w, 4, 0) == values * 80 / 4
+    # with one accumulating correction: + 24 + 16 + 16 + 40 B over 4 more launches
+    assert bench.tc_bytes_per_launch(w, 4, 1) == values * (80 + 96) / 8
+
+
+def test_tf32_peak_follows_the_measured_bf16_figure():
+    import bench
+    peak, src = bench.tf32_peak()
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        bf16 = float(json.load(fh)["bf16_tflops"])
+    assert abs(peak - bf16 * 1.1 / 2.25) < 1e-9
+    assert src.startswith("measured")
+
+
+def test_traffic_records_are_dropped_for_changed_sources(tmp_path, monkeypatch):
+    import bench
+    w_name = "pml-160x160x128-2x2blocks-4rhs-fp64"
+    rec = {"xform_tc_kernel": {"source_sha": "0" * 16, "workload": w_name, "bytes_per_launch": 1}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    src = tmp_path / "paper_1909_01299_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "hz_xform_tc.cu").write_text("// another source\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("xform_tc_kernel", w_name, "hz_xform_tc.cu") is None
+    rec["xform_tc_kernel"]["source_sha"] = bench.kernel_source_hash("hz_xform_tc.cu")
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.profiled_traffic("xform_tc_kernel", w_name, "hz_xform_tc.cu") == 1
