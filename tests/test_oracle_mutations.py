@@ -12,7 +12,7 @@ from tests import oracle_pins as pins
 
 _orig = {name: getattr(O, name) for name in
          ["stiffness", "dual_lengths", "fwd", "inv", "z_coefficients", "mode_solve", "apply_A",
-          "gen_eig", "sigma_half", "weighted_rhs", "adjoint_solve", "layer_gradient"]}
+          "gen_eig", "sigma_half", "weighted_rhs", "adjoint_solve", "layer_gradient", "axis_blocks"]}
 
 
 def _any_pin_fails():
@@ -98,7 +98,31 @@ def _mut_adjoint_no_conj(P, g, A=None, method="blk"):
     return solver(P, g, A)
 
 
+def _mut_blocks_take_interface(n, ifaces):
+    blocks = _orig["axis_blocks"](n, ifaces)
+    if len(blocks) > 1:                                 # the first block swallows its interface node
+        blocks[0] = (blocks[0][0], blocks[0][1] + 1)
+    return blocks
+
+
+def _mut_block_offdiag_shift(h, start, size):
+    kd, ko = O.stiffness(h)
+    m = O.dual_lengths(h)
+    sl = slice(start, start + size)
+    return O.gen_eig(kd[sl], np.roll(ko[start:start + size - 1], 1), m[sl])   # couplings one step along
+
+
+def _mut_iface_mask_x_only(P):
+    nz, ny, nx = P.shape
+    mask = np.zeros((ny, nx), dtype=bool)
+    mask[:, P.x_iface] = True                           # the y interfaces forgotten
+    return mask
+
+
 MUTATIONS = {
+    "block_takes_its_interface_node": ("axis_blocks", _mut_blocks_take_interface),
+    "block_offdiag_one_step_along": ("block_eig", _mut_block_offdiag_shift),
+    "interfaces_x_only": ("iface_mask", _mut_iface_mask_x_only),
     "stiffness_offdiag_sign": ("stiffness", _mut_stiffness_sign),
     "stiffness_offdiag_index": ("stiffness", _mut_stiffness_index),
     "dual_lengths_not_averaged": ("dual_lengths", _mut_dual_lengths),
