@@ -30,10 +30,15 @@ def test_tensor_core_bytes_per_launch():
 def test_tf32_peak_follows_the_measured_bf16_figure():
     import bench
     peak, src = bench.tf32_peak()
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-        bf16 = float(json.load(fh)["bf16_tflops"])
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        assert src.startswith("measured")
+    else:                                   # the peaks file is written per machine
+        bf16 = 1900.0
+        assert src.startswith("fallback")
     assert abs(peak - bf16 * 1.1 / 2.25) < 1e-9
-    assert src.startswith("measured")
 
 
 def test_traffic_records_are_dropped_for_changed_sources(tmp_path, monkeypatch):
