@@ -83,8 +83,8 @@ typedef struct {
  * count: the FP64 path balances the dense block transforms (cost ~ N / B per unknown)
  * against the interface steps (cost ~ B), B ~ sqrt(N) as in the cost estimate of Sec. 2,
  * with blocks at least 16 nodes wide; the mixed path, whose block transforms run on
- * tensor cores at memory speed, takes blocks about 80 nodes wide.  hz_get_info reports
- * the counts chosen. */
+ * the tensor cores (where a wider block costs little more per value), takes blocks
+ * about 80 nodes wide.  hz_get_info reports the counts chosen. */
 #define HZ_BLOCKS_AUTO 0
 typedef struct {
   int nbx, nby;
@@ -96,9 +96,11 @@ typedef struct {
  * residual and the refinement residual in FP64; FP64 iterative refinement until the
  * relative residual ||M f - A u|| / ||M f|| <= rtol for every RHS, at most max_refine
  * corrections; HZ_ERR_NOT_CONVERGED otherwise).  The mixed path carries transformed data
- * in FP32: values below about 1e-30 or above 1e30 lose precision there (the refinement
- * then reports non-convergence rather than a wrong answer), so scale such right-hand
- * sides.  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+ * in FP32 (with tensor-core transforms the mode-space volumes are stored as complex64;
+ * the z eliminations keep FP64 values): values below about 1e-30 or above 1e30 lose
+ * precision there (the refinement then reports non-convergence rather than a wrong
+ * answer), so scale such right-hand sides.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream). */
 typedef struct {
   int precision;
   double rtol;
@@ -144,9 +146,12 @@ hz_status hz_get_stage_times(hz_plan_t plan, double *ms, long long *launches);
 /* Build a plan: 1D operators, per-block and global generalized eigenpairs
  * (K_d W = M_d W Lambda, W^T M_d W = I; the display after Eq. (fdmtrprj) and
  * before Eq. (fdmtrprjfrerr)), the z elimination factors of every mode, and all
- * device tables.  Errors: HZ_ERR_ARG on bad sizes/pointers, HZ_ERR_EIG when an
- * eigen-decomposition fails its checks, HZ_ERR_SINGULAR on a singular pivot,
- * HZ_ERR_OOM / HZ_ERR_CUDA on device failures.  *out is NULL on error. */
+ * device tables (for the tensor-core transforms also one TMA tensor map per tile, encoded
+ * through the driver; if the driver offers no encoder, mixed plans use the CUDA-core FP32
+ * transforms and hz_get_info reports tensor_cores = 0).  Errors: HZ_ERR_ARG on bad
+ * sizes/pointers, HZ_ERR_EIG when an eigen-decomposition fails its checks,
+ * HZ_ERR_SINGULAR on a singular pivot, HZ_ERR_OOM / HZ_ERR_CUDA on device failures.
+ * *out is NULL on error. */
 hz_status hz_plan_create(const hz_grid *grid, const hz_layers *layers, const hz_blocks *blocks,
                          const hz_options *opts, hz_plan_t *out);
 
