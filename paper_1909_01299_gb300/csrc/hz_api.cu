@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only; the ranges cost nothing unless a profiler is attached
+
 #include "hz_internal.h"
 
 using hz::cd;
@@ -138,10 +140,28 @@ void ck(cudaError_t e) {
   if (e != cudaSuccess) throw Fail{HZ_ERR_CUDA};
 }
 
-// Records CUDA events around a stage when the plan's stage timers are on.
+// A named NVTX range for profilers (host timeline; the launches inside it correlate).
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* const kStageNames[HZ_NSTAGES] = {
+    "hz step 1: forward x/y transforms", "hz step 2: block z solves",
+    "hz step 3: v next to the interfaces", "hz step 4: interface residual",
+    "hz step 5: global interface solve", "hz step 6: boundary terms and block z solves",
+    "hz step 7: inverse x/y transforms", "hz step 7: u on the interfaces",
+    "hz residual / refinement"};
+
+// Records CUDA events around a stage when the plan's stage timers are on, and marks the
+// stage as an NVTX range.
 class Stage {
  public:
-  Stage(hz_plan_t p, cudaStream_t st, int stage) : p_(p), st_(st), stage_(stage), l0_(hz::launch_count()) {
+  Stage(hz_plan_t p, cudaStream_t st, int stage)
+      : range_(kStageNames[stage]), p_(p), st_(st), stage_(stage), l0_(hz::launch_count()) {
     if (p_->timing) a_ = next_event(), ck(cudaEventRecord(a_, st_));
   }
   ~Stage() {
@@ -161,6 +181,7 @@ class Stage {
     }
     return p_->ev_pool[p_->ev_used++];
   }
+  NvtxRange range_;
   hz_plan_t p_;
   cudaStream_t st_;
   int stage_;
@@ -1709,6 +1730,7 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
 
 hz_status hz_grad_layers(hz_plan_t p, const hz_c128* u, const hz_c128* lam, int nrhs, hz_c128* G_host) {
   if (!p || !u || !lam || !G_host || nrhs < 1) return HZ_ERR_ARG;
+  NvtxRange range("hz layer gradient");
   try {
     Workspace& w = p->ws;
     const int parts = hz::grad_parts(p->nx, p->ny, nrhs);
