@@ -12,7 +12,8 @@ from tests import oracle_pins as pins
 
 _orig = {name: getattr(O, name) for name in
          ["stiffness", "dual_lengths", "fwd", "inv", "z_coefficients", "mode_solve", "apply_A",
-          "gen_eig", "sigma_half", "weighted_rhs", "adjoint_solve", "layer_gradient", "axis_blocks"]}
+          "gen_eig", "sigma_half", "weighted_rhs", "adjoint_solve", "layer_gradient", "axis_blocks",
+          "residual", "residual_perturbed"]}
 
 
 def _any_pin_fails():
@@ -26,6 +27,8 @@ def _any_pin_fails():
         (lambda: pins.single_mode_error(blocks=(2, 2)), 1e-12),
         (lambda: pins.blk_vs_lu_error(W.tiny_pml(9, 8, 7, 2, 2, sigma=True)), 1e-12),
         (lambda: pins.adjoint_error(W.tiny_pml(9, 8, 7, 2, 2)), 1e-12),
+        (lambda: pins.residual_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1)), 1e-12),
+        (lambda: pins.residual_perturbed_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1, nrhs=2)), 1e-11),
     ]
     for fn, bound in checks:
         try:
@@ -119,7 +122,45 @@ def _mut_iface_mask_x_only(P):
     return mask
 
 
+def _mut_residual_without_M(P, u, f, A=None):
+    # the unweighted residual f - M^{-1} A u over ||f||
+    _, mdiag = O.assemble(P)
+    R = u.shape[0]
+    r = f.reshape(R, -1) - O.apply_A(P, u, A).reshape(R, -1) / mdiag[None]
+    return np.linalg.norm(r, axis=1) / np.linalg.norm(f.reshape(R, -1), axis=1)
+
+
+def _mut_residual_f_denominator(P, u, f, A=None):
+    # ||M f - A u|| over ||f|| instead of ||M f||
+    R = u.shape[0]
+    r = O.weighted_rhs(P, f) - O.apply_A(P, u, A)
+    return np.linalg.norm(r.reshape(R, -1), axis=1) / np.linalg.norm(f.reshape(R, -1), axis=1)
+
+
+def _mut_residual_pooled(P, u, f, A=None):
+    # one norm over all right-hand sides, repeated per RHS
+    r = O.weighted_rhs(P, f) - O.apply_A(P, u, A)
+    return np.full(u.shape[0], np.linalg.norm(r) / np.linalg.norm(O.weighted_rhs(P, f)))
+
+
+def _mut_residual_perturbed_dk2_sign(P, u, f, dk2, A=None):
+    return _orig["residual_perturbed"](P, u, f, -np.asarray(dk2), A)
+
+
+def _mut_residual_perturbed_dk2_unweighted(P, u, f, dk2, A=None):
+    # dk2 u added without the control-volume weight
+    R = u.shape[0]
+    b = O.weighted_rhs(P, f)
+    r = b - O.apply_A(P, u, A) + dk2[None] * u
+    return np.linalg.norm(r.reshape(R, -1), axis=1) / np.linalg.norm(b.reshape(R, -1), axis=1)
+
+
 MUTATIONS = {
+    "residual_without_M": ("residual", _mut_residual_without_M),
+    "residual_f_denominator": ("residual", _mut_residual_f_denominator),
+    "residual_pooled_over_rhs": ("residual", _mut_residual_pooled),
+    "residual_perturbed_dk2_sign": ("residual_perturbed", _mut_residual_perturbed_dk2_sign),
+    "residual_perturbed_dk2_unweighted": ("residual_perturbed", _mut_residual_perturbed_dk2_unweighted),
     "block_takes_its_interface_node": ("axis_blocks", _mut_blocks_take_interface),
     "block_offdiag_one_step_along": ("block_eig", _mut_block_offdiag_shift),
     "interfaces_x_only": ("iface_mask", _mut_iface_mask_x_only),

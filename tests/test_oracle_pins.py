@@ -83,6 +83,16 @@ def test_residual_support_after_block_solves():
     assert pins.residual_support_error(W.tiny_pml()) < 1e-12
 
 
+def test_residual_against_node_by_node_stencil():
+    # per-RHS ||M f - A u|| / ||M f|| from the loop-assembled stencil, u = exact + perturbation
+    assert pins.residual_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1)) < 1e-12
+
+
+def test_residual_perturbed_against_node_by_node_stencil():
+    # nonzero dk2: the perturbed residual from the loop-assembled perturbed stencil
+    assert pins.residual_perturbed_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1, nrhs=2)) < 1e-11
+
+
 def test_residual_of_block_solution():
     w = W.tiny_pml(16, 16, 16, 4, 4, rim=4, pml=2)
     P = O.Problem.from_workload(w)
