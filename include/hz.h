@@ -221,17 +221,19 @@ hz_status hz_residual(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev
                       double *rel_host);
 
 /* Allocation-free residual check (the paper has no counterpart; it serves callers of
- * this library that cannot call cudaMalloc at the time of the check: code running
- * while a CUDA graph is captured, serving or real-time loops that forbid device
- * allocation, frameworks that own all device memory).  Same result as hz_residual
- * (per-RHS ||M f - A u||_2 / ||M f||_2 into rel_host, nrhs entries) but all scratch
- * is a fixed 263 KB device array inside the library and no residual field is
- * written; nothing is allocated (no cudaMalloc, cudaFree or allocating library call).
- * nrhs must be <= 64 (HZ_ERR_ARG otherwise).  The array is shared by every call and
- * plan on a device: calls that overlap on the GPU race on it and must be serialised
- * by the caller.  The first call on a device looks the array up (make it before any
- * stream capture).  Stream-ordered on the plan's stream; returns after the result is
- * on the host.  Errors as hz_residual. */
+ * this library that cannot call cudaMalloc at the time of the check: serving or
+ * real-time loops that forbid device allocation, since an allocation can synchronise the
+ * device and fragment a memory pool, and frameworks that hand out all device memory
+ * themselves).  Same result as hz_residual (per-RHS ||M f - A u||_2 / ||M f||_2 into
+ * rel_host, nrhs entries) but all scratch is a fixed 263 KB device array inside the
+ * library and no residual field is written; nothing is allocated (no cudaMalloc,
+ * cudaFree or allocating library call).  nrhs must be <= 64, and the current device must
+ * be the one the plan was created on (HZ_ERR_ARG otherwise).  The array is shared by
+ * every call and plan on a device and keeps the last call's contents: calls that overlap
+ * on the GPU race on it and must be serialised by the caller.  The first call on a device
+ * looks the array's address up (make that first call before any stream capture).
+ * Stream-ordered on the plan's stream; the call waits for that stream and returns with
+ * the residuals on the host.  Errors as hz_residual. */
 hz_status hz_residual_noalloc(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev, int nrhs,
                               double *rel_host);
 

@@ -81,6 +81,7 @@ struct Workspace {
 
 struct hz_plan_s {
   int nx = 0, ny = 0, nz = 0, nlayers = 0;
+  int device = 0;                    // the device current at plan creation (owns tables and stream)
   hz_options opts{};
   cudaStream_t st = nullptr;
   AxisPlan ax, ay;
@@ -1289,6 +1290,7 @@ namespace hz {
 // Read-only views of a plan for the allocation-free residual (hz_noalloc.cu).
 StencilArgs plan_stencil_args(hz_plan_t p, int nrhs) { return stencil_args(p, nrhs); }
 cudaStream_t plan_stream(hz_plan_t p) { return p->st; }
+int plan_device(hz_plan_t p) { return p->device; }
 }  // namespace hz
 
 extern "C" {
@@ -1370,6 +1372,7 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   }
   if (s != HZ_OK) { delete p; return s; }
   try {
+    ck(cudaGetDevice(&p->device));
     ck(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));

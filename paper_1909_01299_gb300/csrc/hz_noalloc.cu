@@ -1,13 +1,12 @@
 // Residual check that allocates nothing (hz_residual_noalloc).
 //
 // Some callers cannot call cudaMalloc at the point where they want to check a
-// solution: code that runs while a CUDA graph is being captured, real-time or
-// serving loops that forbid device allocation (it can synchronise the device
-// and fragment a memory pool), and frameworks that hand out all device memory
-// themselves.  For them this entry point computes the same per-RHS relative
-// residual ||M f - A u||_2 / ||M f||_2 as hz_residual, but keeps its scratch
-// (per-CTA partial sums and the per-RHS results) in the fixed device array
-// below instead of the plan's workspace, and writes no residual field.
+// solution: real-time or serving loops that forbid device allocation (it can
+// synchronise the device and fragment a memory pool), and frameworks that hand
+// out all device memory themselves.  For them this entry point computes the same
+// per-RHS relative residual ||M f - A u||_2 / ||M f||_2 as hz_residual, but keeps
+// its scratch (per-CTA partial sums and the per-RHS results) in the fixed device
+// array below instead of the plan's workspace, and writes no residual field.
 //
 // The array lives as long as the library is loaded, on every GPU that loads
 // it, and is shared by all calls and plans: calls that overlap on the GPU
@@ -16,7 +15,9 @@
 // call reads is written earlier in the same call, so nothing needs clearing.
 // The first call on a device looks the array's address up with
 // cudaGetSymbolAddress while that device is current (make that first call
-// before any stream capture).
+// before any stream capture).  The plan's kernels and stream belong to the
+// device the plan was created on, so the call requires that device to be the
+// current one.
 #include <cmath>
 #include <mutex>
 
@@ -27,6 +28,7 @@ namespace hz {
 // Accessors of plan internals (defined in hz_api.cu).
 StencilArgs plan_stencil_args(hz_plan_t p, int nrhs);
 cudaStream_t plan_stream(hz_plan_t p);
+int plan_device(hz_plan_t p);
 
 namespace {
 
@@ -119,12 +121,11 @@ __global__ void resid_finish_kernel(const double* __restrict__ partial, int npar
   }
 }
 
-// Device address of g_scratch for the current device (looked up once per device).
-cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of g_scratch on device dev, which must be the current device (looked up
+// once per device).
+cudaError_t scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaError_t e = cudaSuccess;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
@@ -144,8 +145,11 @@ extern "C" hz_status hz_residual_noalloc(hz_plan_t plan, const hz_c128* f_dev, c
   using namespace hz;
   if (!plan || !f_dev || !u_dev || !rel_host || nrhs < 1) return HZ_ERR_ARG;
   if (nrhs > kMaxRhs) return HZ_ERR_ARG;          // beyond the fixed scratch array
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HZ_ERR_CUDA;
+  if (dev != plan_device(plan)) return HZ_ERR_ARG;   // the plan's stream and tables live on its device
   double* scratch = nullptr;
-  if (scratch_address(&scratch) != cudaSuccess) return HZ_ERR_CUDA;
+  if (scratch_address(dev, &scratch) != cudaSuccess) return HZ_ERR_CUDA;
   const StencilArgs a = plan_stencil_args(plan, nrhs);
   cudaStream_t st = plan_stream(plan);
   const long long n = (long long)a.nx * a.ny * a.nz;

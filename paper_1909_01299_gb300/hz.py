@@ -302,9 +302,10 @@ class Plan:
 def residual_noalloc(plan: Plan, f, u) -> np.ndarray:
     """hz_residual_noalloc: the residual check that allocates no device memory.
 
-    For callers that cannot allocate at the time of the check (inside a CUDA
-    graph capture, allocation-free serving loops); nrhs <= 64; concurrent calls on
-    one device must be serialised (they share one fixed scratch array).
+    For callers that cannot allocate device memory at the time of the check
+    (allocation-free serving or real-time loops, frameworks that own all device
+    memory); nrhs <= 64; the plan's device must be the current one; calls that
+    overlap on the GPU must be serialised (they share one fixed scratch array).
     """
     R = plan._check_tensor(f)
     plan._check_tensor(u)

@@ -1,8 +1,8 @@
 """The allocation-free residual check (hz_residual_noalloc) against hz_residual.
 
-Callers that cannot allocate device memory when they check a solution (inside a
-CUDA graph capture, allocation-free serving loops) use hz_residual_noalloc, whose
-scratch is a fixed array inside the library.  This file is collected last so that
+Callers that cannot allocate device memory when they check a solution
+(allocation-free serving or real-time loops, frameworks that own all device memory)
+use hz_residual_noalloc, whose scratch is a fixed array inside the library.  This file is collected last so that
 a run stopping at the first failure has already run every other test.
 """
 import numpy as np
