@@ -216,6 +216,15 @@ hz_status hz_solve_perturbed(hz_plan_t plan, const hz_c128 *dk2_dev, const hz_c1
 hz_status hz_grad_layers(hz_plan_t plan, const hz_c128 *u_dev, const hz_c128 *lam_dev, int nrhs,
                          hz_c128 *G_host);
 
+/* Gradient in the right-hand side.  The solve is u = A^{-1} M f (Eq. (fdmtr), M = Mz (x)
+ * My (x) Mx diagonal), so for a real objective J(u) with adjoint state lam = A^{-H} g,
+ * g = dJ/du* (hz_solve_adjoint), the gradient in f is M^H lam:
+ *     gf[r][k][j][i] = conj(hhat^x_i hhat^y_j hhat^z_k) lam[r][k][j][i].
+ * lam_dev, gf_dev: device arrays of nrhs right-hand sides (layout as f); gf_dev may equal
+ * lam_dev (in place).  Stream-ordered on the plan's stream; returns after the result is
+ * complete.  Errors: HZ_ERR_ARG, HZ_ERR_CUDA. */
+hz_status hz_grad_rhs(hz_plan_t plan, const hz_c128 *lam_dev, hz_c128 *gf_dev, int nrhs);
+
 /* Relative residuals ||M f - A u||_2 / ||M f||_2 per RHS (FP64), into rel_host (nrhs). */
 hz_status hz_residual(hz_plan_t plan, const hz_c128 *f_dev, const hz_c128 *u_dev, int nrhs,
                       double *rel_host);

@@ -364,6 +364,20 @@ def layer_gradient(P: Problem, u, lam):
     return np.array([p_k[P.z_begin[L]:P.z_begin[L + 1]].sum() for L in range(nl)])
 
 
+def rhs_gradient(P: Problem, lam):
+    """M^H lam: the gradient in f of a real objective J(u) whose adjoint state is lam.
+
+    The solve is u = A^{-1} M f with M = Mz (x) My (x) Mx diagonal (Eq. (fdmtr)), so
+    du = A^{-1} M df and the adjoint of that map sends lam = A^{-H} g to M^H lam, i.e.
+    conj(hhat^x_i hhat^y_j hhat^z_k) lam_ijk.  With g = dJ/du* in PyTorch's scaling
+    (g = P^T (P u - d) for J = 1/2 sum |P u - d|^2) the result gr satisfies
+    dJ/dRe f = Re gr and dJ/dIm f = Im gr.
+    """
+    mx, my, mz = dual_lengths(P.hx), dual_lengths(P.hy), dual_lengths(P.hz)
+    w = mz[:, None, None] * my[None, :, None] * mx[None, None, :]
+    return np.conj(w)[None] * lam
+
+
 def misfit(u, rec_flat, d_obs):
     """J = 1/2 sum_s sum_rec |u_s(rec) - d_s,rec|^2 and the adjoint source g_s = P^T (P u_s - d_s)."""
     R = u.shape[0]

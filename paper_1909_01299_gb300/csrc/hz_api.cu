@@ -1753,6 +1753,20 @@ hz_status hz_grad_layers(hz_plan_t p, const hz_c128* u, const hz_c128* lam, int 
   return HZ_OK;
 }
 
+hz_status hz_grad_rhs(hz_plan_t p, const hz_c128* lam, hz_c128* gf, int nrhs) {
+  if (!p || !lam || !gf || nrhs < 1) return HZ_ERR_ARG;
+  NvtxRange range("hz right-hand-side gradient");
+  try {
+    hz::grad_rhs(reinterpret_cast<const double2*>(lam), reinterpret_cast<double2*>(gf), p->dx.m, p->dy.m, p->mz,
+                 p->nx, p->ny, p->nz, nrhs, p->st);
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(p->st));
+  } catch (const Fail& e) {
+    return e.s;
+  }
+  return HZ_OK;
+}
+
 hz_status hz_residual(hz_plan_t p, const hz_c128* f, const hz_c128* u, int nrhs, double* rel_host) {
   if (!p || !f || !u || !rel_host || nrhs < 1) return HZ_ERR_ARG;
   try {

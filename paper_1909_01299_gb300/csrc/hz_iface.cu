@@ -246,6 +246,21 @@ __global__ void adjoint_prep_kernel(const double2* __restrict__ g, double2* __re
   out[t] = cmul(cmul(v, imx[i]), cmul(imy[j], imz[k]));
 }
 
+// Gradient in the right-hand side: out = conj(mx_i my_j mz_k) lam (out may alias lam).
+__global__ void grad_rhs_kernel(const double2* lam, double2* out, const double2* __restrict__ mx,
+                                const double2* __restrict__ my, const double2* __restrict__ mz, int nx, int ny,
+                                int nz, long long total) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int i = (int)(t % nx);
+  const long long q = t / nx;
+  const int j = (int)(q % ny);
+  const int k = (int)((q / ny) % nz);
+  double2 w = cmul(mx[i], cmul(my[j], mz[k]));
+  w.y = -w.y;
+  out[t] = cmul(w, lam[t]);
+}
+
 __global__ void conj_kernel(double2* __restrict__ u, long long n) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t < n) u[t].y = -u[t].y;
@@ -529,6 +544,14 @@ void adjoint_prep(const double2* g, double2* out, const double2* imx, const doub
   const long long n = (long long)nx * ny * nz * nrhs;
   if (n == 0) return;
   adjoint_prep_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g, out, imx, imy, imz, nx, ny, nz, n);
+  count_launch();
+}
+
+void grad_rhs(const double2* lam, double2* out, const double2* mx, const double2* my, const double2* mz,
+              int nx, int ny, int nz, int nrhs, cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz * nrhs;
+  if (n == 0) return;
+  grad_rhs_kernel<<<blocks_for(n, 256), 256, 0, st>>>(lam, out, mx, my, mz, nx, ny, nz, n);
   count_launch();
 }
 

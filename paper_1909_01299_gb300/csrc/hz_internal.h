@@ -276,6 +276,10 @@ void write_iface(const IfaceArgs& a, const double2* wX, const double2* wY, doubl
 void adjoint_prep(const double2* g, double2* out, const double2* imx, const double2* imy,
                   const double2* imz, int nx, int ny, int nz, int nrhs, cudaStream_t st);
 
+// Right-hand-side gradient: out = conj(mx_i my_j mz_k) lam (out may alias lam).
+void grad_rhs(const double2* lam, double2* out, const double2* mx, const double2* my, const double2* mz,
+              int nx, int ny, int nz, int nrhs, cudaStream_t st);
+
 // u = conj(u) elementwise.
 void conj_inplace(double2* u, long long n, cudaStream_t st);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "hz_grad_layers": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_solve_perturbed": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _P, _P]),
+    "hz_grad_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_residual_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "hz_get_info": (ctypes.c_int, [_P, ctypes.POINTER(hz_info)]),
@@ -292,6 +293,14 @@ class Plan:
         _check(_lib.hz_grad_layers(self._h, u.data_ptr(), lam.data_ptr(), R, G.ctypes.data), "hz_grad_layers")
         return G
 
+    def grad_rhs(self, lam, out=None):
+        """M^H lam: the gradient in f of a real objective whose adjoint state is lam (hz_grad_rhs)."""
+        import torch
+        R = self._check_tensor(lam)
+        gf = torch.empty_like(lam) if out is None else out
+        _check(_lib.hz_grad_rhs(self._h, lam.data_ptr(), gf.data_ptr(), R), "hz_grad_rhs")
+        return gf
+
     def residual(self, f, u) -> np.ndarray:
         R = self._check_tensor(f)
         out = np.empty(R, np.float64)
@@ -371,12 +380,6 @@ class Batch:
             pass
 
 
-def dual_weights(plan: Plan):
-    """hhat per axis (host numpy), for callers that weight data by M."""
-    h = lambda s: 0.5 * (s[:-1] + s[1:])
-    return h(plan.hx), h(plan.hy), h(plan.hz)
-
-
 class HzSolve:
     """torch.autograd.Function wrapper: u = A(k2)^{-1} M f, differentiable in k2 and f.
 
@@ -384,7 +387,7 @@ class HzSolve:
     on the CPU (it sets the plan's layer k^2) and f a CUDA tensor.  The backward
     pass runs one adjoint solve lam = A^{-H} grad_u and returns
     k2.grad = conj(G) (G from hz_grad_layers; PyTorch's convention for complex
-    leaves of real losses) and f.grad = conj(M) lam.
+    leaves of real losses) and f.grad = M^H lam (hz_grad_rhs).
     """
 
     @staticmethod
@@ -407,9 +410,7 @@ class HzSolve:
                 lam = plan.solve_adjoint(grad_u.contiguous())
                 G = plan.grad_layers(u, lam)
                 gk = torch.from_numpy(np.conj(G))
-                mx, my, mz = dual_weights(plan)
-                w = (np.conj(mz)[:, None, None] * np.conj(my)[None, :, None] * np.conj(mx)[None, None, :])
-                gf = lam * torch.from_numpy(w).to(lam.device)[None]
+                gf = plan.grad_rhs(lam)
                 return gk, gf, None
 
         return _F

@@ -305,3 +305,29 @@ def residual_perturbed_error(w, amp=0.15):
     ref = _loop_relres(Ad, vol, u, w.f)
     got = O.residual_perturbed(P, u, w.f, dk2)
     return np.max(np.abs(got - ref) / ref)
+
+
+def rhs_gradient_fd_error(w, entries=((0, 1, 2, 3), (0, 3, 1, 2), (1, 2, 4, 1)), eps=1e-6):
+    """Central differences of J(f) = 1/2 sum |P u(f) - d|^2 (u by sparse LU) in Re f and Im f
+    at a few entries against the oracle's right-hand-side gradient of the adjoint state."""
+    P = O.Problem.from_workload(w)
+    A, _ = O.assemble(P)
+    rng = np.random.default_rng(31)
+    rec = rng.choice(w.nx * w.ny * w.nz, 6, replace=False)
+    R = w.f.shape[0]
+    d = rng.standard_normal((R, 6)) * 1e-2 + 0j
+
+    def J(f):
+        return O.misfit(O.solve(P, f, A), rec, d)[0]
+
+    _, g = O.misfit(O.solve(P, w.f, A), rec, d)
+    gr = O.rhs_gradient(P, O.adjoint_solve(P, g, A, method="lu"))
+    err = 0.0
+    for (r, k, j, i) in entries:
+        e = np.zeros_like(w.f)
+        e[r, k, j, i] = eps
+        fd_re = (J(w.f + e) - J(w.f - e)) / (2 * eps)
+        fd_im = (J(w.f + 1j * e) - J(w.f - 1j * e)) / (2 * eps)
+        scale = abs(fd_re) + abs(fd_im)
+        err = max(err, abs(gr[r, k, j, i].real - fd_re) / scale, abs(gr[r, k, j, i].imag - fd_im) / scale)
+    return err

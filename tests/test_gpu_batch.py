@@ -5,6 +5,7 @@ import pytest
 
 from oracle import hz_oracle as O
 from paper_1909_01299_gb300 import workloads as W
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +51,7 @@ def test_batch_matches_oracle_and_single_solves(env):
         rel = batch.solve(fs, us)
         for (w, om, prec), u, ref, r in zip(items, us, refs, rel):
             tol = 1e-8 if prec == "mixed" else 1e-10
-            err = np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref)
+            err = rel(u.cpu().numpy(), ref)
             assert err < tol, (call, prec, err)
             assert r <= (1e-8 if prec == "mixed" else 1e-10)
     info = batch.info()
@@ -92,4 +93,43 @@ def test_plan_autotune_keeps_results(env, precision):
     assert precision == "mixed" or choice["tensor_cores"]
     u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
     tol = 1e-10 if precision == "fp64" else 1e-8
-    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < tol
+    assert rel(u, ref) < tol
+
+
+def test_batch48_subset_at_full_model_size(env):
+    """A seeded subset of the 48-model batched workload at full model sizes: the first model
+    of each size (64^3, 96^3, 128^3, 160^3), all four frequencies and each model's own RHS
+    count, as one batch of 16 items.  Every item is refined to 1e-10 so that the element-wise
+    comparison at the mixed-path tolerance is not limited by the conditioning of the
+    higher frequencies.  Per item: one RHS element by element against the oracle's block
+    solver, every RHS by the oracle's residual."""
+    torch, hz = env
+    items = W.batched_models(48)
+    pick = [next(i for i, (w, _) in enumerate(items) if w.nx == n) for n in (64, 96, 128, 160)]
+    plans, fs, us, meta = [], [], [], []
+    for mi in pick:
+        w, omegas = items[mi]
+        f = torch.from_numpy(w.f).cuda()
+        for om in omegas:
+            p = hz.Plan.from_workload(w, precision="mixed", rtol=1e-10, max_refine=12)
+            p.set_frequency(float(om))
+            plans.append(p)
+            fs.append(f)
+            us.append(torch.empty_like(f))
+            meta.append((mi, float(om)))
+    batch = hz.Batch(plans, [f.shape[0] for f in fs])
+    relres = batch.solve(fs, us)
+    assert np.all(relres <= 1e-10), relres
+    for q, ((mi, om), u) in enumerate(zip(meta, us)):
+        w = items[mi][0]
+        P = O.Problem.from_workload(w, k2=w.k2 * om * om)
+        A, _ = O.assemble(P)
+        uh = u.cpu().numpy()
+        res = O.residual(P, uh, w.f, A)
+        assert np.all(res <= 1e-10), (mi, om, res)
+        r = q % w.nrhs                                   # a different RHS from item to item
+        ref = O.block_solve(P, w.f[r:r + 1], A)
+        assert rel(uh[r:r + 1], ref) < 1e-8, (mi, om, r)
+    batch.close()
+    for p in plans:
+        p.close()

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import hz_oracle as O
 from paper_1909_01299_gb300 import workloads as W
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -31,10 +32,6 @@ def torch_cuda():
 def hz(torch_cuda):
     from paper_1909_01299_gb300 import hz as mod
     return mod
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def solve_and_check(hz, torch, w, precision):

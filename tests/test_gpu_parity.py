@@ -9,6 +9,7 @@ import pytest
 
 from oracle import hz_oracle as O
 from paper_1909_01299_gb300 import workloads as W
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +31,6 @@ def torch_cuda():
 def hz(torch_cuda):
     from paper_1909_01299_gb300 import hz as mod
     return mod
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def gpu_solve(hz, torch, w, precision="fp64", f=None, **kw):
@@ -235,6 +232,44 @@ def test_autograd_wrapper_against_finite_differences(hz, torch_cuda):
         g = k2.grad[Lyr].item()
         assert abs(g.real - fd_re) <= 1e-6 * max(abs(fd_re), 1e-12) + 1e-12
         assert abs(g.imag - fd_im) <= 1e-6 * max(abs(fd_im), 1e-12) + 1e-12
+
+
+def test_autograd_rhs_gradient(hz, torch_cuda):
+    # f.grad = M^H lam from hz_grad_rhs: against the oracle's right-hand-side gradient of its
+    # adjoint state and against central differences in Re f and Im f (PML grid: complex M)
+    torch = torch_cuda
+    w = W.tiny_pml(20, 18, 12, 2, 2, rim=3, pml=2, nrhs=2)
+    plan = hz.Plan.from_workload(w)
+    rng = np.random.default_rng(5)
+    rec_np = rng.choice(w.nx * w.ny * w.nz, 8, replace=False)
+    d_np = rng.standard_normal((2, 8)) * 1e-2 + 0j
+    rec = torch.from_numpy(rec_np).cuda()
+    d = torch.from_numpy(d_np).cuda()
+    k2 = torch.tensor(w.k2, dtype=torch.complex128)
+
+    def loss(f):
+        u = hz.HzSolve.apply(k2, f, plan)
+        return 0.5 * (u.reshape(2, -1)[:, rec] - d).abs().pow(2).sum()
+
+    f = torch.from_numpy(w.f).cuda().requires_grad_()
+    loss(f).backward()
+    gf = f.grad.cpu().numpy()
+    P = O.Problem.from_workload(w)
+    A, _ = O.assemble(P)
+    _, g = O.misfit(O.solve(P, w.f, A), rec_np, d_np)
+    ref = O.rhs_gradient(P, O.adjoint_solve(P, g, A, method="lu"))
+    assert rel(gf, ref) < TOL64
+    eps = 1e-6
+    f0 = torch.from_numpy(w.f).cuda()
+    for (r, k, j, i) in ((0, 3, 4, 5), (1, 6, 9, 10), (0, 11, 17, 19)):
+        e = torch.zeros_like(f0)
+        e[r, k, j, i] = eps
+        with torch.no_grad():
+            fd_re = (loss(f0 + e) - loss(f0 - e)).item() / (2 * eps)
+            fd_im = (loss(f0 + 1j * e) - loss(f0 - 1j * e)).item() / (2 * eps)
+        scale = abs(fd_re) + abs(fd_im)
+        assert abs(gf[r, k, j, i].real - fd_re) <= 1e-6 * scale
+        assert abs(gf[r, k, j, i].imag - fd_im) <= 1e-6 * scale
 
 
 def test_singular_mode_is_reported(hz, torch_cuda):

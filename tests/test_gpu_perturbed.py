@@ -5,6 +5,7 @@ import pytest
 
 from oracle import hz_oracle as O
 from paper_1909_01299_gb300 import workloads as W
+from tests.parity import rel
 from tests import oracle_pins as pins
 
 pytestmark = pytest.mark.gpu
@@ -19,10 +20,6 @@ def env():
     build.build()
     from paper_1909_01299_gb300 import hz
     return torch, hz
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-12, 1e-10), ("mixed", 1e-10, 1e-8)])

@@ -13,7 +13,7 @@ from tests import oracle_pins as pins
 _orig = {name: getattr(O, name) for name in
          ["stiffness", "dual_lengths", "fwd", "inv", "z_coefficients", "mode_solve", "apply_A",
           "gen_eig", "sigma_half", "weighted_rhs", "adjoint_solve", "layer_gradient", "axis_blocks",
-          "residual", "residual_perturbed"]}
+          "residual", "residual_perturbed", "rhs_gradient"]}
 
 
 def _any_pin_fails():
@@ -29,6 +29,7 @@ def _any_pin_fails():
         (lambda: pins.adjoint_error(W.tiny_pml(9, 8, 7, 2, 2)), 1e-12),
         (lambda: pins.residual_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1)), 1e-12),
         (lambda: pins.residual_perturbed_error(W.tiny_pml(6, 5, 4, 2, 2, rim=1, pml=1, nrhs=2)), 1e-11),
+        (lambda: pins.rhs_gradient_fd_error(W.tiny_pml(9, 8, 6, 2, 2, rim=3, pml=2, nrhs=2)), 1e-6),
     ]
     for fn, bound in checks:
         try:
@@ -155,7 +156,17 @@ def _mut_residual_perturbed_dk2_unweighted(P, u, f, dk2, A=None):
     return np.linalg.norm(r.reshape(R, -1), axis=1) / np.linalg.norm(b.reshape(R, -1), axis=1)
 
 
+def _mut_rhs_gradient_no_conj(P, lam):
+    return np.conj(_orig["rhs_gradient"](P, np.conj(lam)))         # M lam instead of M^H lam
+
+
+def _mut_rhs_gradient_no_weight(P, lam):
+    return lam.copy()                                                # M dropped
+
+
 MUTATIONS = {
+    "rhs_gradient_without_conjugate": ("rhs_gradient", _mut_rhs_gradient_no_conj),
+    "rhs_gradient_without_M": ("rhs_gradient", _mut_rhs_gradient_no_weight),
     "residual_without_M": ("residual", _mut_residual_without_M),
     "residual_f_denominator": ("residual", _mut_residual_f_denominator),
     "residual_pooled_over_rhs": ("residual", _mut_residual_pooled),

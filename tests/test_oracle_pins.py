@@ -192,3 +192,8 @@ def test_perturbed_solve_zero_perturbation():
     u1 = O.solve_perturbed(P, w.f, np.zeros(P.shape, dtype=np.complex128))
     assert np.linalg.norm(u1 - u0) <= 1e-14 * np.linalg.norm(u0)
     assert np.all(O.residual_perturbed(P, u1, w.f, np.zeros(P.shape)) < 1e-12)
+
+
+def test_rhs_gradient_against_central_differences():
+    # complex (PML) steps make M complex, so a missing conjugate or a missing M is visible
+    assert pins.rhs_gradient_fd_error(W.tiny_pml(9, 8, 6, 2, 2, rim=3, pml=2, nrhs=2)) < 1e-6
