@@ -1,20 +1,21 @@
 #!/usr/bin/env python
 """Throughput of the GB300 layered-medium Helmholtz solver: solved unknowns/s.
 
-One step = one hz_solve of the two-block PML workload (160 x 160 x 128
-interior nodes, PML rim in x/y, ramped z, 12 layers, 2 x 2 blocks, 4 point
-sources, complex128): steps 1-7 of the block method of Sec. 2 with the
-interface correction, every RHS to relative residual <= 1e-8.  The FP64 path is
-the headline `value`; the mixed path (FP32 transforms, FP64 z solves,
-interface solves and refinement) is measured on the same workload and reported
-beside it.
+One step = one hz_solve of the 320 x 320 x 200 workload (h = 1 on every axis, 4
+layers of 50 planes, 4 x 4 blocks, 8 Gaussian sources, complex128): steps 1-7 of
+the block method of Sec. 2 with the interface correction, every RHS to relative
+residual <= 1e-8.  The FP64 path is the headline `value`; the mixed path (FP32
+transforms on the tensor cores, FP64 z solves, interface solves and refinement) is
+measured on the same workload and reported beside it, and so is the two-block PML
+workload (160 x 160 x 128, 4 point sources).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hz|reference]
 
 N > 1 (torchrun): every rank solves its own copy of the workload (replicas,
 weak scaling, no collective on the data path); value = all ranks' unknowns /
 the slowest rank's time.  `--impl reference` times the CPU FP64 oracle (the
-plain block algorithm in numpy/scipy) on a bounded sample of the workload.
+plain block algorithm in numpy/scipy) on a bounded sample of the workload (one
+of its 8 right-hand sides per step).
 """
 from __future__ import annotations
 
@@ -31,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "solved unknowns/s at rel. residual <=1e-8 (FP64 path; mixed path beside it)"
+METRIC = "solved unknowns/s at rel. residual <=1e-8, mixed vs FP64 path on 1 GB300 (FP64 path as value; mixed beside it)"
 UNIT = "unknowns/s"
 RTOL = 1e-8
 FP64_FLOPS_PER_CLK_SM = 4          # 2 DFMA per SM per clock (1.25 TFLOP/s nominal at 2070 MHz)
@@ -48,9 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="right-hand sides of an extra workload (default: the workload's own count)")
-    ap.add_argument("--workload", default="pml160",
-                    choices=["pml160", "uniform320", "adjoint192", "uniform32", "batch48", "scaling", "perturbed160"],
-                    help="pml160 is the benchmark workload; the others are extra measurements")
+    ap.add_argument("--workload", default="uniform320",
+                    choices=["uniform320", "pml160", "adjoint192", "uniform32", "batch48", "scaling", "perturbed160"],
+                    help="uniform320 is the benchmark line; the others are extra measurements")
     return ap.parse_args()
 
 
@@ -245,33 +246,59 @@ def oracle_single_thread(workload: str, timeout_s: float = 90.0):
         return None
 
 
-def run_reference(args):
+def bench_workload():
+    """The benchmark workload: 320 x 320 x 200, h = 1, 4 layers, 4 x 4 blocks, 8 Gaussian sources
+    (the largest single-GPU configuration)."""
+    from paper_1909_01299_gb300 import workloads as W
+    return W.uniform_320x320x200()
+
+
+def one_rhs(w, r: int = 0):
+    """The same workload restricted to its RHS r (the oracle's bounded sample)."""
+    import dataclasses
+    return dataclasses.replace(w, f=w.f[r:r + 1].copy())
+
+
+def run_reference(args, wall_limit_s: float = 420.0):
+    """The CPU oracle's block solver on 1 of the 8 RHS of the benchmark workload per step.
+
+    Each step is one full 7-step solve of one RHS (about 10 s on 16 Grace cores).  A wall-clock
+    guard stops the timed loop early if the machine is much slower than that; the line then
+    reports the steps actually timed."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import numpy as np
     from oracle import hz_oracle as O
-    from paper_1909_01299_gb300 import workloads as W
-    w = W.pml_160x160x128(nrhs=1)
+    w = one_rhs(bench_workload())
     P = O.Problem.from_workload(w)
     A, _ = O.assemble(P)
+    t_all = time.perf_counter()
     for _ in range(args.warmup):
         O.block_solve(P, w.f, A)
+    done = 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    u = None
+    while done < args.steps:
         u = O.block_solve(P, w.f, A)
-    dt = (time.perf_counter() - t0) / args.steps
+        done += 1
+        if time.perf_counter() - t_all > wall_limit_s:
+            break
+    dt = (time.perf_counter() - t0) / done
     res = float(np.max(O.residual(P, u, w.f, A)))
     value = w.unknowns / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "steps": done, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
             "data": "synthetic",
-            "config": {"workload": "pml-160x160x128-2x2blocks-fp64 (1 of 4 RHS per step)",
-                       "nx": 160, "ny": 160, "nz": 128, "blocks": "2x2", "nrhs": 1},
+            "config": {"workload": w.name + " (1 of 8 RHS per step)", "nx": w.nx, "ny": w.ny, "nz": w.nz,
+                       "blocks": "4x4", "nrhs": 1},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"1 RHS per step, residual {res:.1e}"},
+                             "sample": f"RHS 0 of 8 per step through the full 7-step block algorithm, "
+                                       f"residual {res:.1e}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if done < args.steps:
+        line["steps_note"] = f"wall-clock guard: {done} of {args.steps} steps timed"
     print(json.dumps(line), flush=True)
 
 
@@ -304,8 +331,101 @@ def time_path(torch, hz, plan, f, u, steps, warmup, dist, world, device):
     return ms, launches, stages, clk.summary()
 
 
-def run_hz(args):
+def launch_ms(st):
+    """Average CUDA-event time of one bulk transform launch (steps 1 and 7) from the stage timers."""
+    return (st["fwd"][0] + st["inv"][0]) / max(1, st["fwd"][1] + st["inv"][1])
+
+
+def real_tables(w):
+    """True when every block of both axes has real eigenvectors (all block steps real)."""
     import numpy as np
+    return bool(np.all(np.imag(w.hx) == 0) and np.all(np.imag(w.hy) == 0))
+
+
+def fp64_roofline(w, R, st, traffic_workload=None):
+    """Roofline of the FP64 bulk transform (the FP64 path's dominant kernel), bound by the FP64 pipe.
+
+    Algorithmic flops: the dense product of a block of width n, per transformed complex value
+    4 n real flops for a real table (2 FMA per multiply-add) and 8 n for a complex one; four
+    launches per solve.  Uniform blocks are folded (the kernel issues half the multiply-adds of
+    the dense product), which is why the fraction can exceed 1 on this count.
+    """
+    macs = bulk_macs(w, R)
+    per_mac = 4 if real_tables(w) else 8
+    flops = sum(macs) / 4 * per_mac
+    t = launch_ms(st)
+    achieved = flops / (t * 1e-3) / 1e12
+    peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
+    total_ms = sum(v[0] for v in st.values())
+    return {"bound": "alu", "kernel": "xform_kernel<double> (FP64 bulk x/y transforms)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flop_count": (f"dense product: {per_mac} n real flops per complex value "
+                           f"({'real' if per_mac == 4 else 'complex'} tables, n = block width)"),
+            "peak_note": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s); "
+                         "probe measured 1.197 TFLOP/s at ~1.97 GHz",
+            "flops_per_launch": flops, "launch_ms": t,
+            "traffic": profiled_traffic("xform_kernel<double>", traffic_workload or w.name),
+            "share_of_step": (st["fwd"][0] + st["inv"][0]) / max(total_ms, 1e-9)}
+
+
+def tc_roofline(w, R, st, refinements):
+    """Roofline of the tensor-core bulk transform (the mixed path's transform), HBM-bound.
+
+    Algorithmic bytes per transformed value: forward x reads complex128 f and writes complex64
+    (24 B), forward y and inverse y complex64 both ways (16 B), inverse x reads complex64 and
+    writes complex128 u (24 B), or also reads u when it accumulates a correction (40 B);
+    averaged over the 4 (1 + refinements) launches of a step.  The same launches against the
+    tensor pipe: 3 TF32 products (3xTF32) of 8 real flops per complex multiply-add.
+    """
+    hbm_peak, hbm_src = measured_peaks()
+    t = launch_ms(st)
+    b = tc_bytes_per_launch(w, R, refinements)
+    out = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
+           "achieved": b / (t * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": b / (t * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
+           "bytes_per_launch": b, "launch_ms": t,
+           "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
+    tc_flops = sum(bulk_macs(w, R)) / 4 * 8 * 3
+    tpk, tsrc = tf32_peak()
+    out["tensor"] = {"achieved": tc_flops / (t * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                     "frac": tc_flops / (t * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
+                     "flops_per_launch": tc_flops}
+    return out
+
+
+def measure_both(torch, hz, w, args, dist, world, device):
+    """FP64 and mixed paths on one workload: times, stages, residuals, rooflines."""
+    import numpy as np
+    R = w.nrhs
+    f = torch.from_numpy(w.f).to(device)
+    u = torch.empty_like(f)
+    plan = hz.Plan.from_workload(w, precision="fp64")
+    plan_ms = plan.info()["plan_ms"]
+    ms64, l64, st64, clk64 = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist, world, device)
+    res64 = float(np.max(plan.residual(f, u)))
+    plan.set_options(precision="mixed", rtol=RTOL, max_refine=10)
+    msmx, lmx, stmx, clkmx = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist, world, device)
+    infomx = plan.info()
+    resmx = float(np.max(plan.residual(f, u)))
+    plan.set_options(precision="fp64")
+    unknowns = w.unknowns * R
+    out = {
+        "fp64": {"value": job_throughput(unknowns, world, ms64 * 1e-3), "ms_per_step": ms64,
+                 "rel_residual_max": res64, "gpu_launches": l64, "roofline": fp64_roofline(w, R, st64),
+                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in st64.items() if v[1]},
+                 "clocks": clk64},
+        "mixed": {"value": job_throughput(unknowns, world, msmx * 1e-3), "ms_per_step": msmx,
+                  "roofline": tc_roofline(w, R, stmx, int(infomx.get("refinements", 0))),
+                  "speedup_vs_fp64": ms64 / msmx, "refinements": infomx["refinements"],
+                  "rel_residual_max": resmx, "gpu_launches": lmx, "dtype": "c64 transforms + f64",
+                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in stmx.items() if v[1]},
+                  "clocks": clkmx},
+        "plan_ms": plan_ms,
+    }
+    return plan, f, u, out
+
+
+def run_hz(args):
     import torch
     rank, world, local = dist_env()
     dist = None
@@ -320,24 +440,10 @@ def run_hz(args):
     B.build()
     from paper_1909_01299_gb300 import hz, workloads as W
 
-    w = W.pml_160x160x128()
+    w = bench_workload()
     R = w.nrhs
-    f = torch.from_numpy(w.f).to(device)
-    u = torch.empty_like(f)
-    plan = hz.Plan.from_workload(w, precision="fp64")
-    plan_ms = plan.info()["plan_ms"]
-
-    # FP64 path (headline)
-    ms64, launches64, st64, clk64 = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist, world,
-                                              device)
-    res64 = float(np.max(plan.residual(f, u)))
-    # mixed path on the same workload
-    plan.set_options(precision="mixed", rtol=RTOL, max_refine=10)
-    msmx, launchesmx, stmx, clkmx = time_path(torch, hz, plan, f, u, args.steps, args.warmup, dist,
-                                              world, device)
-    infomx = plan.info()
-    resmx = float(np.max(plan.residual(f, u)))
-    plan.set_options(precision="fp64")
+    plan, f, u, m = measure_both(torch, hz, w, args, dist, world, device)
+    del f, u
 
     # end to end through the host-buffer entry point (H2D of f and D2H of u inside the call)
     fh = torch.from_numpy(w.f).pin_memory()
@@ -351,76 +457,48 @@ def run_hz(args):
     for _ in range(e2e_steps):
         plan.solve_host(fh, out=uh)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
+    plan.close()
+    del fh, uh
+
+    # the two-block PML workload (160 x 160 x 128, 4 point sources) beside it
+    w2 = W.pml_160x160x128()
+    p2, f2, u2, m2 = measure_both(torch, hz, w2, args, dist, world, device)
+    p2.close()
+    del f2, u2
 
     unknowns = w.unknowns * R
-    value = job_throughput(unknowns, world, ms64 * 1e-3)
-    # roofline of the dominant kernel: the FP64 bulk transform (4 launches per solve)
-    macs = bulk_macs(w, R)
-    complex_w = True
-    flops_per_launch = sum(macs) / 4 * (6 if complex_w else 4)
-    t_launch = (st64["fwd"][0] + st64["inv"][0]) / max(1, st64["fwd"][1] + st64["inv"][1])
-    achieved = flops_per_launch / (t_launch * 1e-3) / 1e12
-    peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
-    total_ms = sum(v[0] for v in st64.values())
-    # mixed path: the tensor-core bulk transform (HBM-bound: it reads and writes one volume).
-    # Algorithmic bytes per transformed value: forward x reads complex128 f and writes
-    # complex64 (24 B), forward y and inverse y complex64 both ways (16 B), inverse x reads
-    # complex64 and writes complex128 u (24 B), or also reads u when it accumulates a
-    # correction (40 B); averaged over the 4 (1 + refinements) launches of a step.
-    hbm_peak, hbm_src = measured_peaks()
-    tc_launch_ms = (stmx["fwd"][0] + stmx["inv"][0]) / max(1, stmx["fwd"][1] + stmx["inv"][1])
-    tc_bytes = tc_bytes_per_launch(w, R, int(infomx.get("refinements", 0)))
-    roof_tc = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
-               "achieved": tc_bytes / (tc_launch_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-               "frac": tc_bytes / (tc_launch_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
-               "bytes_per_launch": tc_bytes, "launch_ms": tc_launch_ms,
-               "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
-    # the same launches against the tensor pipe: 3 TF32 products (3xTF32) of 8 real flops per
-    # complex multiply-add of the block transforms
-    tc_flops = sum(macs) / 4 * 8 * 3
-    tpk, tsrc = tf32_peak()
-    roof_tc["tensor"] = {"achieved": tc_flops / (tc_launch_ms * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
-                         "frac": tc_flops / (tc_launch_ms * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
-                         "flops_per_launch": tc_flops}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu, _, _ = oracle_sample()
+        cpu, _, _ = oracle_sample(budget_s=8.0, max_runs=2, w=one_rhs(w), of=str(R))
         one = oracle_single_thread("pml160")
         if one:
-            cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+            cpu["single_thread_pml160"] = {"value": one["value"], "sample": one["sample"]}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "blocks": "2x2", "nrhs": R,
-                   "grid": "uniform core 128 + 16-node geometric rim (ratio 1.3, outer 8 complex) in x/y; "
-                           "z ramp 0.5..2.0; 12 layers",
+        "metric": METRIC, "value": m["fp64"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["fp64"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "blocks": "4x4", "nrhs": R,
+                   "grid": "uniform h = 1 on every axis (uniform blocks: sine eigenvectors); 4 layers of "
+                           "50 planes; 8 Gaussian sources (sigma 2 nodes)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "working set ~0.4 GB (f, u, 3 volume buffers, factors) > 129 MB L2; no flush",
-                   "rel_residual_max": res64, "plan_ms": plan_ms},
-        "gpu_launches": launches64,
-        "roofline": {"bound": "alu", "kernel": "xform_kernel<double> (FP64 bulk x/y transforms)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_note": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s); "
-                                  "probe measured 1.197 TFLOP/s at ~1.97 GHz",
-                     "flops_per_launch": flops_per_launch, "launch_ms": t_launch,
-                     "traffic": profiled_traffic("xform_kernel<double>", w.name),
-                     "share_of_step": (st64["fwd"][0] + st64["inv"][0]) / max(total_ms, 1e-9)},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in st64.items() if v[1]},
-        "mixed": {"value": job_throughput(unknowns, world, msmx * 1e-3), "ms_per_step": msmx,
-                  "roofline": roof_tc,
-                  "speedup_vs_fp64": ms64 / msmx, "refinements": infomx["refinements"],
-                  "rel_residual_max": resmx, "gpu_launches": launchesmx, "dtype": "c64 transforms + f64",
-                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in stmx.items() if v[1]},
-                  "clocks": clkmx},
-        "e2e": {"value": world * unknowns / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(fh.numel() * 16),
-                "d2h_bytes_per_step": int(uh.numel() * 16), "ms_per_step": e2e_s * 1e3,
-                "entry_point": "hz_solve_host (pinned host buffers)"},
-        "clocks": clk64,
+                   "l2": "working set ~8 GB (f, u, 3 volume buffers, factors) > 129 MB L2; no flush",
+                   "rel_residual_max": m["fp64"]["rel_residual_max"], "plan_ms": m["plan_ms"]},
+        "gpu_launches": m["fp64"]["gpu_launches"],
+        "roofline": m["fp64"]["roofline"],
+        "stages_ms_per_step": m["fp64"]["stages_ms_per_step"],
+        "mixed": m["mixed"],
+        "e2e": {"value": world * unknowns / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w.f.size * 16),
+                "d2h_bytes_per_step": int(w.f.size * 16), "ms_per_step": e2e_s * 1e3,
+                "entry_point": "hz_solve_host (pinned host buffers, FP64 path)"},
+        "clocks": m["fp64"]["clocks"],
+        "pml160": {"workload": w2.name, "fp64": {k: m2["fp64"][k] for k in ("value", "ms_per_step",
+                                                                         "rel_residual_max", "roofline")},
+                   "mixed": {k: m2["mixed"][k] for k in ("value", "ms_per_step", "rel_residual_max",
+                                                         "refinements", "speedup_vs_fp64", "roofline")}},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -582,7 +660,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload != "pml160":
+    elif args.workload != "uniform320":
         run_extra(args)
     else:
         run_hz(args)

@@ -172,7 +172,7 @@ def uniform_320x320x200(nrhs: int = 8) -> Workload:
     f = np.empty((nrhs, nz, ny, nx), dtype=np.complex128)
     for r in range(nrhs):
         f[r] = gaussian_source(nz, ny, nx, cen[r])
-    return Workload("uniform-320x320x200-4x4blocks-8rhs-mixed", uniform_steps(nx), uniform_steps(ny),
+    return Workload("uniform-320x320x200-4x4blocks-8rhs", uniform_steps(nx), uniform_steps(ny),
                     uniform_steps(nz), z_begin, k2, default_ifaces(nx, 4), default_ifaces(ny, 4), f,
                     precision="mixed", extra={"centres_zyx": cen})
 

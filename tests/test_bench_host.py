@@ -55,3 +55,23 @@ def test_traffic_records_are_dropped_for_changed_sources(tmp_path, monkeypatch):
     rec["xform_tc_kernel"]["source_sha"] = bench.kernel_source_hash("hz_xform_tc.cu")
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     assert bench.profiled_traffic("xform_tc_kernel", w_name, "hz_xform_tc.cu") == 1
+
+
+def test_benchmark_workload_counts():
+    # 320 x 320 x 200, interfaces at 79, 159, 239: blocks of 79, 79, 79 and 80 nodes, 8 RHS,
+    # real (uniform) tables: 4 n real flops per complex value in the dense product
+    import bench
+    w = bench.bench_workload()
+    assert (w.nx, w.ny, w.nz, w.nrhs) == (320, 320, 200, 8)
+    per_launch = 8 * 200 * 317 * (3 * 79 * 79 + 80 * 80)
+    assert bench.bulk_macs(w, 8) == [per_launch] * 4
+    assert bench.real_tables(w)
+    st = {k: (0.0, 0) for k in ("fwd", "pass_a", "edges", "iface_residual", "global", "pass_b", "inv",
+                                "iface_out", "residual")}
+    st["fwd"] = (2.0, 2)
+    st["inv"] = (2.0, 2)
+    roof = bench.fp64_roofline(w, 8, st)
+    assert roof["flops_per_launch"] == per_launch * 4
+    assert abs(roof["achieved"] - per_launch * 4 / 1e-3 / 1e12) < 1e-9
+    one = bench.one_rhs(w, 3)
+    assert one.nrhs == 1 and (one.f[0] == w.f[3]).all()
