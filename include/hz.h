@@ -122,6 +122,8 @@ typedef struct {
   int tensor_cores;          /* 1: the mixed path's bulk transforms run on the tensor
                                 cores (tcgen05, 3xTF32) with complex64 mode-space data;
                                 0: FP32 CUDA-core transforms on complex128 data          */
+  int fast_sine;             /* FP64 path: 1 when uniform blocks use the FFT-based sine
+                                transform (hz_plan_set_fast_sine), 0 otherwise           */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's
@@ -166,10 +168,27 @@ hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
 
 /* Autotuner: times one solve of nrhs right-hand sides (on zero data, in the plan's
  * workspace) for each kernel variant the plan can use -- one or two right-hand sides per
- * thread in the z sweeps ("pencil batch"), and for mixed plans tensor-core or CUDA-core
- * FP32 bulk transforms -- and keeps the fastest.  *choice_out (may be NULL) receives
- * rhs_per_thread + 10 * tensor_cores. */
+ * thread in the z sweeps ("pencil batch"), for mixed plans tensor-core or CUDA-core FP32
+ * bulk transforms, for FP64 plans with uniform blocks the fast sine transform or the
+ * folded dense product -- and keeps the fastest.  *choice_out (may be NULL) receives
+ * rhs_per_thread + 10 * tensor_cores + 100 * fast_sine. */
 hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
+
+/* FP64 path: transform the uniform blocks (all steps equal and real, so that the block's
+ * eigenvectors are the discrete sines and its tables a scaled DST-I) by the FFT-based sine
+ * transform, the fast transform of the uniform core in the cost estimate of Sec. 2
+ * (enable = 1, the default: one complex FFT of length n + 1 per row, for blocks whose
+ * n + 1 <= 128 has no prime factor above 5), or by the folded dense product (enable = 0).
+ * Both give the FP64 result; the autotuner times both. */
+hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
+
+/* Host-only helper (no device memory is touched): the fast sine transform that the plan
+ * runs on the GPU, applied to one row: out[c] = scale sum_j in[g(j)] sin(pi j m / (n + 1)).
+ * dir = 1 (forward table of a uniform block): in holds the nodes j = 1..n in order and
+ * out the modes m in the symmetric-modes-first order (column c < (n + 1) / 2 is m = 2 c + 1,
+ * then the even m); dir = 2 (inverse table): in holds the modes in that order and out the
+ * nodes in order.  HZ_ERR_ARG if n + 1 > 128 or has a prime factor above 5, or n < 2. */
+hz_status hz_sine_transform_host(int n, int dir, double scale, const hz_c128 *in, hz_c128 *out);
 
 /* Change the options' stream, precision, rtol and max_refine of a plan. */
 hz_status hz_plan_set_options(hz_plan_t plan, const hz_options *opts);

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhz.so")
 SOURCES = ["hz_api.cu", "hz_xform.cu", "hz_xform_tc.cu", "hz_zsolve.cu", "hz_iface.cu", "hz_noalloc.cu",
-           "hz_pert.cu", "hz_eig.cpp"]
+           "hz_pert.cu", "hz_dst.cu", "hz_eig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

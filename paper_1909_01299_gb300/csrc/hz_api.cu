@@ -92,6 +92,8 @@ struct hz_plan_s {
   bool need_global = false;
   bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
   bool tc_ok = true;                 // the tensor-core tables have their TMA tensor maps
+  bool fast_sine = true;             // FP64 path: uniform blocks through the FFT-based sine transform
+  bool has_dst = false;              // some block has a fast sine transform
   int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
@@ -401,6 +403,46 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
   xs.d_tiles = upload(p, tiles);
   xs.d_tab = upload(p, t64);
   xs.d_tab32 = upload(p, t32);
+  // FP64 fast sine transforms of the uniform blocks: the table must be S sin(pi j m / N)
+  // (rows j = nodes, columns m = modes in the symmetric-first order, or the transpose)
+  std::vector<hz::DstBlock> dblk;
+  std::vector<int> didx;
+  std::vector<double> dcoef;
+  std::vector<double2> dtw;
+  std::vector<char> fast(xs.nblocks, 0);
+  const double pi = 3.14159265358979323846;
+  for (int b = 0; b < xs.nblocks; ++b) {
+    const hz::XBlock& xb = blocks[b];
+    if (!xb.sym) continue;
+    const int n = xb.size, N = n + 1, ns = (n + 1) / 2;
+    auto mode = [&](int c) { return c < ns ? 2 * c + 1 : 2 * (c - ns) + 2; };
+    const double S = get(b, 0, 0).real() / std::sin(pi / N);
+    double dev = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) {
+        const long long jm = (dir == 1) ? (long long)(a + 1) * mode(c) : (long long)mode(a) * (c + 1);
+        const double ref = S * std::sin((double)(jm % (2 * N)) * pi / N);
+        dev = std::max(dev, std::abs(get(b, a, c) - cd(ref)));
+      }
+    if (!(dev <= 1e-13 * std::abs(S))) continue;
+    if (hz::dst_plan_block(n, xb.start, dir, S, dblk, didx, dcoef, dtw)) {
+      fast[b] = 1;
+      xs.dst.nmax = std::max(xs.dst.nmax, N);
+    }
+  }
+  std::vector<hz::XTile> tiles64;
+  for (const auto& t : tiles)
+    if (!fast[t.blk]) tiles64.push_back(t);
+  xs.ntiles64 = (int)tiles64.size();
+  xs.d_tiles64 = upload(p, tiles64);
+  xs.dst.nblk = (int)dblk.size();
+  if (xs.dst.nblk) {
+    xs.dst.d_blk = upload(p, dblk);
+    xs.dst.d_idx = upload(p, didx);
+    xs.dst.d_coef = upload(p, dcoef);
+    xs.dst.d_tw = upload(p, dtw);
+    p->has_dst = true;
+  }
 }
 
 // Tensor-core tables of a block-diagonal transform: tab(b)[a][c] = get(b, a, c).
@@ -751,7 +793,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
         throw Fail{HZ_ERR_ARG};
     } else if (!lo) {
       hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
-                    store_mode, conj, skip, st);
+                    store_mode, conj, skip, st, p->fast_sine);
     } else {
       hz::xform_f32(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
                     store_mode, conj, skip, st);
@@ -765,7 +807,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   // refinement residual stay FP64.
   auto rowx = [&](const hz::XformSet& xs, const double2* in, double2* out, long long rows, cudaStream_t s) {
     if (lo) hz::xform_f32(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
-    else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
+    else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s, p->fast_sine);
   };
   // contractions of the current z-sweep result (complex64 in V32, or complex128 in V)
   auto crows = [&](const AxisDev& d, double2* out, bool edge, int nslots, cudaStream_t s) {
@@ -1059,8 +1101,13 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   float best = 1e30f;
   int best_rb = p->zs_rb;
   bool best_tc = p->use_tc;
+  bool best_fs = p->fast_sine;
+  const int fs_lo = (!mixed && p->has_dst) ? 0 : (p->fast_sine ? 1 : 0);
+  const int fs_hi = (!mixed && p->has_dst) ? 1 : fs_lo;
+  for (int fs = fs_lo; fs <= fs_hi; ++fs)
   for (int rb = 1; rb <= 2; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
+      p->fast_sine = fs != 0;
       p->zs_rb = rb;
       p->use_tc = tc != 0;
       solve_core(p, w, st, f, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up
@@ -1070,14 +1117,15 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
       ck(cudaEventSynchronize(e1));
       float ms = 0.f;
       ck(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; }
+      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; best_fs = fs != 0; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->zs_rb = best_rb;
   p->use_tc = best_tc;
+  p->fast_sine = best_fs;
   p->timing = timing;
-  return best_rb + (best_tc ? 10 : 0);
+  return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0);
 }
 
 }  // namespace
@@ -1373,6 +1421,7 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   if (s != HZ_OK) { delete p; return s; }
   try {
     ck(cudaGetDevice(&p->device));
+    hz::dst_prepare(hz::kDstMaxN);
     ck(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
@@ -1436,6 +1485,19 @@ hz_status hz_tridiag_eig(int n, const hz_c128* kd, const hz_c128* ko, const hz_c
   for (int i = 0; i < n; ++i) lam[i] = hz_c128{l[i].real(), l[i].imag()};
   for (size_t i = 0; i < (size_t)n * n; ++i) W[i] = hz_c128{w[i].real(), w[i].imag()};
   if (residual) *residual = res;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_fast_sine(hz_plan_t p, int enable) {
+  if (!p) return HZ_ERR_ARG;
+  p->fast_sine = enable != 0;
+  return HZ_OK;
+}
+
+hz_status hz_sine_transform_host(int n, int dir, double scale, const hz_c128* in, hz_c128* out) {
+  if (n < 2 || !in || !out || (dir != 1 && dir != 2) || !std::isfinite(scale)) return HZ_ERR_ARG;
+  if (!hz::dst_apply_host(n, dir, scale, reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out)))
+    return HZ_ERR_ARG;
   return HZ_OK;
 }
 
@@ -1808,6 +1870,7 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   if (!p || !out) return HZ_ERR_ARG;
   p->info.device_bytes = p->bytes;
   p->info.tensor_cores = p->use_tc ? 1 : 0;
+  p->info.fast_sine = (p->fast_sine && p->has_dst) ? 1 : 0;
   *out = p->info;
   return HZ_OK;
 }

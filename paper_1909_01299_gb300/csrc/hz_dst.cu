@@ -1,0 +1,354 @@
+// Fast sine transforms of uniform blocks on the FP64 path (steps 1 and 7 of Sec. 2).
+//
+// A block whose steps are all equal to h has the discrete sine eigenvectors, so its
+// forward table (M W) and inverse table (W) are both a scaled DST-I,
+//     X_m = S sum_{j=1}^{n} x_j sin(pi j m / N),   N = n + 1,
+// which the paper's cost estimate for a uniform survey core (Sec. 2) computes with an FFT
+// instead of a dense product.  Here each row of a block is transformed through one complex
+// FFT of length N, valid for complex data because the transform has real coefficients:
+//   pre:   y_0 = 0,  y_j = p_j x_j + q_j x_{N-j}  (j = 1..N-1),
+//          p_j = (S/2)(sin(pi j / N) + 1/2),  q_j = (S/2)(sin(pi j / N) - 1/2);
+//   FFT:   Y_k = sum_j y_j exp(-2 pi i j k / N);
+//   post:  X_1 = Y_0,  X_{2k} = i (Y_k - Y_{N-k}),  X_{2k+1} = X_{2k-1} + Y_k + Y_{N-k}.
+// (The symmetric part of y picks out sin(pi j / N) (x_j + x_{N-j}), whose cosine sums give
+// X_{2k+1} - X_{2k-1}; the antisymmetric part gives the sine sums X_{2k}.)  With FP64 as
+// scarce as it is on this GPU (2 DFMA per SM per clock), the count that matters is FP64
+// instructions per transformed value: about 4 (pre) + 20-27 (FFT, N = 80 or 81) + 3 (post)
+// against n for the folded dense product.
+//
+// The FFT is the iterative mixed-radix decimation in time: the pre step writes y_j to its
+// digit-reversed position, and stage s (radix r, sub-transforms of length M = r_1 .. r_{s-1})
+// multiplies element q of each group by exp(-2 pi i q k / (M r)) and applies an r-point DFT.
+// The post step runs in place: X_{2k} goes to position k and X_{2k+1} to position N - k
+// (X_1 stays at 0), and the store gathers the columns from those positions.
+//
+// Kernel layout: one CTA takes TM rows of one block; the rows are staged in shared memory
+// (odd row stride in 16-byte units, so that the threads of a warp, one row each, hit
+// distinct banks); the load, the pre step and the store are shared by all threads with
+// consecutive columns (coalesced); each thread then runs the FFT and the post step of its
+// own row.
+#include <algorithm>
+#include <cmath>
+
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// a * w (4 FP64 operations)
+__host__ __device__ __forceinline__ double2 cmulw(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+
+// r-point DFTs (exp(-2 pi i q q' / r)) of a[0..r-1], in place.
+__host__ __device__ __forceinline__ void dft2(double2* a) {
+  const double2 t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+__host__ __device__ __forceinline__ void dft3(double2* a) {
+  const double c = 0.86602540378443864676;          // sin(2 pi / 3)
+  const double2 s = cadd(a[1], a[2]);
+  const double2 d = csub(a[1], a[2]);
+  const double2 m = make_double2(fma(-0.5, s.x, a[0].x), fma(-0.5, s.y, a[0].y));
+  a[0] = cadd(a[0], s);
+  // X1 = m - i c d, X2 = m + i c d
+  a[1] = make_double2(fma(c, d.y, m.x), fma(-c, d.x, m.y));
+  a[2] = make_double2(fma(-c, d.y, m.x), fma(c, d.x, m.y));
+}
+
+__host__ __device__ __forceinline__ void dft4(double2* a) {
+  const double2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  const double2 t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+  a[0] = cadd(t0, t2);
+  a[2] = csub(t0, t2);
+  a[1] = make_double2(t1.x + t3.y, t1.y - t3.x);       // t1 - i t3
+  a[3] = make_double2(t1.x - t3.y, t1.y + t3.x);       // t1 + i t3
+}
+
+__host__ __device__ __forceinline__ void dft5(double2* a) {
+  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2 pi / 5), cos(4 pi / 5)
+  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2 pi / 5), sin(4 pi / 5)
+  const double2 a1 = cadd(a[1], a[4]), a2 = cadd(a[2], a[3]);
+  const double2 b1 = csub(a[1], a[4]), b2 = csub(a[2], a[3]);
+  const double2 x0 = a[0];
+  const double2 m1 = make_double2(fma(c2, a2.x, fma(c1, a1.x, x0.x)), fma(c2, a2.y, fma(c1, a1.y, x0.y)));
+  const double2 m2 = make_double2(fma(c1, a2.x, fma(c2, a1.x, x0.x)), fma(c1, a2.y, fma(c2, a1.y, x0.y)));
+  const double2 n1 = make_double2(fma(s2, b2.x, s1 * b1.x), fma(s2, b2.y, s1 * b1.y));
+  const double2 n2 = make_double2(fma(-s1, b2.x, s2 * b1.x), fma(-s1, b2.y, s2 * b1.y));
+  a[0] = cadd(cadd(x0, a1), a2);
+  a[1] = make_double2(m1.x + n1.y, m1.y - n1.x);       // m1 - i n1
+  a[4] = make_double2(m1.x - n1.y, m1.y + n1.x);       // m1 + i n1
+  a[2] = make_double2(m2.x + n2.y, m2.y - n2.x);       // m2 - i n2
+  a[3] = make_double2(m2.x - n2.y, m2.y + n2.x);       // m2 + i n2
+}
+
+// One decimation-in-time stage of radix R over a row x of length N (element stride 1):
+// groups of L = M R; element q of group g, offset k, is x[g L + q M + k]; twiddles tw[k][q-1]
+// (k = 0 needs none).
+template <int R>
+__host__ __device__ __forceinline__ void fft_stage(double2* x, int N, int M, const double2* tw) {
+  const int L = M * R;
+  for (int g = 0; g < N; g += L) {
+    for (int k = 0; k < M; ++k) {
+      double2 a[R];
+      double2* p = x + g + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q] = p[q * M];
+      if (k > 0) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[k * (R - 1) + q - 1]);
+      }
+      if (R == 2) dft2(a);
+      else if (R == 3) dft3(a);
+      else if (R == 4) dft4(a);
+      else dft5(a);
+#pragma unroll
+      for (int q = 0; q < R; ++q) p[q * M] = a[q];
+    }
+  }
+}
+
+// All stages of the FFT of one row (input already digit-reversed).
+__host__ __device__ __forceinline__ void fft_row(double2* x, const DstBlock& b, const double2* tw) {
+  const int N = b.n + 1;
+  int M = 1;
+  int off = 0;
+  for (int s = 0; s < b.nst; ++s) {
+    const int r = b.rad[s];
+    switch (r) {
+      case 2: fft_stage<2>(x, N, M, tw + off); break;
+      case 3: fft_stage<3>(x, N, M, tw + off); break;
+      case 4: fft_stage<4>(x, N, M, tw + off); break;
+      default: fft_stage<5>(x, N, M, tw + off); break;
+    }
+    off += M * (r - 1);
+    M *= r;
+  }
+}
+
+// In place: Y -> X with X_1 at 0, X_{2k} at k, X_{2k+1} at N - k (k = 1..(N-1)/2).
+__host__ __device__ __forceinline__ void post_row(double2* x, int N) {
+  double2 acc = x[0];
+  for (int k = 1; 2 * k < N; ++k) {
+    const double2 yk = x[k], ym = x[N - k];
+    acc.x += yk.x + ym.x;
+    acc.y += yk.y + ym.y;
+    x[k] = make_double2(ym.y - yk.y, yk.x - ym.x);     // i (Y_k - Y_{N-k})
+    x[N - k] = acc;
+  }
+}
+
+// y_j and y_{N-j} from x_j and x_{N-j} (equal when 2 j = N).
+__host__ __device__ __forceinline__ void pre_pair(double2 xj, double2 xm, double p, double q, double2* yj,
+                                                  double2* ym) {
+  *yj = make_double2(fma(p, xj.x, q * xm.x), fma(p, xj.y, q * xm.y));
+  *ym = make_double2(fma(p, xm.x, q * xj.x), fma(p, xm.y, q * xj.y));
+}
+
+// Smem position of output index m (1..n) after post_row.
+int post_pos(int m, int N) { return m == 1 ? 0 : (m % 2 == 0 ? m / 2 : N - (m - 1) / 2); }
+
+// Mode m of column c in the symmetric-modes-first order of a uniform block (and back).
+int sym_mode(int c, int n) {
+  const int ns = (n + 1) / 2;
+  return c < ns ? 2 * c + 1 : 2 * (c - ns) + 2;
+}
+int sym_col(int m, int n) {
+  const int ns = (n + 1) / 2;
+  return (m % 2 == 1) ? (m - 1) / 2 : ns + m / 2 - 1;
+}
+
+constexpr int kTM = 64;      // rows per CTA (one thread each in the FFT phase)
+constexpr int kNT = 128;     // threads per CTA (all of them load and store)
+
+// Odd row stride (16-byte units) for rows of N values: threads of a warp, one row each,
+// then address distinct shared-memory banks.
+__host__ __device__ __forceinline__ int row_stride(int N) { return N | 1; }
+
+__global__ void __launch_bounds__(kNT)
+dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstBlock* __restrict__ blocks,
+           const int* __restrict__ idx, const double* __restrict__ coef, const double2* __restrict__ twg, int nblk,
+           long long nrows, int rows_per_plane, int ncols, int trans, int store, int conj_out,
+           const signed char* __restrict__ rowskip, int stride) {
+  extern __shared__ double2 sm[];
+  __shared__ int s_ok[kTM];
+  __shared__ long long s_base[kTM];         // first output element of the row (trans: the plane slot)
+  const int blk = (int)(blockIdx.x % (unsigned)nblk);
+  const long long row0 = (long long)(blockIdx.x / (unsigned)nblk) * kTM;
+  const DstBlock b = blocks[blk];
+  const int n = b.n, N = n + 1;
+  double2* tw = sm + kTM * stride;
+  for (int t = threadIdx.x; t < b.ntw; t += kNT) tw[t] = twg[b.tw_off + t];
+  if (threadIdx.x < kTM) {
+    const long long row = row0 + threadIdx.x;
+    int ok = row < nrows;
+    long long base = 0;
+    if (ok) {
+      const long long plane = row / rows_per_plane;
+      const int rip = (int)(row - plane * rows_per_plane);
+      if (rowskip && rowskip[rip]) ok = 0;
+      base = trans ? plane * (long long)ncols * rows_per_plane + rip : row * (long long)ncols;
+    }
+    s_ok[threadIdx.x] = ok;
+    s_base[threadIdx.x] = base;
+    sm[threadIdx.x * stride] = make_double2(0.0, 0.0);      // y_0 (digit-reversed position 0)
+  }
+  __syncthreads();
+  const int* __restrict__ rev = idx + b.ioff;
+  const int* __restrict__ gin = rev + N;
+  const int* __restrict__ src = gin + N;
+  const double* __restrict__ pq = coef + b.coff;
+  // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} digit-reversed
+  const int np = N / 2;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < kTM * np; e += kNT) {
+    const int r = e / np, j = 1 + (e - r * np);
+    double2 xj = make_double2(0.0, 0.0), xm = xj;
+    if (s_ok[r]) {
+      const double2* rp = in + (row0 + r) * (long long)ncols + b.start;
+      xj = rp[gin[j]];
+      xm = rp[gin[N - j]];
+    }
+    double2 yj, ym;
+    pre_pair(xj, xm, pq[2 * j], pq[2 * j + 1], &yj, &ym);
+    double2* x = sm + r * stride;
+    x[rev[j]] = yj;
+    if (N - j != j) x[rev[N - j]] = ym;
+  }
+  __syncthreads();
+  // phase 2: FFT and post step of one row per thread
+  if (threadIdx.x < kTM && s_ok[threadIdx.x]) {
+    double2* x = sm + threadIdx.x * stride;
+    fft_row(x, b, tw);
+    post_row(x, N);
+  }
+  __syncthreads();
+  // phase 3: store (row-contiguous, or transposed with the rows of a column contiguous)
+  for (int e = threadIdx.x; e < kTM * n; e += kNT) {
+    int r, c;
+    if (trans) {
+      c = e / kTM;
+      r = e - c * kTM;
+    } else {
+      r = e / n;
+      c = e - r * n;
+    }
+    if (!s_ok[r]) continue;
+    double2 v = sm[r * stride + src[c]];
+    if (conj_out) v.y = -v.y;
+    double2* p = out + s_base[r] + (long long)(b.start + c) * (trans ? rows_per_plane : 1);
+    if (store == XS_ACCUM) {
+      const double2 o = *p;
+      v.x += o.x;
+      v.y += o.y;
+    }
+    *p = v;
+  }
+}
+
+size_t dst_smem(int nmax) { return sizeof(double2) * ((size_t)kTM * row_stride(nmax) + nmax); }
+
+}  // namespace
+
+void dst_prepare(int nmax) {
+  cudaFuncSetAttribute(dst_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_smem(nmax));
+}
+
+void dst_f64(const DstSet& ds, const double2* in, double2* out, int rows_per_plane, long long nplanes, int ncols,
+             int trans, int store, int conj_out, const signed char* rowskip, cudaStream_t st) {
+  const long long nrows = nplanes * (long long)rows_per_plane;
+  if (nrows <= 0 || ds.nblk == 0) return;
+  const long long ctas = ((nrows + kTM - 1) / kTM) * ds.nblk;
+  dst_kernel<<<(unsigned)ctas, kNT, dst_smem(ds.nmax), st>>>(in, out, ds.d_blk, ds.d_idx, ds.d_coef, ds.d_tw,
+                                                            ds.nblk, nrows, rows_per_plane, ncols, trans, store,
+                                                            conj_out, rowskip, row_stride(ds.nmax));
+  count_launch();
+}
+
+bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& blk, std::vector<int>& idx,
+                    std::vector<double>& coef, std::vector<double2>& tw) {
+  const int N = n + 1;
+  if (n < 2 || N > kDstMaxN || (dir != 1 && dir != 2)) return false;
+  DstBlock b{};
+  b.start = start;
+  b.n = n;
+  int m = N;
+  for (int r : {4, 3, 5, 2}) {
+    while (m % r == 0) {
+      if (b.nst == kDstMaxStages) return false;
+      b.rad[b.nst++] = r;
+      m /= r;
+    }
+  }
+  if (m != 1) return false;
+  const double pi = 3.14159265358979323846;
+  // stage twiddles exp(-2 pi i q k / (M r)), k = 0..M-1, q = 1..r-1 (argument reduced exactly)
+  b.tw_off = (long long)tw.size();
+  int M = 1;
+  for (int s = 0; s < b.nst; ++s) {
+    const int r = b.rad[s], L = M * r;
+    for (int k = 0; k < M; ++k)
+      for (int q = 1; q < r; ++q) {
+        const int e = (q * k) % L;
+        const double th = -2.0 * pi * e / L;
+        tw.push_back(make_double2(std::cos(th), std::sin(th)));
+      }
+    M = L;
+  }
+  b.ntw = (int)(tw.size() - b.tw_off);
+  // rev[N]: digit-reversed position of y_j; gin[N]: column of input index j (1..n);
+  // src[n]: position holding the value of output column c
+  b.ioff = (long long)idx.size();
+  for (int j = 0; j < N; ++j) {
+    int jj = j, pos = 0;
+    int Ls[kDstMaxStages + 1];
+    Ls[0] = 1;
+    for (int s = 0; s < b.nst; ++s) Ls[s + 1] = Ls[s] * b.rad[s];
+    for (int s = b.nst - 1; s >= 0; --s) {
+      pos += (jj % b.rad[s]) * Ls[s];
+      jj /= b.rad[s];
+    }
+    idx.push_back(pos);
+  }
+  for (int j = 0; j < N; ++j) idx.push_back(j == 0 ? 0 : (dir == 1 ? j - 1 : sym_col(j, n)));
+  for (int c = 0; c < n; ++c) idx.push_back(post_pos(dir == 1 ? sym_mode(c, n) : c + 1, N));
+  b.coff = (long long)coef.size();
+  for (int j = 0; j <= N / 2; ++j) {
+    const double sj = std::sin(pi * j / N);
+    coef.push_back(0.5 * S * (sj + 0.5));
+    coef.push_back(0.5 * S * (sj - 0.5));
+  }
+  blk.push_back(b);
+  return true;
+}
+
+bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out) {
+  std::vector<DstBlock> blk;
+  std::vector<int> idx;
+  std::vector<double> coef;
+  std::vector<double2> tw;
+  if (!dst_plan_block(n, 0, dir, S, blk, idx, coef, tw)) return false;
+  const DstBlock& b = blk[0];
+  const int N = n + 1;
+  const int* rev = idx.data() + b.ioff;
+  const int* gin = rev + N;
+  const int* src = gin + N;
+  std::vector<double2> x(N);
+  x[rev[0]] = make_double2(0.0, 0.0);
+  for (int j = 1; 2 * j <= N; ++j) {
+    double2 yj, ym;
+    pre_pair(in[gin[j]], in[gin[N - j]], coef[b.coff + 2 * j], coef[b.coff + 2 * j + 1], &yj, &ym);
+    x[rev[j]] = yj;
+    if (N - j != j) x[rev[N - j]] = ym;
+  }
+  fft_row(x.data(), b, tw.data() + b.tw_off);
+  post_row(x.data(), N);
+  for (int c = 0; c < n; ++c) out[c] = x[src[c]];
+  return true;
+}
+
+}  // namespace hz

@@ -55,6 +55,47 @@ struct XTile {
   int pad;
 };
 
+// Fast sine transform of a uniform block (FP64 path).  The block's table is
+// S sin(pi j m / N), N = n + 1 (forward: rows = nodes j, columns = modes m in the
+// symmetric-modes-first order; inverse: the transpose), i.e. a scaled DST-I.  It is
+// computed from one complex FFT of length N per row: y_j = p_j x_j + q_j x_{N-j}
+// (p_j, q_j = (S / 2) (sin(pi j / N) +- 1/2)), Y = FFT(y) by mixed-radix stages
+// (radices 2, 3, 4, 5; input in digit-reversed order, decimation in time), then
+// X_{2k} = i (Y_k - Y_{N-k}) and X_{2k+1} = X_{2k-1} + Y_k + Y_{N-k}, X_1 = Y_0.
+constexpr int kDstMaxStages = 8;
+constexpr int kDstMaxN = 128;     // largest N = n + 1 handled by the fast transform
+struct DstBlock {
+  int start;                      // first column of the block in the row
+  int n;                          // block width; N = n + 1 = product of the radices
+  int nst;                        // radix stages
+  int rad[kDstMaxStages];         // radices in stage order
+  int ntw;                        // twiddles of all stages (complex entries)
+  long long tw_off;               // offset (complex) of the stage twiddles
+  long long ioff;                 // offset (ints) of rev[N], gin[N], src[n]
+  long long coff;                 // offset (doubles) of (p_j, q_j), j = 0..N/2
+};
+struct DstSet {
+  int nblk = 0;
+  int nmax = 0;                   // largest N of the set
+  DstBlock* d_blk = nullptr;
+  int* d_idx = nullptr;
+  double* d_coef = nullptr;
+  double2* d_tw = nullptr;
+};
+// Host: the fast-transform descriptor of a block of width n whose table is S sin(pi j m / N);
+// dir = 1: forward (natural nodes in, symmetric-modes-first out), 2: inverse (the reverse).
+// Appends to the index, coefficient and twiddle arrays; false if N has a prime factor > 5,
+// N > kDstMaxN or n < 2.
+bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& blk, std::vector<int>& idx,
+                    std::vector<double>& coef, std::vector<double2>& tw);
+// Host reference of the same computation (the code the kernel runs per row), for tests:
+// out = table^T applied to one row in (n values each).
+bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out);
+// Set the kernel's shared-memory limit for blocks up to N = nmax (current device, before any capture).
+void dst_prepare(int nmax);
+void dst_f64(const DstSet& ds, const double2* in, double2* out, int rows_per_plane, long long nplanes, int ncols,
+             int trans, int store, int conj_out, const signed char* rowskip, cudaStream_t st);
+
 // A device-resident block-diagonal transform (one per axis and use).
 struct XformSet {
   int ncols = 0;                  // row length (axis length)
@@ -65,6 +106,11 @@ struct XformSet {
   double* d_tab = nullptr;        // FP64 tables (3M layout for complex blocks)
   float* d_tab32 = nullptr;       // FP32 copy of the same tables for the mixed path
   std::vector<XBlock> h_blocks;
+  // FP64 fast sine transforms of the uniform blocks whose N = n + 1 factors into 2, 3, 5:
+  // with fast_sine the dense kernel runs only the tiles64 (the other blocks)
+  DstSet dst;
+  int ntiles64 = 0;
+  XTile* d_tiles64 = nullptr;
 };
 
 enum XformStore { XS_STORE = 0, XS_ACCUM = 1 };
@@ -118,9 +164,10 @@ bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, i
 // conjugates the result before it is stored.
 // rowskip (may be NULL) flags rows (index within the plane) that are neither computed nor
 // written: the interface rows, which belong to no block.
+// fast_sine: uniform blocks with a fast-transform descriptor use dst_f64.
 void xform_f64(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
-               cudaStream_t st);
+               cudaStream_t st, bool fast_sine = false);
 // Same contraction with FP32 arithmetic on FP64 data (SIMT FFMA), for the mixed path.
 void xform_f32(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,

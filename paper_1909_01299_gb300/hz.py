@@ -48,7 +48,7 @@ class hz_info(ctypes.Structure):
                 ("min_abs_pivot", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("eig_max_residual", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("nbx", ctypes.c_int), ("nby", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("fast_sine", ctypes.c_int)]
 
 
 # Every symbol declared in include/hz.h, with its ctypes signature.
@@ -60,6 +60,8 @@ SIGNATURES = {
     "hz_plan_set_frequency": (ctypes.c_int, [_P, ctypes.c_double]),
     "hz_plan_set_k2": (ctypes.c_int, [_P, _P]),
     "hz_plan_set_options": (ctypes.c_int, [_P, ctypes.POINTER(hz_options)]),
+    "hz_plan_set_fast_sine": (ctypes.c_int, [_P, ctypes.c_int]),
+    "hz_sine_transform_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P]),
     "hz_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "hz_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
@@ -126,6 +128,15 @@ def tridiag_eig(kd, ko, m):
     _check(_lib.hz_tridiag_eig(n, kd.ctypes.data, ko.ctypes.data if n > 1 else None, m.ctypes.data,
                                lam.ctypes.data, W.ctypes.data, ctypes.byref(res)), "hz_tridiag_eig")
     return lam, W, res.value
+
+
+def sine_transform_host(x, direction: int, scale: float) -> np.ndarray:
+    """Host-only: the plan's fast sine transform of one row (hz_sine_transform_host)."""
+    x = _c128_array(x)
+    out = np.empty_like(x)
+    _check(_lib.hz_sine_transform_host(len(x), int(direction), float(scale), x.ctypes.data, out.ctypes.data),
+           "hz_sine_transform_host")
+    return out
 
 
 def _stream_handle(stream):
@@ -204,7 +215,13 @@ class Plan:
         """hz_plan_autotune: pick the fastest kernel variants for nrhs right-hand sides."""
         c = ctypes.c_int()
         _check(_lib.hz_plan_autotune(self._h, int(nrhs), ctypes.byref(c)), "hz_plan_autotune")
-        return {"rhs_per_thread": c.value % 10, "tensor_cores": c.value >= 10}
+        return {"rhs_per_thread": c.value % 10, "tensor_cores": (c.value // 10) % 10 == 1,
+                "fast_sine": c.value >= 100}
+
+    def set_fast_sine(self, enable: bool):
+        """FP64 path: uniform blocks by the FFT-based sine transform (True) or the folded
+        dense product (False) (hz_plan_set_fast_sine)."""
+        _check(_lib.hz_plan_set_fast_sine(self._h, int(bool(enable))), "hz_plan_set_fast_sine")
 
     def set_frequency(self, omega: float):
         _check(_lib.hz_plan_set_frequency(self._h, float(omega)), "hz_plan_set_frequency")

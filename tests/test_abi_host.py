@@ -101,3 +101,34 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_device(hz):
 
 class _NoStream:
     cuda_stream = 0
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7, 8, 9, 11, 14, 15, 19, 23, 24, 29, 31, 35, 39, 47, 63, 79, 80, 99, 119, 127])
+def test_fast_sine_transform_matches_the_definition(hz, n):
+    # the plan's FFT-based sine transform (host twin of the GPU kernel) against the DST-I sum
+    # out = S sum_j x_j sin(pi j m / (n + 1)) with the symmetric-modes-first column order
+    rng = np.random.default_rng(n)
+    N = n + 1
+    ns = (n + 1) // 2
+    modes = np.array([2 * c + 1 if c < ns else 2 * (c - ns) + 2 for c in range(n)])
+    Sm = np.sin(np.pi * np.outer(np.arange(1, N), np.arange(1, N)) / N)   # [j-1][m-1]
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    S = 0.37
+    # forward: natural nodes in, modes out in the symmetric-first order
+    ref_f = S * (x @ Sm)[modes - 1]
+    got_f = hz.sine_transform_host(x, 1, S)
+    assert np.max(np.abs(got_f - ref_f)) <= 1e-13 * np.max(np.abs(ref_f))
+    # inverse: modes in (symmetric-first order), natural nodes out
+    X = np.empty(n, complex)
+    X[modes - 1] = x
+    ref_i = S * (Sm @ X)
+    got_i = hz.sine_transform_host(x, 2, S)
+    assert np.max(np.abs(got_i - ref_i)) <= 1e-13 * np.max(np.abs(ref_i))
+
+
+@pytest.mark.parametrize("n", [1, 6, 12, 128, 160])
+def test_fast_sine_transform_rejects_unsupported_lengths(hz, n):
+    # n + 1 with a prime factor above 5 (7, 13, 161 = 7 x 23), n + 1 > 128, or n < 2
+    with pytest.raises(hz.HzError) as e:
+        hz.sine_transform_host(np.ones(n, complex), 1, 1.0)
+    assert e.value.code == 1

@@ -48,8 +48,8 @@ def test_batch_matches_oracle_and_single_solves(env):
     for call in range(2):                                   # capture, then replay
         for u in us:
             u.zero_()
-        rel = batch.solve(fs, us)
-        for (w, om, prec), u, ref, r in zip(items, us, refs, rel):
+        relres = batch.solve(fs, us)
+        for (w, om, prec), u, ref, r in zip(items, us, refs, relres):
             tol = 1e-8 if prec == "mixed" else 1e-10
             err = rel(u.cpu().numpy(), ref)
             assert err < tol, (call, prec, err)
@@ -77,8 +77,8 @@ def test_batch_autotune_picks_a_lane_count(env):
     batch = hz.Batch(plans, [w.f.shape[0] for w, _, _ in items])
     lanes = batch.autotune(fs, us)
     assert lanes in (1, 2, 4)
-    rel = batch.solve(fs, us)
-    assert np.all(rel <= 1e-8)
+    relres = batch.solve(fs, us)
+    assert np.all(relres <= 1e-8)
     batch.close()
 
 

@@ -356,14 +356,54 @@ def _uniform_mix_workload(nrhs=2):
                       rng.standard_normal((nrhs, nz, ny, nx)) + 1j * rng.standard_normal((nrhs, nz, ny, nx)))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_uniform_blocks_sine_path(hz, torch_cuda, precision):
+@pytest.mark.parametrize("precision,fast", [("fp64", True), ("fp64", False), ("mixed", True)])
+def test_uniform_blocks_sine_path(hz, torch_cuda, precision, fast):
+    # x blocks 17 (n + 1 = 18 = 2 x 3 x 3: fast sine transform), 18 (19 is prime: folded dense),
+    # 17; y core block of 35 (36 = 4 x 3 x 3) between dense complex rim blocks
     w = _uniform_mix_workload()
     P = O.Problem.from_workload(w)
     ref = O.solve(P, w.f)
-    plan, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+    plan = hz.Plan.from_workload(w, precision=precision)
+    plan.set_fast_sine(fast)
+    u = plan.solve(torch_cuda.from_numpy(w.f).cuda()).cpu().numpy()
     assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
     assert plan.info()["eig_max_residual"] < 1e-12
+    assert plan.info()["fast_sine"] == int(fast)
+
+
+def test_fast_sine_many_tiles_against_lu_and_dense(hz, torch_cuda):
+    # uniform 160 x 99 x 7 grid: x blocks of 79 and 80 nodes (n + 1 = 80 = 4 x 4 x 5 and
+    # 81 = 3^4, as in the 320-node benchmark grid), y one block of 99 (100 = 4 x 5 x 5);
+    # 3 RHS give 2079 and 3339 rows per transform launch (ragged last row tile)
+    torch = torch_cuda
+    rng = np.random.default_rng(17)
+    nx, ny, nz = 160, 99, 7
+    f = rng.standard_normal((3, nz, ny, nx)) + 1j * rng.standard_normal((3, nz, ny, nx))
+    w = W.Workload("uniform-fast-sine", W.uniform_steps(nx, 0.8), W.uniform_steps(ny, 1.2), W.ramp_z(nz),
+                   np.array([0, 3, nz], np.int32), np.array([0.3 + 0.02j, 0.15 + 0.01j]),
+                   np.array([79], np.int32), np.zeros(0, np.int32), f)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan = hz.Plan.from_workload(w, precision="fp64")
+    fd = torch.from_numpy(w.f).cuda()
+    u_fast = plan.solve(fd).cpu().numpy()
+    assert plan.info()["fast_sine"] == 1
+    plan.set_fast_sine(False)
+    u_dense = plan.solve(fd).cpu().numpy()
+    assert rel(u_fast, ref) < TOL64
+    assert rel(u_fast, u_dense) < 1e-12
+
+
+def test_fast_sine_adjoint(hz, torch_cuda):
+    # the conjugating inverse transform of the FP64 adjoint through the fast sine kernel
+    torch = torch_cuda
+    w = _uniform_mix_workload()
+    rng = np.random.default_rng(13)
+    g = rng.standard_normal(w.f.shape) + 1j * rng.standard_normal(w.f.shape)
+    lam_o = O.adjoint_solve(O.Problem.from_workload(w), g, method="lu")
+    plan = hz.Plan.from_workload(w, precision="fp64")
+    lam = plan.solve_adjoint(torch.from_numpy(g).cuda()).cpu().numpy()
+    assert plan.info()["fast_sine"] == 1
+    assert rel(lam, lam_o) < TOL64
 
 
 def test_uniform_blocks_mixed_adjoint(hz, torch_cuda):
