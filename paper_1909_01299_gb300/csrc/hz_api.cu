@@ -61,6 +61,7 @@ struct AxisDev {
   float2 *cl32 = nullptr, *cr32 = nullptr;
   double2* ks = nullptr;                                     // stencil rows / mhat
   signed char* kreal = nullptr;                              // off-diagonals of row real
+  bool edge_real = false, g_real = false, lr_real = false;   // edge_coef, gcoef, cl/cr all real
 };
 
 struct Workspace {
@@ -515,6 +516,12 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
     erng[2 * q] = make_int2(sl, sl + nl);
     erng[2 * q + 1] = make_int2(sr, sr + nr);
   }
+  auto all_real = [](const std::vector<cd>& v) {
+    for (const cd& z : v)
+      if (z.imag() != 0.0) return false;
+    return true;
+  };
+  D.edge_real = all_real(ecoef);
   D.edge_coef = upload_c(p, ecoef);
   D.edge_coef32 = upload_c32(p, ecoef);
   D.edge_rng = upload(p, erng);
@@ -524,6 +531,7 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
   if (need_global)
     for (int q = 0; q < nI; ++q)
       for (int l = 0; l < n; ++l) gcoef[(size_t)q * n + l] = A.gW[(size_t)A.iface[q] * n + l];
+  D.g_real = all_real(gcoef);
   D.gcoef = upload_c(p, gcoef);
   D.gcoef32 = upload_c32(p, gcoef);
   D.grng = upload(p, grng);
@@ -545,6 +553,7 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
   }
   D.gl = upload(p, gl);
   D.gr = upload(p, grr);
+  D.lr_real = all_real(cl) && all_real(cr);
   D.cl = upload_c(p, cl);
   D.cr = upload_c(p, cr);
   D.cl32 = upload_c32(p, cl);
@@ -821,7 +830,8 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     // one pass saves no work but gives fewer threads)
     if (!edge && lo && hz::contract_all(true, w.V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
     if (lo) hz::contract_rows(w.V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
-    else hz::contract_rows(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+    else hz::contract_rows(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s,
+                           edge ? d.edge_real : d.g_real);
   };
   auto ccols = [&](const AxisDev& d, double2* out, bool edge, int nslots, cudaStream_t s) {
     const int2* rng = edge ? d.edge_rng : d.grng;
@@ -832,7 +842,8 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     }
     if (!edge && lo && hz::contract_all(false, w.V, out, d.gcoef32, nx, ny, nslots, planes, s)) return;
     if (lo) hz::contract_cols(w.V, out, edge ? d.edge_coef32 : d.gcoef32, rng, nx, ny, nslots, planes, s);
-    else hz::contract_cols(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s);
+    else hz::contract_cols(w.V, out, edge ? d.edge_coef : d.gcoef, rng, nx, ny, nslots, planes, s,
+                           edge ? d.edge_real : d.g_real);
   };
   // Step 1: f~ = (W_x^T M_x) (x) (W_y^T M_y) f per plane; rows j -> G[i][j] -> FT[i][j]
   {
@@ -890,6 +901,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     hz::GlobalRhsArgs ga;
     ga.nx = nx; ga.ny = ny; ga.nz = nz; ga.nrhs = R; ga.nIx = nIx; ga.nIy = nIy;
     ga.aX = w.aX; ga.bY = w.bY; ga.WgxI = p->dx.gcoef; ga.WgyI = p->dy.gcoef;
+    ga.real_x = p->dx.g_real ? 1 : 0; ga.real_y = p->dy.g_real ? 1 : 0;
     if (lo) { ga.WgxI32 = p->dx.gcoef32; ga.WgyI32 = p->dy.gcoef32; }
     hz::ZSolveArgs zg = za;
     zg.skip_i = nullptr; zg.skip_j = nullptr;
@@ -921,6 +933,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     ba.alphaX = w.alX; ba.alphaY = w.alY;
     ba.gxl = p->dx.gl; ba.gxr = p->dx.gr; ba.gyl = p->dy.gl; ba.gyr = p->dy.gr;
     ba.cxl = p->dx.cl; ba.cxr = p->dx.cr; ba.cyl = p->dy.cl; ba.cyr = p->dy.cr;
+    ba.real_x = p->dx.lr_real ? 1 : 0; ba.real_y = p->dy.lr_real ? 1 : 0;
     if (lo) { ba.cxl32 = p->dx.cl32; ba.cxr32 = p->dx.cr32; ba.cyl32 = p->dy.cl32; ba.cyr32 = p->dy.cr32; }
     if (c64) hz::boundary_rhs(ba, FT32, st);        // f~ + g~ / M_z, in place
     else hz::boundary_rhs(ba, w.FT, st);

@@ -31,10 +31,11 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 
 // C = double2: FP64 arithmetic; C = float2: FP32 arithmetic (mixed path) on complex128 or
 // complex64 data (TV).
+// real_coef (FP64): the coefficients are real (their imaginary parts are zero), 2 FMA per term.
 template <typename C, typename TV>
 __global__ void contract_rows_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                      const C* __restrict__ coef, const int2* __restrict__ range,
-                                     int nrows, int ncols, int nslots, long long nplanes) {
+                                     int nrows, int ncols, int nslots, long long nplanes, int real_coef) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long total = nplanes * nslots * (long long)ncols;
   if (t >= total) return;
@@ -47,7 +48,16 @@ __global__ void contract_rows_kernel(const TV* __restrict__ V, double2* __restri
   const C* __restrict__ c = coef + (long long)s * nrows;
   if constexpr (sizeof(C) == sizeof(double2)) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = rg.x; i < rg.y; ++i) acc = cfma(c[i], v[(long long)i * ncols], acc);
+    if (real_coef) {
+      for (int i = rg.x; i < rg.y; ++i) {
+        const double ci = c[i].x;
+        const double2 x = v[(long long)i * ncols];
+        acc.x = fma(ci, x.x, acc.x);
+        acc.y = fma(ci, x.y, acc.y);
+      }
+    } else {
+      for (int i = rg.x; i < rg.y; ++i) acc = cfma(c[i], v[(long long)i * ncols], acc);
+    }
     out[t] = acc;
   } else {
     float2 acc = make_float2(0.f, 0.f);
@@ -62,7 +72,7 @@ __global__ void contract_rows_kernel(const TV* __restrict__ V, double2* __restri
 template <typename C, typename TV>
 __global__ void contract_cols_kernel(const TV* __restrict__ V, double2* __restrict__ out,
                                      const C* __restrict__ coef, const int2* __restrict__ range,
-                                     int nrows, int ncols, int nslots, long long nplanes) {
+                                     int nrows, int ncols, int nslots, long long nplanes, int real_coef) {
   constexpr bool F64 = sizeof(C) == sizeof(double2);
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long t = F64 ? gt : gt >> 5;
@@ -78,7 +88,16 @@ __global__ void contract_cols_kernel(const TV* __restrict__ V, double2* __restri
   const C* __restrict__ c = coef + (long long)s * ncols;
   if constexpr (F64) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
+    if (real_coef) {
+      for (int j = rg.x; j < rg.y; ++j) {
+        const double cj = c[j].x;
+        const double2 x = v[j];
+        acc.x = fma(cj, x.x, acc.x);
+        acc.y = fma(cj, x.y, acc.y);
+      }
+    } else {
+      for (int j = rg.x; j < rg.y; ++j) acc = cfma(c[j], v[j], acc);
+    }
     out[t] = acc;
   } else {
     float2 a32 = make_float2(0.f, 0.f);
@@ -439,22 +458,22 @@ unsigned blocks_for(long long n, int T) { return (unsigned)((n + T - 1) / T); }
 
 template <typename C, typename TV>
 void contract_rows_t(const TV* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
-                     int nslots, long long nplanes, cudaStream_t st) {
+                     int nslots, long long nplanes, cudaStream_t st, int real_coef = 0) {
   const long long n = nplanes * nslots * (long long)ncols;
   if (n == 0) return;
   contract_rows_kernel<C, TV><<<blocks_for(n, 128), 128, 0, st>>>(V, out, coef, range, nrows, ncols, nslots,
-                                                                 nplanes);
+                                                                 nplanes, real_coef);
   count_launch();
 }
 
 template <typename C, typename TV>
 void contract_cols_t(const TV* V, double2* out, const C* coef, const int2* range, int nrows, int ncols,
-                     int nslots, long long nplanes, cudaStream_t st) {
+                     int nslots, long long nplanes, cudaStream_t st, int real_coef = 0) {
   const long long n = nplanes * nslots * (long long)nrows;
   if (n == 0) return;
   const long long threads = sizeof(C) == sizeof(double2) ? n : n * 32;   // FP32: one warp per output
   contract_cols_kernel<C, TV><<<blocks_for(threads, 256), 256, 0, st>>>(V, out, coef, range, nrows, ncols,
-                                                                       nslots, nplanes);
+                                                                       nslots, nplanes, real_coef);
   count_launch();
 }
 
@@ -499,8 +518,8 @@ bool contract_all(bool rows, const float2* V, double2* out, const float2* coef, 
 }
 
 void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
-                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
-  contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+                   int ncols, int nslots, long long nplanes, cudaStream_t st, bool real_coef) {
+  contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st, real_coef ? 1 : 0);
 }
 void contract_rows(const double2* V, double2* out, const float2* coef, const int2* range, int nrows,
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {
@@ -511,8 +530,8 @@ void contract_rows(const float2* V, double2* out, const float2* coef, const int2
   contract_rows_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
 }
 void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range, int nrows,
-                   int ncols, int nslots, long long nplanes, cudaStream_t st) {
-  contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st);
+                   int ncols, int nslots, long long nplanes, cudaStream_t st, bool real_coef) {
+  contract_cols_t(V, out, coef, range, nrows, ncols, nslots, nplanes, st, real_coef ? 1 : 0);
 }
 void contract_cols(const double2* V, double2* out, const float2* coef, const int2* range, int nrows,
                    int ncols, int nslots, long long nplanes, cudaStream_t st) {

@@ -218,6 +218,7 @@ struct BoundaryArgs {
   // FP32 and added to f~ in FP64 (mixed path)
   const float2* cxl32 = nullptr; const float2* cxr32 = nullptr;
   const float2* cyl32 = nullptr; const float2* cyr32 = nullptr;
+  int real_x = 0, real_y = 0;            // FP64: cxl/cxr (cyl/cyr) are real
 };
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st);
 // complex64 f~ (mixed path, needs the FP32 coefficient copies): the sum is formed in FP64
@@ -233,6 +234,7 @@ struct GlobalRhsArgs {
   const double2* WgyI = nullptr;         // [nIy][ny]
   const float2* WgxI32 = nullptr;        // FP32 copies: when set, FP32 arithmetic (mixed path)
   const float2* WgyI32 = nullptr;
+  int real_x = 0, real_y = 0;            // FP64: WgxI (WgyI) is real
 };
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
 // complex64 output (mixed path, needs the FP32 coefficient copies)
@@ -249,12 +251,13 @@ void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,
 // ---------------------------------------------------------------------------
 // Interface steps
 // ---------------------------------------------------------------------------
-// out[plane][s][j] = sum_{i in [lo_s, hi_s)} coef[s][i] V[plane][i][j]  (contraction over rows)
+// out[plane][s][j] = sum_{i in [lo_s, hi_s)} coef[s][i] V[plane][i][j]  (contraction over rows);
+// real_coef: every coefficient is real (2 FMA per term instead of 4)
 void contract_rows(const double2* V, double2* out, const double2* coef, const int2* range,
-                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st, bool real_coef = false);
 // out[plane][s][i] = sum_{j in [lo_s, hi_s)} coef[s][j] V[plane][i][j]  (contraction within rows)
 void contract_cols(const double2* V, double2* out, const double2* coef, const int2* range,
-                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st);
+                   int nrows, int ncols, int nslots, long long nplanes, cudaStream_t st, bool real_coef = false);
 // Contractions whose every slot covers the whole row (rows = true: over i, out[plane][s][j];
 // false: over j, out[plane][s][i]) in one pass over V; false (nothing launched) unless
 // 2 <= nslots <= 8.  FP32 arithmetic (mixed path).

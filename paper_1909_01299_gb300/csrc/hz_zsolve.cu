@@ -40,6 +40,10 @@ __device__ __forceinline__ double2 csub_mul(double2 b, double2 c, double2 y) {
 __device__ __forceinline__ double2 cfma(double2 c, double2 y, double2 acc) {
   return make_double2(fma(c.x, y.x, fma(-c.y, y.y, acc.x)), fma(c.x, y.y, fma(c.y, y.x, acc.y)));
 }
+// acc + c * y with a real c
+__device__ __forceinline__ double2 rfma(double c, double2 y, double2 acc) {
+  return make_double2(fma(c, y.x, acc.x), fma(c, y.y, acc.y));
+}
 
 // RB right-hand sides per thread share each factor load and give the sweep RB independent
 // dependency chains.  C64: complex64 right-hand side and result (mixed path); the forward
@@ -152,10 +156,20 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
       v.y = fma(s, gd.y, v.y);
     } else {
       double2 g = make_double2(0.0, 0.0);
-      if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
-      if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
-      if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
-      if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
+      if (a.real_x) {
+        if (pl >= 0) g = rfma(a.cxl[i].x, ax[(long long)pl * a.ny], g);
+        if (pr >= 0) g = rfma(a.cxr[i].x, ax[(long long)pr * a.ny], g);
+      } else {
+        if (pl >= 0) g = cfma(a.cxl[i], ax[(long long)pl * a.ny], g);
+        if (pr >= 0) g = cfma(a.cxr[i], ax[(long long)pr * a.ny], g);
+      }
+      if (a.real_y) {
+        if (ql >= 0) g = rfma(a.cyl[j].x, ay[(long long)ql * a.nx], g);
+        if (qr >= 0) g = rfma(a.cyr[j].x, ay[(long long)qr * a.nx], g);
+      } else {
+        if (ql >= 0) g = cfma(a.cyl[j], ay[(long long)ql * a.nx], g);
+        if (qr >= 0) g = cfma(a.cyr[j], ay[(long long)qr * a.nx], g);
+      }
       if (a.sig) {
         v.x = fma(s, g.x, v.x);
         v.y = fma(s, g.y, v.y);
@@ -197,8 +211,14 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, O
       val[e] = to_c128(g);
     } else {
       double2 b = make_double2(0.0, 0.0);
-      for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
-      for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
+      if (a.real_x)
+        for (int p = 0; p < a.nIx; ++p) b = rfma(a.WgxI[(long long)p * a.nx + i].x, ax[(long long)p * a.ny], b);
+      else
+        for (int p = 0; p < a.nIx; ++p) b = cfma(a.WgxI[(long long)p * a.nx + i], ax[(long long)p * a.ny], b);
+      if (a.real_y)
+        for (int q = 0; q < a.nIy; ++q) b = rfma(a.WgyI[(long long)q * a.ny + j].x, by[(long long)q * a.nx], b);
+      else
+        for (int q = 0; q < a.nIy; ++q) b = cfma(a.WgyI[(long long)q * a.ny + j], by[(long long)q * a.nx], b);
       val[e] = b;
     }
   }
