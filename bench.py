@@ -342,29 +342,88 @@ def real_tables(w):
     return bool(np.all(np.imag(w.hx) == 0) and np.all(np.imag(w.hy) == 0))
 
 
-def fp64_roofline(w, R, st, traffic_workload=None):
-    """Roofline of the FP64 bulk transform (the FP64 path's dominant kernel), bound by the FP64 pipe.
+def fast_sine_ok(n):
+    """A uniform block of width n takes the FFT-based sine transform: n >= 2 and n + 1 <= 128
+    with no prime factor above 5."""
+    N = n + 1
+    if n < 2 or N > 128:
+        return False
+    for q in (2, 3, 5):
+        while N % q == 0:
+            N //= q
+    return N == 1
 
-    Algorithmic flops: the dense product of a block of width n, per transformed complex value
-    4 n real flops for a real table (2 FMA per multiply-add) and 8 n for a complex one; four
-    launches per solve.  Uniform blocks are folded (the kernel issues half the multiply-adds of
-    the dense product), which is why the fraction can exceed 1 on this count.
+
+def fast_sine_flops(n):
+    """Algorithmic flops of the fast sine transform of one row of a block of width n: one
+    complex FFT of length N = n + 1 at the standard 5 N log2 N count, the pre step (6 flops per
+    value) and the post step (3 per value)."""
+    import math
+    N = n + 1
+    return 5 * N * math.log2(N) + 9 * (N - 1)
+
+
+def uniform_blocks(h, ifaces):
+    """Per block of the axis: True when all its steps are equal, real and positive."""
+    import numpy as np
+    edges = [-1] + [int(p) for p in ifaces] + [len(h) - 1]
+    out = []
+    for b in range(len(edges) - 1):
+        s, n = edges[b] + 1, edges[b + 1] - edges[b] - 1
+        st = np.asarray(h[s:s + n + 1])
+        out.append(bool(np.all(st.imag == 0) and st[0].real > 0 and np.all(st == st[0])))
+    return out
+
+
+def fp64_transform_work(w, nrhs):
+    """Per bulk launch of the FP64 path (average of the 4 launches of a solve): algorithmic flops
+    of the dense products (4 n real flops per complex value for real tables, 8 n for complex
+    ones) and of the fast sine transforms, and whether every block is a fast-sine block."""
+    import numpy as np
+    dense, fast, all_fast = 0.0, 0.0, True
+    for h, ifc, other_n, other_ifc in ((w.hx, w.x_iface, w.ny, w.y_iface), (w.hy, w.y_iface, w.nx, w.x_iface)):
+        rows = nrhs * w.nz * (other_n - len(other_ifc))
+        real = bool(np.all(np.imag(h) == 0))
+        for n, uni in zip(block_sizes(len(h) - 1, ifc), uniform_blocks(h, ifc)):
+            if uni and fast_sine_ok(n):
+                fast += 2 * rows * fast_sine_flops(n)            # forward and inverse launches
+            else:
+                all_fast = False
+                dense += 2 * rows * n * n * (4 if (real or uni) else 8)
+    return dense / 4, fast / 4, all_fast
+
+
+def fp64_roofline(w, R, st, traffic_workload=None):
+    """Roofline of the FP64 path's bulk transforms (its dominant kernels), bound by the FP64 pipe.
+
+    Algorithmic flops per launch: for blocks on the fast sine transform the FFT count of
+    fast_sine_flops per row; for the others the dense product, 4 n real flops per complex value
+    for a real table (2 FMA per multiply-add) and 8 n for a complex one.  Four launches per
+    solve; the launch time is the stage timers' average.
     """
-    macs = bulk_macs(w, R)
-    per_mac = 4 if real_tables(w) else 8
-    flops = sum(macs) / 4 * per_mac
+    dense, fast, all_fast = fp64_transform_work(w, R)
+    flops = dense + fast
     t = launch_ms(st)
     achieved = flops / (t * 1e-3) / 1e12
     peak = N_SM * SM_MAX_MHZ * 1e6 * FP64_FLOPS_PER_CLK_SM / 1e12
     total_ms = sum(v[0] for v in st.values())
-    return {"bound": "alu", "kernel": "xform_kernel<double> (FP64 bulk x/y transforms)",
+    if all_fast:
+        kernel, fname = "dst_kernel (FP64 fast sine transforms of the uniform blocks)", "hz_dst.cu"
+        count = "fast sine transform: 5 N log2 N + 9 (N - 1) real flops per row of a block of width n, N = n + 1"
+    elif fast == 0:
+        kernel, fname = "xform_kernel<double> (FP64 bulk x/y transforms)", "hz_xform.cu"
+        count = ("dense product: 4 n real flops per complex value for real tables, 8 n for complex ones "
+                 "(n = block width)")
+    else:
+        kernel, fname = "xform_kernel<double> + dst_kernel (FP64 bulk x/y transforms)", "hz_xform.cu"
+        count = "dense product for the non-uniform blocks, fast sine transform count for the uniform ones"
+    return {"bound": "alu", "kernel": kernel,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "flop_count": (f"dense product: {per_mac} n real flops per complex value "
-                           f"({'real' if per_mac == 4 else 'complex'} tables, n = block width)"),
+            "flop_count": count,
             "peak_note": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s); "
                          "probe measured 1.197 TFLOP/s at ~1.97 GHz",
             "flops_per_launch": flops, "launch_ms": t,
-            "traffic": profiled_traffic("xform_kernel<double>", traffic_workload or w.name),
+            "traffic": profiled_traffic(kernel.split(" ")[0], traffic_workload or w.name, fname),
             "share_of_step": (st["fwd"][0] + st["inv"][0]) / max(total_ms, 1e-9)}
 
 

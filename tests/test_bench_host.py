@@ -58,20 +58,37 @@ def test_traffic_records_are_dropped_for_changed_sources(tmp_path, monkeypatch):
 
 
 def test_benchmark_workload_counts():
-    # 320 x 320 x 200, interfaces at 79, 159, 239: blocks of 79, 79, 79 and 80 nodes, 8 RHS,
-    # real (uniform) tables: 4 n real flops per complex value in the dense product
+    # 320 x 320 x 200, interfaces at 79, 159, 239: blocks of 79, 79, 79 and 80 nodes, 8 RHS;
+    # every block is uniform with n + 1 = 80 or 81, so all take the fast sine transform
+    import math
     import bench
     w = bench.bench_workload()
     assert (w.nx, w.ny, w.nz, w.nrhs) == (320, 320, 200, 8)
     per_launch = 8 * 200 * 317 * (3 * 79 * 79 + 80 * 80)
     assert bench.bulk_macs(w, 8) == [per_launch] * 4
     assert bench.real_tables(w)
+    assert bench.uniform_blocks(w.hx, w.x_iface) == [True] * 4
+    assert [bench.fast_sine_ok(n) for n in (79, 80, 12, 127, 128)] == [True, True, False, True, False]
+    rows = 8 * 200 * 317
+    fft = lambda N: 5 * N * math.log2(N) + 9 * (N - 1)
+    dense, fast, all_fast = bench.fp64_transform_work(w, 8)
+    assert all_fast and dense == 0
+    assert abs(fast - rows * (3 * fft(80) + fft(81))) < 1e-6 * fast
     st = {k: (0.0, 0) for k in ("fwd", "pass_a", "edges", "iface_residual", "global", "pass_b", "inv",
                                 "iface_out", "residual")}
     st["fwd"] = (2.0, 2)
     st["inv"] = (2.0, 2)
     roof = bench.fp64_roofline(w, 8, st)
-    assert roof["flops_per_launch"] == per_launch * 4
-    assert abs(roof["achieved"] - per_launch * 4 / 1e-3 / 1e12) < 1e-9
+    assert roof["kernel"].startswith("dst_kernel")
+    assert abs(roof["achieved"] - fast / 1e-3 / 1e12) < 1e-9
     one = bench.one_rhs(w, 3)
     assert one.nrhs == 1 and (one.f[0] == w.f[3]).all()
+
+
+def test_pml_workload_uses_the_dense_count():
+    # the PML rim makes every block non-uniform (complex tables): 8 n flops per value
+    import bench
+    w = W.pml_160x160x128()
+    dense, fast, all_fast = bench.fp64_transform_work(w, 4)
+    assert fast == 0 and not all_fast
+    assert dense == 4 * 128 * 159 * (79 * 79 + 80 * 80) * 8
