@@ -55,7 +55,8 @@ typedef enum {
   HZ_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up                     */
 } hz_status;
 
-enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+/* Precision of a plan (hz_options.precision).  HZ_MIXED is HZ_MIXED_3XTF32. */
+enum { HZ_FP64 = 0, HZ_MIXED = 1, HZ_MIXED_3XTF32 = 1, HZ_MIXED_TF32 = 2 };
 
 typedef struct hz_plan_s *hz_plan_t;
 
@@ -91,7 +92,10 @@ typedef struct {
   const int *x_iface, *y_iface;
 } hz_blocks;
 
-/* Options.  precision: HZ_FP64 (all arithmetic FP64) or HZ_MIXED (x/y
+/* Options.  precision: HZ_FP64 (all arithmetic FP64) or a mixed precision, HZ_MIXED (=
+ * HZ_MIXED_3XTF32: the bulk tensor-core transforms as three TF32 products, A_hi B_hi + A_hi B_lo
+ * + A_lo B_hi, about FP32 accuracy) or HZ_MIXED_TF32 (one TF32 product, about 1e-3 relative
+ * accuracy per transform, so the refinement needs more corrections) (x/y
  * eigen-transforms in FP32, the bulk ones on the tensor cores; z solves, the interface
  * residual and the refinement residual in FP64; FP64 iterative refinement until the
  * relative residual ||M f - A u|| / ||M f|| <= rtol for every RHS, at most max_refine

@@ -798,7 +798,8 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   auto bulk = [&](const hz::XformSet& xs, const hz::TCSet& ts, const void* in, int in32, void* out, int out32,
                   int rpp, int trans, int store_mode, int conj, const signed char* skip) {
     if (in32 || out32 || (lo && p->use_tc && !conj)) {
-      if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st))
+      if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st,
+                        p->opts.precision == HZ_MIXED_TF32 ? 1 : 3))
         throw Fail{HZ_ERR_ARG};
     } else if (!lo) {
       hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
@@ -1023,7 +1024,7 @@ void solve_full_impl(hz_plan_t p, const double2* f, double2* u, int R, int conj_
   ensure_ws(p, R);
   p->info.refinements = 0;
   p->info.rel_residual = -1.0;
-  if (p->opts.precision != HZ_MIXED) {
+  if (p->opts.precision == HZ_FP64) {
     solve_core(p, p->ws, p->st, f, u, R, false, hz::XS_STORE, conj_out);
     ck(cudaStreamSynchronize(p->st));
     return;
@@ -1105,7 +1106,7 @@ namespace {
 // or CUDA-core bulk transforms) with three solves each on workspace w and stream st, keep the
 // fastest; returns rb + 10 * tc of the choice.  f and out are device buffers of nrhs RHS.
 int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* out, int nrhs) {
-  const bool mixed = p->opts.precision == HZ_MIXED;
+  const bool mixed = p->opts.precision != HZ_FP64;
   const bool timing = p->timing;
   p->timing = false;
   cudaEvent_t e0, e1;
@@ -1249,7 +1250,7 @@ void batch_enqueue(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_
     const double2* f = reinterpret_cast<const double2*>(f_dev[i]);
     double2* u = reinterpret_cast<double2*>(u_dev[i]);
     double* nrm = b->norms + b->norm_off[i];
-    if (p->opts.precision == HZ_MIXED) {
+    if (p->opts.precision != HZ_FP64) {
       // first solve, its residual (with ||M f||), one correction, the final residual
       solve_core(p, w, st, f, u, R, true, hz::XS_STORE, 0);
       residual_enqueue(p, w, st, f, u, b->rho[l], nrm, R, 1);
@@ -1326,7 +1327,7 @@ void batch_run(hz_batch_t b, const hz_c128* const* f_dev, hz_c128* const* u_dev,
     for (int r = 0; r < R; ++r) fn2[r] = nrm[b->norm_off[i] + 2 * r + 1];
     for (int q = 0; q < 2 * R; ++q) fin[q] = nrm[b->norm_off[i] + 2 * R + q];
     double rel = residual_from_sums(fin, R, nullptr, fn2);
-    if (p->opts.precision == HZ_MIXED && rel > p->opts.rtol) {
+    if (p->opts.precision != HZ_FP64 && rel > p->opts.rtol) {
       // finish on the plan's own stream and workspace: more corrections, eagerly
       const double2* f = reinterpret_cast<const double2*>(f_dev[i]);
       double2* u = reinterpret_cast<double2*>(u_dev[i]);
@@ -1385,8 +1386,8 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
     if (!std::isfinite(layers->k2[L].re) || !std::isfinite(layers->k2[L].im)) return HZ_ERR_ARG;
     if (layers->sigma && !(layers->sigma[L] > 0.0 && std::isfinite(layers->sigma[L]))) return HZ_ERR_ARG;
   }
-  if (opts && (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED)) return HZ_ERR_ARG;
-  const bool mixed = opts && opts->precision == HZ_MIXED;
+  if (opts && (opts->precision < HZ_FP64 || opts->precision > HZ_MIXED_TF32)) return HZ_ERR_ARG;
+  const bool mixed = opts && opts->precision != HZ_FP64;
   int nbx = blocks ? blocks->nbx : 1, nby = blocks ? blocks->nby : 1;
   if (blocks && nbx == HZ_BLOCKS_AUTO) {
     if (blocks->x_iface) return HZ_ERR_ARG;
@@ -1516,7 +1517,7 @@ hz_status hz_sine_transform_host(int n, int dir, double scale, const hz_c128* in
 
 hz_status hz_plan_set_options(hz_plan_t p, const hz_options* opts) {
   if (!p || !opts) return HZ_ERR_ARG;
-  if (opts->precision != HZ_FP64 && opts->precision != HZ_MIXED) return HZ_ERR_ARG;
+  if (opts->precision < HZ_FP64 || opts->precision > HZ_MIXED_TF32) return HZ_ERR_ARG;
   p->opts = *opts;
   if (!(p->opts.rtol > 0)) p->opts.rtol = 1e-8;
   if (p->opts.max_refine < 0) p->opts.max_refine = 0;
@@ -1800,7 +1801,7 @@ hz_status hz_solve_perturbed(hz_plan_t p, const hz_c128* dk2_dev, const hz_c128*
                              double rtol, int max_iter, int restart, int* iters_out, double* relres_out) {
   if (!p || !dk2_dev || !f_dev || !u_dev || nrhs < 1 || !(rtol > 0.0) || max_iter < 1) return HZ_ERR_ARG;
   if (static_cast<const void*>(f_dev) == static_cast<const void*>(u_dev)) return HZ_ERR_ARG;
-  if (p->opts.precision == HZ_MIXED)
+  if (p->opts.precision != HZ_FP64)
     return perturbed_impl<float2>(p, dk2_dev, f_dev, u_dev, nrhs, rtol, max_iter, restart, iters_out, relres_out);
   return perturbed_impl<double2>(p, dk2_dev, f_dev, u_dev, nrhs, rtol, max_iter, restart, iters_out, relres_out);
 }

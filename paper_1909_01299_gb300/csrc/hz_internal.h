@@ -154,9 +154,10 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
 // err: device status word (set to HZ_ERR_TIMEOUT if a bounded wait gives up).
 // in32 / out32: the input / output are complex64 (float2) instead of complex128 (double2).
 // Returns false (nothing launched) for XS_ACCUM with a complex64 output.
+// products: 3 (3xTF32) or 1 (plain TF32).
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st);
+              cudaStream_t st, int products = 3);
 
 // FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
 // trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out

@@ -187,8 +187,10 @@ constexpr int RAW_BYTES = TC_M * RAW_ROWB;
 __host__ __device__ constexpr int nbstages(bool in32) { return in32 ? 3 : 2; }
 __host__ __device__ constexpr int raw_bytes(bool in32) { return in32 ? RAW_BYTES / 2 : RAW_BYTES; }
 
-// TI / TO: double2 (complex128) or float2 (complex64) input / output elements.
-template <typename TI, typename TO>
+// TI / TO: double2 (complex128) or float2 (complex64) input / output elements.  NP: TF32
+// products per chunk, 3 (3xTF32: A_hi B_hi + A_hi B_lo + A_lo B_hi) or 1 (plain TF32: A_hi B_hi,
+// the data's lo plane is neither formed nor read).
+template <typename TI, typename TO, int NP>
 __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM)
 xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* __restrict__ blocks,
                 const TCTile* __restrict__ tiles, const unsigned char* __restrict__ tmaps, int ntiles,
@@ -304,11 +306,11 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           h[e] = to_tf32(f[e]);
-          l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
+          if (NP == 3) l[e] = to_tf32(f[e] - __uint_as_float(h[e]));
         }
         const uint32_t off = swz64(r, c);
         st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
-        st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+        if (NP == 3) st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
     }
     int w2 = 1;
@@ -329,8 +331,10 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
         const uint64_t dbh = smem_desc_sw64(b_hi + koff), dbl = smem_desc_sw64(b_lo + koff);
         const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
         mma_tf32(tmem, dah, dbh, idesc, first);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+        if (NP == 3) {
+          mma_tf32(tmem, dah, dbl, idesc, 1u);
+          mma_tf32(tmem, dal, dbh, idesc, 1u);
+        }
       }
       mma_commit(&bars[s]);
       if (kc + 1 < nk) {
@@ -564,7 +568,9 @@ uint32_t xform_tc_idesc(int nt) { return idesc_tf32(nt); }
 
 template <typename TI, typename TO>
 void set_smem_attr() {
-  cudaFuncSetAttribute(xform_tc_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(xform_tc_kernel<TI, TO, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)xform_tc_smem(kTcMaxN, sizeof(TI) == 8));
+  cudaFuncSetAttribute(xform_tc_kernel<TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)xform_tc_smem(kTcMaxN, sizeof(TI) == 8));
 }
 
@@ -584,7 +590,7 @@ void xform_tc_prepare() {
 
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st) {
+              cudaStream_t st, int products) {
   if (out32 && store != XS_STORE) return false;          // accumulation needs a complex128 output
   if (!ts.d_tmaps) return false;
   const long long nrows = nplanes * (long long)rows_per_plane;
@@ -592,14 +598,21 @@ bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, i
   xform_tc_prepare();
   const long long ctas = ((nrows + TC_M - 1) / TC_M) * ts.ntiles;
   const size_t smem = xform_tc_smem(ts.nt_max, in32 != 0);
-#define HZ_TC_LAUNCH(TI, TO)                                                                          \
-  xform_tc_kernel<TI, TO><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                                 \
+#define HZ_TC_LAUNCH(TI, TO, NP)                                                                      \
+  xform_tc_kernel<TI, TO, NP><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                             \
       static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, ts.d_tiles, ts.d_tmaps,            \
       ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
-  if (in32 && out32) HZ_TC_LAUNCH(float2, float2);
-  else if (in32) HZ_TC_LAUNCH(float2, double2);
-  else if (out32) HZ_TC_LAUNCH(double2, float2);
-  else HZ_TC_LAUNCH(double2, double2);
+  if (products == 1) {
+    if (in32 && out32) HZ_TC_LAUNCH(float2, float2, 1);
+    else if (in32) HZ_TC_LAUNCH(float2, double2, 1);
+    else if (out32) HZ_TC_LAUNCH(double2, float2, 1);
+    else HZ_TC_LAUNCH(double2, double2, 1);
+  } else {
+    if (in32 && out32) HZ_TC_LAUNCH(float2, float2, 3);
+    else if (in32) HZ_TC_LAUNCH(float2, double2, 3);
+    else if (out32) HZ_TC_LAUNCH(double2, float2, 3);
+    else HZ_TC_LAUNCH(double2, double2, 3);
+  }
 #undef HZ_TC_LAUNCH
   count_launch();
   return true;

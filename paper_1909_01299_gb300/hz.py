@@ -16,7 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhz.so")
 
-HZ_FP64, HZ_MIXED = 0, 1
+HZ_FP64, HZ_MIXED, HZ_MIXED_TF32 = 0, 1, 2
+_PRECISION = {"fp64": HZ_FP64, "mixed": HZ_MIXED, "mixed_3xtf32": HZ_MIXED, "mixed_tf32": HZ_MIXED_TF32}
 
 
 class c128(ctypes.Structure):
@@ -149,8 +150,9 @@ def _stream_handle(stream):
 class Plan:
     """A solver plan (hz_plan_create): grid, layers, blocks and options.
 
-    precision: "fp64" (DFMA transforms) or "mixed" (FP32 transforms, FP64 z solves,
-    interface solves and refinement to `rtol`).
+    precision: "fp64" (DFMA transforms) or "mixed" (= "mixed_3xtf32"; FP32 transforms, the bulk
+    ones as three TF32 products on the tensor cores, FP64 z solves, interface solves and
+    refinement to `rtol`) or "mixed_tf32" (one TF32 product per bulk transform).
     """
 
     def __init__(self, hx, hy, hz, z_begin, k2, sigma=None, x_iface=None, y_iface=None,
@@ -173,8 +175,7 @@ class Plan:
         blk = hz_blocks(nbx, nby, None if xi is None or len(xi) == 0 else xi.ctypes.data,
                         None if yi is None or len(yi) == 0 else yi.ctypes.data)
         self.precision = precision
-        self._opts = hz_options(HZ_MIXED if precision == "mixed" else HZ_FP64, rtol, max_refine,
-                                _stream_handle(stream))
+        self._opts = hz_options(_PRECISION[precision], rtol, max_refine, _stream_handle(stream))
         h = _P()
         _check(_lib.hz_plan_create(ctypes.byref(g), ctypes.byref(lay), ctypes.byref(blk),
                                    ctypes.byref(self._opts), ctypes.byref(h)), "hz_plan_create")
@@ -203,7 +204,7 @@ class Plan:
     def set_options(self, precision=None, rtol=None, max_refine=None, stream=None):
         if precision is not None:
             self.precision = precision
-            self._opts.precision = HZ_MIXED if precision == "mixed" else HZ_FP64
+            self._opts.precision = _PRECISION[precision]
         if rtol is not None:
             self._opts.rtol = rtol
         if max_refine is not None:

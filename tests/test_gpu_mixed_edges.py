@@ -58,3 +58,22 @@ def test_mixed_blocks_wider_than_one_tile(hz, torch_cuda, kw):
 def test_one_and_two_z_planes(hz, torch_cuda, nz, precision):
     solve_and_check(hz, torch_cuda, W.tiny_pml(nx=23, ny=19, nz=nz, bx=2, by=3, rim=4, pml=2, nrhs=3),
                     precision)
+
+
+def test_single_product_tf32_mixed_precision(hz, torch_cuda):
+    # HZ_MIXED_TF32: one TF32 product per bulk transform (about 1e-3 per transform) reaches the
+    # same tolerance through more corrections than the 3xTF32 form
+    torch = torch_cuda
+    w = W.tiny_pml(70, 45, 33, 3, 2, rim=6, pml=3, nrhs=2)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    f = torch.from_numpy(w.f).cuda()
+    refinements = {}
+    for precision in ("mixed_tf32", "mixed"):
+        plan = hz.Plan.from_workload(w, precision=precision, rtol=1e-10, max_refine=20)
+        u = plan.solve(f).cpu().numpy()
+        info = plan.info()
+        assert info["tensor_cores"] == 1
+        assert info["rel_residual"] <= 1e-10
+        assert rel(u, ref) < TOLMIX
+        refinements[precision] = info["refinements"]
+    assert refinements["mixed_tf32"] > refinements["mixed"]
