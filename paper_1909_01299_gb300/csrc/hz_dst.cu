@@ -22,11 +22,13 @@
 // The post step runs in place: X_{2k} goes to position k and X_{2k+1} to position N - k
 // (X_1 stays at 0), and the store gathers the columns from those positions.
 //
-// Kernel layout: one CTA takes TM rows of one block; the rows are staged in shared memory
-// (odd row stride in 16-byte units, so that the threads of a warp, one row each, hit
-// distinct banks); the load, the pre step and the store are shared by all threads with
-// consecutive columns (coalesced); each thread then runs the FFT and the post step of its
-// own row.
+// Kernel layout: one CTA takes 32 rows of one block; the rows are staged in shared memory
+// (odd row stride in 16-byte units, so that threads on different rows hit distinct banks);
+// the load, the pre step and the store are shared by all threads with consecutive columns
+// (coalesced); four lanes of a warp then run the FFT stages and the post step of each row
+// (the post step's running sum as a four-lane scan).  About 43 KB of shared memory per CTA
+// keeps five CTAs (20 warps) on an SM, enough to keep the FP64 pipe busy while other CTAs
+// load or store.
 #include <algorithm>
 #include <cmath>
 
@@ -86,61 +88,13 @@ __host__ __device__ __forceinline__ void dft5(double2* a) {
   a[3] = make_double2(m2.x - n2.y, m2.y + n2.x);       // m2 + i n2
 }
 
-// One decimation-in-time stage of radix R over a row x of length N (element stride 1):
-// groups of L = M R; element q of group g, offset k, is x[g L + q M + k]; twiddles tw[k][q-1]
-// (k = 0 needs none).
-template <int R>
-__host__ __device__ __forceinline__ void fft_stage(double2* x, int N, int M, const double2* tw) {
-  const int L = M * R;
-  for (int g = 0; g < N; g += L) {
-    for (int k = 0; k < M; ++k) {
-      double2 a[R];
-      double2* p = x + g + k;
-#pragma unroll
-      for (int q = 0; q < R; ++q) a[q] = p[q * M];
-      if (k > 0) {
-#pragma unroll
-        for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[k * (R - 1) + q - 1]);
-      }
-      if (R == 2) dft2(a);
-      else if (R == 3) dft3(a);
-      else if (R == 4) dft4(a);
-      else dft5(a);
-#pragma unroll
-      for (int q = 0; q < R; ++q) p[q * M] = a[q];
-    }
-  }
-}
+constexpr int kTM = 32;      // rows per CTA
+constexpr int kTPR = 4;      // threads per row in the FFT and post phases (lanes 4r..4r+3 of a warp)
+constexpr int kNT = kTM * kTPR;
 
-// All stages of the FFT of one row (input already digit-reversed).
-__host__ __device__ __forceinline__ void fft_row(double2* x, const DstBlock& b, const double2* tw) {
-  const int N = b.n + 1;
-  int M = 1;
-  int off = 0;
-  for (int s = 0; s < b.nst; ++s) {
-    const int r = b.rad[s];
-    switch (r) {
-      case 2: fft_stage<2>(x, N, M, tw + off); break;
-      case 3: fft_stage<3>(x, N, M, tw + off); break;
-      case 4: fft_stage<4>(x, N, M, tw + off); break;
-      default: fft_stage<5>(x, N, M, tw + off); break;
-    }
-    off += M * (r - 1);
-    M *= r;
-  }
-}
-
-// In place: Y -> X with X_1 at 0, X_{2k} at k, X_{2k+1} at N - k (k = 1..(N-1)/2).
-__host__ __device__ __forceinline__ void post_row(double2* x, int N) {
-  double2 acc = x[0];
-  for (int k = 1; 2 * k < N; ++k) {
-    const double2 yk = x[k], ym = x[N - k];
-    acc.x += yk.x + ym.x;
-    acc.y += yk.y + ym.y;
-    x[k] = make_double2(ym.y - yk.y, yk.x - ym.x);     // i (Y_k - Y_{N-k})
-    x[N - k] = acc;
-  }
-}
+// Odd row stride (16-byte units) for rows of N values: threads of a warp on different rows
+// then address distinct shared-memory banks.
+__host__ __device__ __forceinline__ int row_stride(int N) { return N | 1; }
 
 // y_j and y_{N-j} from x_j and x_{N-j} (equal when 2 j = N).
 __host__ __device__ __forceinline__ void pre_pair(double2 xj, double2 xm, double p, double q, double2* yj,
@@ -162,12 +116,104 @@ int sym_col(int m, int n) {
   return (m % 2 == 1) ? (m - 1) / 2 : ns + m / 2 - 1;
 }
 
-constexpr int kTM = 64;      // rows per CTA (one thread each in the FFT phase)
-constexpr int kNT = 128;     // threads per CTA (all of them load and store)
+// One radix-R stage of a row shared by its kTPR threads (sub = 0..kTPR-1), butterflies
+// sub, sub + kTPR, ... (groups of L = M R; element q of group g, offset k, is x[g L + q M + k];
+// twiddles tw[k][q-1], none for k = 0).  The caller synchronises the row's lanes after the
+// stage; the host reference calls it for every sub in turn.
+template <int R>
+__host__ __device__ __forceinline__ void fft_stage_par(double2* x, int N, int M, const double2* tw, int sub) {
+  const int L = M * R;
+  const int nb = N / R;
+  for (int t = sub; t < nb; t += kTPR) {
+    const int g = t / M, k = t - g * M;
+    double2 a[R];
+    double2* p = x + g * L + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[q] = p[q * M];
+    if (k > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[k * (R - 1) + q - 1]);
+    }
+    if (R == 2) dft2(a);
+    else if (R == 3) dft3(a);
+    else if (R == 4) dft4(a);
+    else dft5(a);
+#pragma unroll
+    for (int q = 0; q < R; ++q) p[q * M] = a[q];
+  }
+}
 
-// Odd row stride (16-byte units) for rows of N values: threads of a warp, one row each,
-// then address distinct shared-memory banks.
-__host__ __device__ __forceinline__ int row_stride(int N) { return N | 1; }
+__host__ __device__ __forceinline__ void fft_stage_any(double2* x, int N, int M, int r, const double2* tw,
+                                                       int sub) {
+  switch (r) {
+    case 2: fft_stage_par<2>(x, N, M, tw, sub); break;
+    case 3: fft_stage_par<3>(x, N, M, tw, sub); break;
+    case 4: fft_stage_par<4>(x, N, M, tw, sub); break;
+    default: fft_stage_par<5>(x, N, M, tw, sub); break;
+  }
+}
+
+// The post step, shared by the kTPR threads of a row: each takes a contiguous range of pairs
+// k; part A writes X_{2k} = i (Y_k - Y_{N-k}) at k and the pair sum at N - k and returns the
+// range's total; part B adds the running sum (Y_0 + the totals of the lower ranges, excl) in place.
+__host__ __device__ __forceinline__ void post_range(int N, int sub, int* k0, int* k1) {
+  const int K = (N - 1) / 2;
+  const int chunk = (K + kTPR - 1) / kTPR;
+  *k0 = 1 + sub * chunk;
+  *k1 = K < *k0 + chunk - 1 ? K : *k0 + chunk - 1;
+}
+__host__ __device__ __forceinline__ double2 post_part_a(double2* x, int N, int sub) {
+  int k0, k1;
+  post_range(N, sub, &k0, &k1);
+  double2 part = make_double2(0.0, 0.0);
+  for (int k = k0; k <= k1; ++k) {
+    const double2 yk = x[k], ym = x[N - k];
+    const double2 sk = cadd(yk, ym);
+    part = cadd(part, sk);
+    x[k] = make_double2(ym.y - yk.y, yk.x - ym.x);
+    x[N - k] = sk;
+  }
+  return part;
+}
+__host__ __device__ __forceinline__ void post_part_b(double2* x, int N, int sub, double2 excl) {
+  int k0, k1;
+  post_range(N, sub, &k0, &k1);
+  double2 acc = cadd(x[0], excl);
+  for (int k = k0; k <= k1; ++k) {
+    acc = cadd(acc, x[N - k]);
+    x[N - k] = acc;
+  }
+}
+
+__device__ __forceinline__ void fft_row_par(double2* x, const DstBlock& b, const double2* tw, int sub) {
+  const int N = b.n + 1;
+  int M = 1, off = 0;
+  for (int s = 0; s < b.nst; ++s) {
+    const int r = b.rad[s];
+    fft_stage_any(x, N, M, r, tw + off, sub);
+    __syncwarp();
+    off += M * (r - 1);
+    M *= r;
+  }
+}
+
+__device__ __forceinline__ void post_row_par(double2* x, int N, int sub) {
+  const double2 part = post_part_a(x, N, sub);
+  double2 excl = make_double2(0.0, 0.0);            // sum of the lower lanes' parts
+  double2 incl = part;
+#pragma unroll
+  for (int o = 1; o < kTPR; o <<= 1) {
+    const double ox = __shfl_up_sync(0xffffffffu, incl.x, o, kTPR);
+    const double oy = __shfl_up_sync(0xffffffffu, incl.y, o, kTPR);
+    if (sub >= o) {
+      incl.x += ox;
+      incl.y += oy;
+      excl.x += ox;
+      excl.y += oy;
+    }
+  }
+  post_part_b(x, N, sub, excl);
+}
 
 __global__ void __launch_bounds__(kNT)
 dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstBlock* __restrict__ blocks,
@@ -202,7 +248,8 @@ dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstB
   const int* __restrict__ gin = rev + N;
   const int* __restrict__ src = gin + N;
   const double* __restrict__ pq = coef + b.coff;
-  // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} digit-reversed
+  // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} digit-reversed (rows that
+  // are skipped or past the end transform zeros and are not stored)
   const int np = N / 2;
 #pragma unroll 4
   for (int e = threadIdx.x; e < kTM * np; e += kNT) {
@@ -220,11 +267,12 @@ dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstB
     if (N - j != j) x[rev[N - j]] = ym;
   }
   __syncthreads();
-  // phase 2: FFT and post step of one row per thread
-  if (threadIdx.x < kTM && s_ok[threadIdx.x]) {
-    double2* x = sm + threadIdx.x * stride;
-    fft_row(x, b, tw);
-    post_row(x, N);
+  // phase 2: FFT and post step, kTPR lanes per row
+  {
+    double2* x = sm + (threadIdx.x / kTPR) * stride;
+    const int sub = threadIdx.x % kTPR;
+    fft_row_par(x, b, tw, sub);
+    post_row_par(x, N, sub);
   }
   __syncthreads();
   // phase 3: store (row-contiguous, or transposed with the rows of a column contiguous)
@@ -345,8 +393,20 @@ bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out) {
     x[rev[j]] = yj;
     if (N - j != j) x[rev[N - j]] = ym;
   }
-  fft_row(x.data(), b, tw.data() + b.tw_off);
-  post_row(x.data(), N);
+  // the kernel's per-lane code, the lanes of a row taken in turn
+  int M = 1, off = 0;
+  for (int st = 0; st < b.nst; ++st) {
+    for (int sub = 0; sub < kTPR; ++sub) fft_stage_any(x.data(), N, M, b.rad[st], tw.data() + b.tw_off + off, sub);
+    off += M * (b.rad[st] - 1);
+    M *= b.rad[st];
+  }
+  double2 part[kTPR];
+  for (int sub = 0; sub < kTPR; ++sub) part[sub] = post_part_a(x.data(), N, sub);
+  double2 excl = make_double2(0.0, 0.0);
+  for (int sub = 0; sub < kTPR; ++sub) {
+    post_part_b(x.data(), N, sub, excl);
+    excl = cadd(excl, part[sub]);
+  }
   for (int c = 0; c < n; ++c) out[c] = x[src[c]];
   return true;
 }
