@@ -126,8 +126,8 @@ typedef struct {
   int tensor_cores;          /* 1: the mixed path's bulk transforms run on the tensor
                                 cores (tcgen05, 3xTF32) with complex64 mode-space data;
                                 0: FP32 CUDA-core transforms on complex128 data          */
-  int fast_sine;             /* FP64 path: 1 when uniform blocks use the FFT-based sine
-                                transform (hz_plan_set_fast_sine), 0 otherwise           */
+  int fast_sine;             /* 1 when uniform blocks use the FFT-based sine transform
+                                (hz_plan_set_fast_sine), 0 otherwise                     */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's
@@ -178,12 +178,13 @@ hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
  * rhs_per_thread + 10 * tensor_cores + 100 * fast_sine. */
 hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
 
-/* FP64 path: transform the uniform blocks (all steps equal and real, so that the block's
- * eigenvectors are the discrete sines and its tables a scaled DST-I) by the FFT-based sine
- * transform, the fast transform of the uniform core in the cost estimate of Sec. 2
- * (enable = 1, the default: one complex FFT of length n + 1 per row, for blocks whose
- * n + 1 <= 128 has no prime factor above 5), or by the folded dense product (enable = 0).
- * Both give the FP64 result; the autotuner times both. */
+/* Transform the uniform blocks (all steps equal and real, so that the block's eigenvectors
+ * are the discrete sines and its tables a scaled DST-I) by the FFT-based sine transform, the
+ * fast transform of the uniform core in the cost estimate of Sec. 2 (enable = 1, the
+ * default: one complex FFT of length n + 1 per row, for blocks whose n + 1 <= 128 has no
+ * prime factor above 5), or by the dense product (enable = 0: the folded FP64 product on the
+ * FP64 path, the tensor cores on the mixed path).  The FP64 path computes it in FP64, the
+ * mixed path's bulk transforms in FP32; the autotuner times both choices. */
 hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
 
 /* Host-only helper (no device memory is touched): the fast sine transform that the plan

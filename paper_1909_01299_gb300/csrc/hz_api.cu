@@ -350,9 +350,10 @@ template <typename Get>
 // sym[b] marks a uniform block (sine pairs, symmetric modes first); dir = 1 for a forward
 // table (rows = nodes), 2 for an inverse table (rows = modes).  The table is stored whole
 // either way; symmetric blocks read half of it (see the row-transform kernels).
+// fast[b]: block b takes the fast sine transform (a uniform block, dst_supported(size[b])).
 void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>& start,
                 const std::vector<int>& size, const std::vector<int>& real, const std::vector<int>& sym,
-                int dir, Get get) {
+                int dir, const std::vector<char>& fastb, Get get) {
   xs.ncols = ncols;
   xs.nblocks = (int)start.size();
   std::vector<hz::XBlock> blocks;
@@ -414,7 +415,8 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
   const double pi = 3.14159265358979323846;
   for (int b = 0; b < xs.nblocks; ++b) {
     const hz::XBlock& xb = blocks[b];
-    if (!xb.sym) continue;
+    if (!fastb[b]) continue;
+    if (!xb.sym) throw Fail{HZ_ERR_EIG};
     const int n = xb.size, N = n + 1, ns = (n + 1) / 2;
     auto mode = [&](int c) { return c < ns ? 2 * c + 1 : 2 * (c - ns) + 2; };
     const double S = get(b, 0, 0).real() / std::sin(pi / N);
@@ -425,11 +427,12 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
         const double ref = S * std::sin((double)(jm % (2 * N)) * pi / N);
         dev = std::max(dev, std::abs(get(b, a, c) - cd(ref)));
       }
-    if (!(dev <= 1e-13 * std::abs(S))) continue;
-    if (hz::dst_plan_block(n, xb.start, dir, S, dblk, didx, dcoef, dtw)) {
-      fast[b] = 1;
-      xs.dst.nmax = std::max(xs.dst.nmax, N);
-    }
+    // the closed-form sine table and the fast transform must agree (the tensor-core tile subset
+    // already leaves this block out)
+    if (!(dev <= 1e-13 * std::abs(S)) || !hz::dst_plan_block(n, xb.start, dir, S, dblk, didx, dcoef, dtw))
+      throw Fail{HZ_ERR_EIG};
+    fast[b] = 1;
+    xs.dst.nmax = std::max(xs.dst.nmax, N);
   }
   std::vector<hz::XTile> tiles64;
   for (const auto& t : tiles)
@@ -442,6 +445,11 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
     xs.dst.d_idx = upload(p, didx);
     xs.dst.d_coef = upload(p, dcoef);
     xs.dst.d_tw = upload(p, dtw);
+    std::vector<float> c32(dcoef.begin(), dcoef.end());
+    std::vector<float2> t32(dtw.size());
+    for (size_t i = 0; i < dtw.size(); ++i) t32[i] = make_float2((float)dtw[i].x, (float)dtw[i].y);
+    xs.dst.d_coef32 = upload(p, c32);
+    xs.dst.d_tw32 = upload(p, t32);
     p->has_dst = true;
   }
 }
@@ -449,7 +457,7 @@ void make_xform(hz_plan_t p, hz::XformSet& xs, int ncols, const std::vector<int>
 // Tensor-core tables of a block-diagonal transform: tab(b)[a][c] = get(b, a, c).
 template <typename Get>
 void make_tc(hz_plan_t p, hz::TCSet& ts, int ncols, const std::vector<int>& start,
-             const std::vector<int>& size, Get get) {
+             const std::vector<int>& size, const std::vector<char>& fastb, Get get) {
   std::vector<float> tab;
   std::vector<hz::TCBlock> blocks(start.size());
   std::vector<hz::TCTile> tiles;
@@ -470,19 +478,32 @@ void make_tc(hz_plan_t p, hz::TCSet& ts, int ncols, const std::vector<int>& star
   std::vector<unsigned char> maps;
   if (hz::tc_encode_tmaps(ts.d_tab, blocks, tiles, maps)) ts.d_tmaps = upload(p, maps);
   else p->use_tc = p->tc_ok = false;   // no tensor maps: the mixed path runs the SIMT FP32 transforms
+  std::vector<hz::TCTile> nf;
+  for (const auto& t : tiles)
+    if (!fastb[t.blk]) nf.push_back(t);
+  ts.ntiles_nf = (int)nf.size();
+  if (!nf.empty() && p->tc_ok) {
+    std::vector<unsigned char> maps_nf;
+    ts.d_tiles_nf = upload(p, nf);
+    if (hz::tc_encode_tmaps(ts.d_tab, blocks, nf, maps_nf)) ts.d_tmaps_nf = upload(p, maps_nf);
+    else p->use_tc = p->tc_ok = false;
+  }
 }
 
 void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global) {
   const int n = A.n, nI = (int)A.iface.size();
-  make_tc(p, D.tfwd, n, A.bstart, A.bsize, [&](int b, int a, int c) {
+  // uniform blocks whose width suits the FFT take the fast sine transform (FP64 and mixed paths)
+  std::vector<char> fastb(A.nb, 0);
+  for (int b = 0; b < A.nb; ++b) fastb[b] = (A.bsym[b] && A.breal[b] && hz::dst_supported(A.bsize[b])) ? 1 : 0;
+  make_tc(p, D.tfwd, n, A.bstart, A.bsize, fastb, [&](int b, int a, int c) {
     return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
   });
-  make_tc(p, D.tinv, n, A.bstart, A.bsize,
+  make_tc(p, D.tinv, n, A.bstart, A.bsize, fastb,
           [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
-  make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, A.bsym, 1, [&](int b, int a, int c) {
+  make_xform(p, D.fwd, n, A.bstart, A.bsize, A.breal, A.bsym, 1, fastb, [&](int b, int a, int c) {
     return A.mh[A.bstart[b] + a] * A.bW[b][(size_t)a * A.bsize[b] + c];
   });
-  make_xform(p, D.inv, n, A.bstart, A.bsize, A.breal, A.bsym, 2,
+  make_xform(p, D.inv, n, A.bstart, A.bsize, A.breal, A.bsym, 2, fastb,
              [&](int b, int a, int c) { return A.bW[b][(size_t)c * A.bsize[b] + a]; });
   std::vector<cd> lam_b(n, cd(0)), lam_g(n, cd(0));
   std::vector<signed char> skip(n, 0);
@@ -491,8 +512,9 @@ void build_axis_dev(hz_plan_t p, const AxisPlan& A, AxisDev& D, bool need_global
     for (int a = 0; a < A.bsize[b]; ++a) lam_b[A.bstart[b] + a] = A.blam[b][a];
   if (need_global) {
     std::vector<int> s0{0}, sn{n}, gr{A.greal}, gs{A.gsym};
-    make_xform(p, D.gfwd, n, s0, sn, gr, gs, 1, [&](int, int a, int c) { return A.gW[(size_t)a * n + c]; });
-    make_xform(p, D.ginv, n, s0, sn, gr, gs, 2, [&](int, int a, int c) { return A.gW[(size_t)c * n + a]; });
+    std::vector<char> gf{(char)((A.gsym && A.greal && hz::dst_supported(n)) ? 1 : 0)};
+    make_xform(p, D.gfwd, n, s0, sn, gr, gs, 1, gf, [&](int, int a, int c) { return A.gW[(size_t)a * n + c]; });
+    make_xform(p, D.ginv, n, s0, sn, gr, gs, 2, gf, [&](int, int a, int c) { return A.gW[(size_t)c * n + a]; });
     lam_g = A.glam;
   }
   D.lam_b = upload_c(p, lam_b);
@@ -798,8 +820,12 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   auto bulk = [&](const hz::XformSet& xs, const hz::TCSet& ts, const void* in, int in32, void* out, int out32,
                   int rpp, int trans, int store_mode, int conj, const signed char* skip) {
     if (in32 || out32 || (lo && p->use_tc && !conj)) {
+      // uniform blocks by the FP32 fast sine transform, the others on the tensor cores
+      const bool fs = p->fast_sine && xs.dst.nblk > 0 && (in32 || out32);
+      if (fs && !hz::dst_f32(xs.dst, in, in32, out, out32, rpp, planes, xs.ncols, trans, store_mode, skip, st))
+        throw Fail{HZ_ERR_ARG};
       if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st,
-                        p->opts.precision == HZ_MIXED_TF32 ? 1 : 3))
+                        p->opts.precision == HZ_MIXED_TF32 ? 1 : 3, fs))
         throw Fail{HZ_ERR_ARG};
     } else if (!lo) {
       hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
@@ -1116,8 +1142,8 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   int best_rb = p->zs_rb;
   bool best_tc = p->use_tc;
   bool best_fs = p->fast_sine;
-  const int fs_lo = (!mixed && p->has_dst) ? 0 : (p->fast_sine ? 1 : 0);
-  const int fs_hi = (!mixed && p->has_dst) ? 1 : fs_lo;
+  const int fs_lo = p->has_dst ? 0 : (p->fast_sine ? 1 : 0);
+  const int fs_hi = p->has_dst ? 1 : fs_lo;
   for (int fs = fs_lo; fs <= fs_hi; ++fs)
   for (int rb = 1; rb <= 2; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {

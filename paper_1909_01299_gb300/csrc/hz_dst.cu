@@ -32,60 +32,82 @@
 #include <algorithm>
 #include <cmath>
 
+#include "hz_convert.cuh"
 #include "hz_internal.h"
 
 namespace hz {
 namespace {
 
-__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-// a * w (4 FP64 operations)
-__host__ __device__ __forceinline__ double2 cmulw(double2 a, double2 w) {
-  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+// Complex helpers over V = double2 (FP64 path) or float2 (mixed path), scalar type S.
+template <typename V> struct Scalar;
+template <> struct Scalar<double2> { using T = double; };
+template <> struct Scalar<float2> { using T = float; };
+template <typename V>
+__host__ __device__ __forceinline__ V mk(typename Scalar<V>::T x, typename Scalar<V>::T y) {
+  V r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+// a * w (4 operations)
+template <typename V> __host__ __device__ __forceinline__ V cmulw(V a, V w) {
+  return mk<V>(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
 }
 
 // r-point DFTs (exp(-2 pi i q q' / r)) of a[0..r-1], in place.
-__host__ __device__ __forceinline__ void dft2(double2* a) {
-  const double2 t = a[0];
+template <typename V> __host__ __device__ __forceinline__ void dft2(V* a) {
+  const V t = a[0];
   a[0] = cadd(t, a[1]);
   a[1] = csub(t, a[1]);
 }
 
-__host__ __device__ __forceinline__ void dft3(double2* a) {
-  const double c = 0.86602540378443864676;          // sin(2 pi / 3)
-  const double2 s = cadd(a[1], a[2]);
-  const double2 d = csub(a[1], a[2]);
-  const double2 m = make_double2(fma(-0.5, s.x, a[0].x), fma(-0.5, s.y, a[0].y));
+template <typename V> __host__ __device__ __forceinline__ void dft3(V* a) {
+  using S = typename Scalar<V>::T;
+  const S c = (S)0.86602540378443864676;            // sin(2 pi / 3)
+  const S h = (S)-0.5;
+  const V s = cadd(a[1], a[2]);
+  const V d = csub(a[1], a[2]);
+  const V m = mk<V>(fma(h, s.x, a[0].x), fma(h, s.y, a[0].y));
   a[0] = cadd(a[0], s);
   // X1 = m - i c d, X2 = m + i c d
-  a[1] = make_double2(fma(c, d.y, m.x), fma(-c, d.x, m.y));
-  a[2] = make_double2(fma(-c, d.y, m.x), fma(c, d.x, m.y));
+  a[1] = mk<V>(fma(c, d.y, m.x), fma(-c, d.x, m.y));
+  a[2] = mk<V>(fma(-c, d.y, m.x), fma(c, d.x, m.y));
 }
 
-__host__ __device__ __forceinline__ void dft4(double2* a) {
-  const double2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-  const double2 t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+template <typename V> __host__ __device__ __forceinline__ void dft4(V* a) {
+  const V t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  const V t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
   a[0] = cadd(t0, t2);
   a[2] = csub(t0, t2);
-  a[1] = make_double2(t1.x + t3.y, t1.y - t3.x);       // t1 - i t3
-  a[3] = make_double2(t1.x - t3.y, t1.y + t3.x);       // t1 + i t3
+  a[1] = mk<V>(t1.x + t3.y, t1.y - t3.x);              // t1 - i t3
+  a[3] = mk<V>(t1.x - t3.y, t1.y + t3.x);              // t1 + i t3
 }
 
-__host__ __device__ __forceinline__ void dft5(double2* a) {
-  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2 pi / 5), cos(4 pi / 5)
-  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2 pi / 5), sin(4 pi / 5)
-  const double2 a1 = cadd(a[1], a[4]), a2 = cadd(a[2], a[3]);
-  const double2 b1 = csub(a[1], a[4]), b2 = csub(a[2], a[3]);
-  const double2 x0 = a[0];
-  const double2 m1 = make_double2(fma(c2, a2.x, fma(c1, a1.x, x0.x)), fma(c2, a2.y, fma(c1, a1.y, x0.y)));
-  const double2 m2 = make_double2(fma(c1, a2.x, fma(c2, a1.x, x0.x)), fma(c1, a2.y, fma(c2, a1.y, x0.y)));
-  const double2 n1 = make_double2(fma(s2, b2.x, s1 * b1.x), fma(s2, b2.y, s1 * b1.y));
-  const double2 n2 = make_double2(fma(-s1, b2.x, s2 * b1.x), fma(-s1, b2.y, s2 * b1.y));
+template <typename V> __host__ __device__ __forceinline__ void dft5(V* a) {
+  using S = typename Scalar<V>::T;
+  const S c1 = (S)0.30901699437494742410, c2 = (S)-0.80901699437494742410;  // cos(2 pi / 5), cos(4 pi / 5)
+  const S s1 = (S)0.95105651629515357212, s2 = (S)0.58778525229247312917;   // sin(2 pi / 5), sin(4 pi / 5)
+  const V a1 = cadd(a[1], a[4]), a2 = cadd(a[2], a[3]);
+  const V b1 = csub(a[1], a[4]), b2 = csub(a[2], a[3]);
+  const V x0 = a[0];
+  const V m1 = mk<V>(fma(c2, a2.x, fma(c1, a1.x, x0.x)), fma(c2, a2.y, fma(c1, a1.y, x0.y)));
+  const V m2 = mk<V>(fma(c1, a2.x, fma(c2, a1.x, x0.x)), fma(c1, a2.y, fma(c2, a1.y, x0.y)));
+  const V n1 = mk<V>(fma(s2, b2.x, s1 * b1.x), fma(s2, b2.y, s1 * b1.y));
+  const V n2 = mk<V>(fma(-s1, b2.x, s2 * b1.x), fma(-s1, b2.y, s2 * b1.y));
   a[0] = cadd(cadd(x0, a1), a2);
-  a[1] = make_double2(m1.x + n1.y, m1.y - n1.x);       // m1 - i n1
-  a[4] = make_double2(m1.x - n1.y, m1.y + n1.x);       // m1 + i n1
-  a[2] = make_double2(m2.x + n2.y, m2.y - n2.x);       // m2 - i n2
-  a[3] = make_double2(m2.x - n2.y, m2.y + n2.x);       // m2 + i n2
+  a[1] = mk<V>(m1.x + n1.y, m1.y - n1.x);              // m1 - i n1
+  a[4] = mk<V>(m1.x - n1.y, m1.y + n1.x);              // m1 + i n1
+  a[2] = mk<V>(m2.x + n2.y, m2.y - n2.x);              // m2 - i n2
+  a[3] = mk<V>(m2.x - n2.y, m2.y + n2.x);              // m2 + i n2
+}
+
+// y_j and y_{N-j} from x_j and x_{N-j} (equal when 2 j = N).
+template <typename V, typename S>
+__host__ __device__ __forceinline__ void pre_pair(V xj, V xm, S p, S q, V* yj, V* ym) {
+  *yj = mk<V>(fma(p, xj.x, q * xm.x), fma(p, xj.y, q * xm.y));
+  *ym = mk<V>(fma(p, xm.x, q * xj.x), fma(p, xm.y, q * xj.y));
 }
 
 constexpr int kTM = 32;      // rows per CTA
@@ -96,12 +118,6 @@ constexpr int kNT = kTM * kTPR;
 // then address distinct shared-memory banks.
 __host__ __device__ __forceinline__ int row_stride(int N) { return N | 1; }
 
-// y_j and y_{N-j} from x_j and x_{N-j} (equal when 2 j = N).
-__host__ __device__ __forceinline__ void pre_pair(double2 xj, double2 xm, double p, double q, double2* yj,
-                                                  double2* ym) {
-  *yj = make_double2(fma(p, xj.x, q * xm.x), fma(p, xj.y, q * xm.y));
-  *ym = make_double2(fma(p, xm.x, q * xj.x), fma(p, xm.y, q * xj.y));
-}
 
 // Smem position of output index m (1..n) after post_row.
 int post_pos(int m, int N) { return m == 1 ? 0 : (m % 2 == 0 ? m / 2 : N - (m - 1) / 2); }
@@ -120,14 +136,14 @@ int sym_col(int m, int n) {
 // sub, sub + kTPR, ... (groups of L = M R; element q of group g, offset k, is x[g L + q M + k];
 // twiddles tw[k][q-1], none for k = 0).  The caller synchronises the row's lanes after the
 // stage; the host reference calls it for every sub in turn.
-template <int R>
-__host__ __device__ __forceinline__ void fft_stage_par(double2* x, int N, int M, const double2* tw, int sub) {
+template <int R, typename V>
+__host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int M, const V* tw, int sub) {
   const int L = M * R;
   const int nb = N / R;
   for (int t = sub; t < nb; t += kTPR) {
     const int g = t / M, k = t - g * M;
-    double2 a[R];
-    double2* p = x + g * L + k;
+    V a[R];
+    V* p = x + g * L + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) a[q] = p[q * M];
     if (k > 0) {
@@ -143,8 +159,8 @@ __host__ __device__ __forceinline__ void fft_stage_par(double2* x, int N, int M,
   }
 }
 
-__host__ __device__ __forceinline__ void fft_stage_any(double2* x, int N, int M, int r, const double2* tw,
-                                                       int sub) {
+template <typename V>
+__host__ __device__ __forceinline__ void fft_stage_any(V* x, int N, int M, int r, const V* tw, int sub) {
   switch (r) {
     case 2: fft_stage_par<2>(x, N, M, tw, sub); break;
     case 3: fft_stage_par<3>(x, N, M, tw, sub); break;
@@ -162,30 +178,33 @@ __host__ __device__ __forceinline__ void post_range(int N, int sub, int* k0, int
   *k0 = 1 + sub * chunk;
   *k1 = K < *k0 + chunk - 1 ? K : *k0 + chunk - 1;
 }
-__host__ __device__ __forceinline__ double2 post_part_a(double2* x, int N, int sub) {
+template <typename V>
+__host__ __device__ __forceinline__ V post_part_a(V* x, int N, int sub) {
   int k0, k1;
   post_range(N, sub, &k0, &k1);
-  double2 part = make_double2(0.0, 0.0);
+  V part = mk<V>(0, 0);
   for (int k = k0; k <= k1; ++k) {
-    const double2 yk = x[k], ym = x[N - k];
-    const double2 sk = cadd(yk, ym);
+    const V yk = x[k], ym = x[N - k];
+    const V sk = cadd(yk, ym);
     part = cadd(part, sk);
-    x[k] = make_double2(ym.y - yk.y, yk.x - ym.x);
+    x[k] = mk<V>(ym.y - yk.y, yk.x - ym.x);
     x[N - k] = sk;
   }
   return part;
 }
-__host__ __device__ __forceinline__ void post_part_b(double2* x, int N, int sub, double2 excl) {
+template <typename V>
+__host__ __device__ __forceinline__ void post_part_b(V* x, int N, int sub, V excl) {
   int k0, k1;
   post_range(N, sub, &k0, &k1);
-  double2 acc = cadd(x[0], excl);
+  V acc = cadd(x[0], excl);
   for (int k = k0; k <= k1; ++k) {
     acc = cadd(acc, x[N - k]);
     x[N - k] = acc;
   }
 }
 
-__device__ __forceinline__ void fft_row_par(double2* x, const DstBlock& b, const double2* tw, int sub) {
+template <typename V>
+__device__ __forceinline__ void fft_row_par(V* x, const DstBlock& b, const V* tw, int sub) {
   const int N = b.n + 1;
   int M = 1, off = 0;
   for (int s = 0; s < b.nst; ++s) {
@@ -197,14 +216,15 @@ __device__ __forceinline__ void fft_row_par(double2* x, const DstBlock& b, const
   }
 }
 
-__device__ __forceinline__ void post_row_par(double2* x, int N, int sub) {
-  const double2 part = post_part_a(x, N, sub);
-  double2 excl = make_double2(0.0, 0.0);            // sum of the lower lanes' parts
-  double2 incl = part;
+template <typename V>
+__device__ __forceinline__ void post_row_par(V* x, int N, int sub) {
+  const V part = post_part_a(x, N, sub);
+  V excl = mk<V>(0, 0);                              // sum of the lower lanes' parts
+  V incl = part;
 #pragma unroll
   for (int o = 1; o < kTPR; o <<= 1) {
-    const double ox = __shfl_up_sync(0xffffffffu, incl.x, o, kTPR);
-    const double oy = __shfl_up_sync(0xffffffffu, incl.y, o, kTPR);
+    const auto ox = __shfl_up_sync(0xffffffffu, incl.x, o, kTPR);
+    const auto oy = __shfl_up_sync(0xffffffffu, incl.y, o, kTPR);
     if (sub >= o) {
       incl.x += ox;
       incl.y += oy;
@@ -215,21 +235,30 @@ __device__ __forceinline__ void post_row_par(double2* x, int N, int sub) {
   post_part_b(x, N, sub, excl);
 }
 
-__global__ void __launch_bounds__(kNT)
-dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstBlock* __restrict__ blocks,
-           const int* __restrict__ idx, const double* __restrict__ coef, const double2* __restrict__ twg, int nblk,
-           long long nrows, int rows_per_plane, int ncols, int trans, int store, int conj_out,
+// Rows per CTA: 32 rows of complex128 or 64 of complex64 fill the same 43 KB.
+template <typename V> constexpr int rows_per_cta() { return sizeof(V) == 16 ? 32 : 64; }
+
+// V: arithmetic (double2: FP64 path; float2: mixed path, FP32 arithmetic); TI / TO: input and
+// output elements (complex128 or complex64; FP64 <-> FP32 by the integer conversions, which
+// keep the FP64 pipe free).  An accumulating store adds to a complex128 output in FP64.
+template <typename V, typename TI, typename TO>
+__global__ void __launch_bounds__(rows_per_cta<V>() * kTPR)
+dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __restrict__ blocks,
+           const int* __restrict__ idx, const typename Scalar<V>::T* __restrict__ coef, const V* __restrict__ twg,
+           int nblk, long long nrows, int rows_per_plane, int ncols, int trans, int store, int conj_out,
            const signed char* __restrict__ rowskip, int stride) {
-  extern __shared__ double2 sm[];
-  __shared__ int s_ok[kTM];
-  __shared__ long long s_base[kTM];         // first output element of the row (trans: the plane slot)
+  constexpr int TM = rows_per_cta<V>(), NT = TM * kTPR;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  __shared__ int s_ok[TM];
+  __shared__ long long s_base[TM];          // first output element of the row (trans: the plane slot)
   const int blk = (int)(blockIdx.x % (unsigned)nblk);
-  const long long row0 = (long long)(blockIdx.x / (unsigned)nblk) * kTM;
+  const long long row0 = (long long)(blockIdx.x / (unsigned)nblk) * TM;
   const DstBlock b = blocks[blk];
   const int n = b.n, N = n + 1;
-  double2* tw = sm + kTM * stride;
-  for (int t = threadIdx.x; t < b.ntw; t += kNT) tw[t] = twg[b.tw_off + t];
-  if (threadIdx.x < kTM) {
+  V* tw = sm + TM * stride;
+  for (int t = threadIdx.x; t < b.ntw; t += NT) tw[t] = twg[b.tw_off + t];
+  if (threadIdx.x < TM) {
     const long long row = row0 + threadIdx.x;
     int ok = row < nrows;
     long long base = 0;
@@ -241,80 +270,133 @@ dst_kernel(const double2* __restrict__ in, double2* __restrict__ out, const DstB
     }
     s_ok[threadIdx.x] = ok;
     s_base[threadIdx.x] = base;
-    sm[threadIdx.x * stride] = make_double2(0.0, 0.0);      // y_0 (digit-reversed position 0)
+    sm[threadIdx.x * stride] = mk<V>(0, 0);                 // y_0 (digit-reversed position 0)
   }
   __syncthreads();
   const int* __restrict__ rev = idx + b.ioff;
   const int* __restrict__ gin = rev + N;
   const int* __restrict__ src = gin + N;
-  const double* __restrict__ pq = coef + b.coff;
+  const typename Scalar<V>::T* __restrict__ pq = coef + b.coff;
   // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} digit-reversed (rows that
   // are skipped or past the end transform zeros and are not stored)
   const int np = N / 2;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < kTM * np; e += kNT) {
+  for (int e = threadIdx.x; e < TM * np; e += NT) {
     const int r = e / np, j = 1 + (e - r * np);
-    double2 xj = make_double2(0.0, 0.0), xm = xj;
+    V xj = mk<V>(0, 0), xm = xj;
     if (s_ok[r]) {
-      const double2* rp = in + (row0 + r) * (long long)ncols + b.start;
-      xj = rp[gin[j]];
-      xm = rp[gin[N - j]];
+      const TI* rp = in + (row0 + r) * (long long)ncols + b.start;
+      if constexpr (sizeof(V) == 16) {
+        xj = to_c128(rp[gin[j]]);
+        xm = to_c128(rp[gin[N - j]]);
+      } else {
+        xj = to_c64t(rp[gin[j]]);
+        xm = to_c64t(rp[gin[N - j]]);
+      }
     }
-    double2 yj, ym;
+    V yj, ym;
     pre_pair(xj, xm, pq[2 * j], pq[2 * j + 1], &yj, &ym);
-    double2* x = sm + r * stride;
+    V* x = sm + r * stride;
     x[rev[j]] = yj;
     if (N - j != j) x[rev[N - j]] = ym;
   }
   __syncthreads();
   // phase 2: FFT and post step, kTPR lanes per row
   {
-    double2* x = sm + (threadIdx.x / kTPR) * stride;
+    V* x = sm + (threadIdx.x / kTPR) * stride;
     const int sub = threadIdx.x % kTPR;
     fft_row_par(x, b, tw, sub);
     post_row_par(x, N, sub);
   }
   __syncthreads();
   // phase 3: store (row-contiguous, or transposed with the rows of a column contiguous)
-  for (int e = threadIdx.x; e < kTM * n; e += kNT) {
+  for (int e = threadIdx.x; e < TM * n; e += NT) {
     int r, c;
     if (trans) {
-      c = e / kTM;
-      r = e - c * kTM;
+      c = e / TM;
+      r = e - c * TM;
     } else {
       r = e / n;
       c = e - r * n;
     }
     if (!s_ok[r]) continue;
-    double2 v = sm[r * stride + src[c]];
+    V v = sm[r * stride + src[c]];
     if (conj_out) v.y = -v.y;
-    double2* p = out + s_base[r] + (long long)(b.start + c) * (trans ? rows_per_plane : 1);
-    if (store == XS_ACCUM) {
-      const double2 o = *p;
-      v.x += o.x;
-      v.y += o.y;
+    TO* p = out + s_base[r] + (long long)(b.start + c) * (trans ? rows_per_plane : 1);
+    if constexpr (sizeof(TO) == 16) {
+      double2 w = to_c128(v);
+      if (store == XS_ACCUM) {
+        const double2 o = *p;
+        w.x += o.x;
+        w.y += o.y;
+      }
+      *p = w;
+    } else {
+      *p = to_c64t(v);
     }
-    *p = v;
   }
 }
 
-size_t dst_smem(int nmax) { return sizeof(double2) * ((size_t)kTM * row_stride(nmax) + nmax); }
+template <typename V>
+size_t dst_smem(int nmax) { return sizeof(V) * ((size_t)rows_per_cta<V>() * row_stride(nmax) + nmax); }
+
+template <typename V, typename TI, typename TO>
+void dst_launch(const DstSet& ds, const V* tw, const typename Scalar<V>::T* coef, const TI* in, TO* out,
+                int rows_per_plane, long long nplanes, int ncols, int trans, int store, int conj_out,
+                const signed char* rowskip, cudaStream_t st) {
+  const long long nrows = nplanes * (long long)rows_per_plane;
+  if (nrows <= 0 || ds.nblk == 0) return;
+  constexpr int TM = rows_per_cta<V>();
+  const long long ctas = ((nrows + TM - 1) / TM) * ds.nblk;
+  dst_kernel<V, TI, TO><<<(unsigned)ctas, TM * kTPR, dst_smem<V>(ds.nmax), st>>>(
+      in, out, ds.d_blk, ds.d_idx, coef, tw, ds.nblk, nrows, rows_per_plane, ncols, trans, store, conj_out,
+      rowskip, row_stride(ds.nmax));
+  count_launch();
+}
+
+template <typename V, typename TI, typename TO>
+void set_attr(int nmax) {
+  cudaFuncSetAttribute(dst_kernel<V, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_smem<V>(nmax));
+}
 
 }  // namespace
 
 void dst_prepare(int nmax) {
-  cudaFuncSetAttribute(dst_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_smem(nmax));
+  set_attr<double2, double2, double2>(nmax);
+  set_attr<float2, double2, float2>(nmax);
+  set_attr<float2, float2, float2>(nmax);
+  set_attr<float2, float2, double2>(nmax);
 }
 
 void dst_f64(const DstSet& ds, const double2* in, double2* out, int rows_per_plane, long long nplanes, int ncols,
              int trans, int store, int conj_out, const signed char* rowskip, cudaStream_t st) {
-  const long long nrows = nplanes * (long long)rows_per_plane;
-  if (nrows <= 0 || ds.nblk == 0) return;
-  const long long ctas = ((nrows + kTM - 1) / kTM) * ds.nblk;
-  dst_kernel<<<(unsigned)ctas, kNT, dst_smem(ds.nmax), st>>>(in, out, ds.d_blk, ds.d_idx, ds.d_coef, ds.d_tw,
-                                                            ds.nblk, nrows, rows_per_plane, ncols, trans, store,
-                                                            conj_out, rowskip, row_stride(ds.nmax));
-  count_launch();
+  dst_launch<double2>(ds, ds.d_tw, ds.d_coef, in, out, rows_per_plane, nplanes, ncols, trans, store, conj_out,
+                      rowskip, st);
+}
+
+bool dst_f32(const DstSet& ds, const void* in, int in32, void* out, int out32, int rows_per_plane, long long nplanes,
+             int ncols, int trans, int store, const signed char* rowskip, cudaStream_t st) {
+  if (!ds.d_tw32 || (out32 && store != XS_STORE)) return false;
+  if (in32 && out32)
+    dst_launch<float2>(ds, ds.d_tw32, ds.d_coef32, static_cast<const float2*>(in), static_cast<float2*>(out),
+                       rows_per_plane, nplanes, ncols, trans, store, 0, rowskip, st);
+  else if (in32)
+    dst_launch<float2>(ds, ds.d_tw32, ds.d_coef32, static_cast<const float2*>(in), static_cast<double2*>(out),
+                       rows_per_plane, nplanes, ncols, trans, store, 0, rowskip, st);
+  else if (out32)
+    dst_launch<float2>(ds, ds.d_tw32, ds.d_coef32, static_cast<const double2*>(in), static_cast<float2*>(out),
+                       rows_per_plane, nplanes, ncols, trans, store, 0, rowskip, st);
+  else
+    return false;
+  return true;
+}
+
+bool dst_supported(int n) {
+  int N = n + 1;
+  if (n < 2 || N > kDstMaxN) return false;
+  for (int r : {2, 3, 5})
+    while (N % r == 0) N /= r;
+  return N == 1;
 }
 
 bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& blk, std::vector<int>& idx,

@@ -81,7 +81,12 @@ struct DstSet {
   int* d_idx = nullptr;
   double* d_coef = nullptr;
   double2* d_tw = nullptr;
+  float* d_coef32 = nullptr;      // FP32 copies (mixed path)
+  float2* d_tw32 = nullptr;
 };
+// Whether a uniform block of width n takes the fast transform (n >= 2, n + 1 <= kDstMaxN with no
+// prime factor above 5).
+bool dst_supported(int n);
 // Host: the fast-transform descriptor of a block of width n whose table is S sin(pi j m / N);
 // dir = 1: forward (natural nodes in, symmetric-modes-first out), 2: inverse (the reverse).
 // Appends to the index, coefficient and twiddle arrays; false if N has a prime factor > 5,
@@ -93,6 +98,10 @@ bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& 
 bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out);
 // Set the kernel's shared-memory limit for blocks up to N = nmax (current device, before any capture).
 void dst_prepare(int nmax);
+// Mixed path: the same transform in FP32 arithmetic; in32 / out32: complex64 input / output,
+// at least one of them (an accumulating store needs a complex128 output).  false: nothing launched.
+bool dst_f32(const DstSet& ds, const void* in, int in32, void* out, int out32, int rows_per_plane, long long nplanes,
+             int ncols, int trans, int store, const signed char* rowskip, cudaStream_t st);
 void dst_f64(const DstSet& ds, const double2* in, double2* out, int rows_per_plane, long long nplanes, int ncols,
              int trans, int store, int conj_out, const signed char* rowskip, cudaStream_t st);
 
@@ -139,6 +148,11 @@ struct TCSet {
   TCTile* d_tiles = nullptr;
   float* d_tab = nullptr;
   unsigned char* d_tmaps = nullptr;   // one 128-byte TMA tensor map per tile (its table rows)
+  // the tiles of the blocks without a fast sine transform, with their tensor maps (mixed path
+  // with fast_sine: the other blocks go through dst_f32)
+  int ntiles_nf = 0;
+  TCTile* d_tiles_nf = nullptr;
+  unsigned char* d_tmaps_nf = nullptr;
 };
 // Encode the TMA tensor maps of the tiles (tables already on the device at d_tab) into
 // 128-byte records; false if the driver offers no encoder or rejects a map.
@@ -154,10 +168,11 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
 // err: device status word (set to HZ_ERR_TIMEOUT if a bounded wait gives up).
 // in32 / out32: the input / output are complex64 (float2) instead of complex128 (double2).
 // Returns false (nothing launched) for XS_ACCUM with a complex64 output.
-// products: 3 (3xTF32) or 1 (plain TF32).
+// products: 3 (3xTF32) or 1 (plain TF32).  skip_fast: only the tiles of the blocks without a
+// fast sine transform.
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st, int products = 3);
+              cudaStream_t st, int products = 3, bool skip_fast = false);
 
 // FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
 // trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out

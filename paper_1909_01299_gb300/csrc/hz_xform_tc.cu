@@ -590,18 +590,21 @@ void xform_tc_prepare() {
 
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st, int products) {
+              cudaStream_t st, int products, bool skip_fast) {
   if (out32 && store != XS_STORE) return false;          // accumulation needs a complex128 output
-  if (!ts.d_tmaps) return false;
+  const TCTile* tiles = skip_fast ? ts.d_tiles_nf : ts.d_tiles;
+  const unsigned char* tmaps = skip_fast ? ts.d_tmaps_nf : ts.d_tmaps;
+  const int ntiles = skip_fast ? ts.ntiles_nf : ts.ntiles;
   const long long nrows = nplanes * (long long)rows_per_plane;
-  if (nrows <= 0 || ts.ntiles == 0) return true;
+  if (nrows <= 0 || ntiles == 0) return true;
+  if (!tmaps) return false;
   xform_tc_prepare();
-  const long long ctas = ((nrows + TC_M - 1) / TC_M) * ts.ntiles;
+  const long long ctas = ((nrows + TC_M - 1) / TC_M) * ntiles;
   const size_t smem = xform_tc_smem(ts.nt_max, in32 != 0);
 #define HZ_TC_LAUNCH(TI, TO, NP)                                                                      \
   xform_tc_kernel<TI, TO, NP><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                             \
-      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, ts.d_tiles, ts.d_tmaps,            \
-      ts.ntiles, nrows, rows_per_plane, ts.ncols, trans, store, rowskip, err)
+      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, tiles, tmaps, ntiles, nrows,          \
+      rows_per_plane, ts.ncols, trans, store, rowskip, err)
   if (products == 1) {
     if (in32 && out32) HZ_TC_LAUNCH(float2, float2, 1);
     else if (in32) HZ_TC_LAUNCH(float2, double2, 1);
