@@ -16,11 +16,12 @@
 // instructions per transformed value: about 4 (pre) + 20-27 (FFT, N = 80 or 81) + 3 (post)
 // against n for the folded dense product.
 //
-// The FFT is the iterative mixed-radix decimation in time: the pre step writes y_j to its
-// digit-reversed position, and stage s (radix r, sub-transforms of length M = r_1 .. r_{s-1})
-// multiplies element q of each group by exp(-2 pi i q k / (M r)) and applies an r-point DFT.
-// The post step runs in place: X_{2k} goes to position k and X_{2k+1} to position N - k
-// (X_1 stays at 0), and the store gathers the columns from those positions.
+// The FFT is the iterative mixed-radix decimation in frequency: the pre step writes y_j in
+// natural order (consecutive lanes on consecutive positions, free of bank conflicts), stage s
+// (radix r, sub-transforms of length L = N / (r_1 .. r_{s-1})) applies an r-point DFT and
+// multiplies output q by exp(-2 pi i j1 q / L), and Y_k ends at the digit-reversed position
+// pos[k].  The post step runs in place: X_{2k} replaces Y_k and X_{2k+1} replaces Y_{N-k}
+// (X_1 = Y_0 stays at 0), and the store gathers the columns from those positions.
 //
 // Kernel layout: one CTA takes 32 rows of one block; the rows are staged in shared memory
 // (odd row stride in 16-byte units, so that threads on different rows hit distinct banks);
@@ -119,9 +120,6 @@ constexpr int kNT = kTM * kTPR;
 __host__ __device__ __forceinline__ int row_stride(int N) { return N | 1; }
 
 
-// Smem position of output index m (1..n) after post_row.
-int post_pos(int m, int N) { return m == 1 ? 0 : (m % 2 == 0 ? m / 2 : N - (m - 1) / 2); }
-
 // Mode m of column c in the symmetric-modes-first order of a uniform block (and back).
 int sym_mode(int c, int n) {
   const int ns = (n + 1) / 2;
@@ -132,46 +130,48 @@ int sym_col(int m, int n) {
   return (m % 2 == 1) ? (m - 1) / 2 : ns + m / 2 - 1;
 }
 
-// One radix-R stage of a row shared by its kTPR threads (sub = 0..kTPR-1), butterflies
-// sub, sub + kTPR, ... (groups of L = M R; element q of group g, offset k, is x[g L + q M + k];
-// twiddles tw[k][q-1], none for k = 0).  The caller synchronises the row's lanes after the
-// stage; the host reference calls it for every sub in turn.
+// One radix-R decimation-in-frequency stage of a row shared by its kTPR threads (sub =
+// 0..kTPR-1), butterflies sub, sub + kTPR, ...: sub-transforms of length L, M = L / R; element q
+// of butterfly (b, j1) is x[b L + j1 + q M]; after the R-point DFT output q is multiplied by
+// exp(-2 pi i j1 q / L) (tw[j1][q-1]; none for j1 = 0).  The caller synchronises the row's lanes
+// after the stage; the host reference calls it for every sub in turn.
 template <int R, typename V>
-__host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int M, const V* tw, int sub) {
-  const int L = M * R;
+__host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int L, const V* tw, int sub) {
+  const int M = L / R;
   const int nb = N / R;
   for (int t = sub; t < nb; t += kTPR) {
-    const int g = t / M, k = t - g * M;
+    const int blk = t / M, j1 = t - blk * M;
     V a[R];
-    V* p = x + g * L + k;
+    V* p = x + blk * L + j1;
 #pragma unroll
     for (int q = 0; q < R; ++q) a[q] = p[q * M];
-    if (k > 0) {
-#pragma unroll
-      for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[k * (R - 1) + q - 1]);
-    }
     if (R == 2) dft2(a);
     else if (R == 3) dft3(a);
     else if (R == 4) dft4(a);
     else dft5(a);
+    if (j1 > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[j1 * (R - 1) + q - 1]);
+    }
 #pragma unroll
     for (int q = 0; q < R; ++q) p[q * M] = a[q];
   }
 }
 
 template <typename V>
-__host__ __device__ __forceinline__ void fft_stage_any(V* x, int N, int M, int r, const V* tw, int sub) {
+__host__ __device__ __forceinline__ void fft_stage_any(V* x, int N, int L, int r, const V* tw, int sub) {
   switch (r) {
-    case 2: fft_stage_par<2>(x, N, M, tw, sub); break;
-    case 3: fft_stage_par<3>(x, N, M, tw, sub); break;
-    case 4: fft_stage_par<4>(x, N, M, tw, sub); break;
-    default: fft_stage_par<5>(x, N, M, tw, sub); break;
+    case 2: fft_stage_par<2>(x, N, L, tw, sub); break;
+    case 3: fft_stage_par<3>(x, N, L, tw, sub); break;
+    case 4: fft_stage_par<4>(x, N, L, tw, sub); break;
+    default: fft_stage_par<5>(x, N, L, tw, sub); break;
   }
 }
 
 // The post step, shared by the kTPR threads of a row: each takes a contiguous range of pairs
-// k; part A writes X_{2k} = i (Y_k - Y_{N-k}) at k and the pair sum at N - k and returns the
-// range's total; part B adds the running sum (Y_0 + the totals of the lower ranges, excl) in place.
+// k; part A writes X_{2k} = i (Y_k - Y_{N-k}) in place of Y_k and the pair sum in place of
+// Y_{N-k} and returns the range's total; part B adds the running sum (Y_0 + the totals of the
+// lower ranges, excl) in place.  pos[k]: where the FFT left Y_k (digit-reversed order).
 __host__ __device__ __forceinline__ void post_range(int N, int sub, int* k0, int* k1) {
   const int K = (N - 1) / 2;
   const int chunk = (K + kTPR - 1) / kTPR;
@@ -179,46 +179,48 @@ __host__ __device__ __forceinline__ void post_range(int N, int sub, int* k0, int
   *k1 = K < *k0 + chunk - 1 ? K : *k0 + chunk - 1;
 }
 template <typename V>
-__host__ __device__ __forceinline__ V post_part_a(V* x, int N, int sub) {
+__host__ __device__ __forceinline__ V post_part_a(V* x, const int* pos, int N, int sub) {
   int k0, k1;
   post_range(N, sub, &k0, &k1);
   V part = mk<V>(0, 0);
   for (int k = k0; k <= k1; ++k) {
-    const V yk = x[k], ym = x[N - k];
+    const int pk = pos[k], pm = pos[N - k];
+    const V yk = x[pk], ym = x[pm];
     const V sk = cadd(yk, ym);
     part = cadd(part, sk);
-    x[k] = mk<V>(ym.y - yk.y, yk.x - ym.x);
-    x[N - k] = sk;
+    x[pk] = mk<V>(ym.y - yk.y, yk.x - ym.x);
+    x[pm] = sk;
   }
   return part;
 }
 template <typename V>
-__host__ __device__ __forceinline__ void post_part_b(V* x, int N, int sub, V excl) {
+__host__ __device__ __forceinline__ void post_part_b(V* x, const int* pos, int N, int sub, V excl) {
   int k0, k1;
   post_range(N, sub, &k0, &k1);
-  V acc = cadd(x[0], excl);
+  V acc = cadd(x[0], excl);                        // Y_0 sits at position 0
   for (int k = k0; k <= k1; ++k) {
-    acc = cadd(acc, x[N - k]);
-    x[N - k] = acc;
+    const int pm = pos[N - k];
+    acc = cadd(acc, x[pm]);
+    x[pm] = acc;
   }
 }
 
 template <typename V>
 __device__ __forceinline__ void fft_row_par(V* x, const DstBlock& b, const V* tw, int sub) {
   const int N = b.n + 1;
-  int M = 1, off = 0;
+  int L = N, off = 0;
   for (int s = 0; s < b.nst; ++s) {
     const int r = b.rad[s];
-    fft_stage_any(x, N, M, r, tw + off, sub);
+    fft_stage_any(x, N, L, r, tw + off, sub);
     __syncwarp();
-    off += M * (r - 1);
-    M *= r;
+    off += (L / r) * (r - 1);
+    L /= r;
   }
 }
 
 template <typename V>
-__device__ __forceinline__ void post_row_par(V* x, int N, int sub) {
-  const V part = post_part_a(x, N, sub);
+__device__ __forceinline__ void post_row_par(V* x, const int* pos, int N, int sub) {
+  const V part = post_part_a(x, pos, N, sub);
   V excl = mk<V>(0, 0);                              // sum of the lower lanes' parts
   V incl = part;
 #pragma unroll
@@ -232,7 +234,8 @@ __device__ __forceinline__ void post_row_par(V* x, int N, int sub) {
       excl.y += oy;
     }
   }
-  post_part_b(x, N, sub, excl);
+  __syncwarp();
+  post_part_b(x, pos, N, sub, excl);
 }
 
 // Rows per CTA: 32 rows of complex128 or 64 of complex64 fill the same 43 KB.
@@ -270,15 +273,15 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     }
     s_ok[threadIdx.x] = ok;
     s_base[threadIdx.x] = base;
-    sm[threadIdx.x * stride] = mk<V>(0, 0);                 // y_0 (digit-reversed position 0)
+    sm[threadIdx.x * stride] = mk<V>(0, 0);                 // y_0
   }
   __syncthreads();
-  const int* __restrict__ rev = idx + b.ioff;
-  const int* __restrict__ gin = rev + N;
+  const int* __restrict__ pos = idx + b.ioff;
+  const int* __restrict__ gin = pos + N;
   const int* __restrict__ src = gin + N;
   const typename Scalar<V>::T* __restrict__ pq = coef + b.coff;
-  // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} digit-reversed (rows that
-  // are skipped or past the end transform zeros and are not stored)
+  // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} in natural order (rows
+  // that are skipped or past the end transform zeros and are not stored)
   const int np = N / 2;
 #pragma unroll 4
   for (int e = threadIdx.x; e < TM * np; e += NT) {
@@ -297,8 +300,8 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     V yj, ym;
     pre_pair(xj, xm, pq[2 * j], pq[2 * j + 1], &yj, &ym);
     V* x = sm + r * stride;
-    x[rev[j]] = yj;
-    if (N - j != j) x[rev[N - j]] = ym;
+    x[j] = yj;
+    if (N - j != j) x[N - j] = ym;
   }
   __syncthreads();
   // phase 2: FFT and post step, kTPR lanes per row
@@ -306,7 +309,7 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     V* x = sm + (threadIdx.x / kTPR) * stride;
     const int sub = threadIdx.x % kTPR;
     fft_row_par(x, b, tw, sub);
-    post_row_par(x, N, sub);
+    post_row_par(x, pos, N, sub);
   }
   __syncthreads();
   // phase 3: store (row-contiguous, or transposed with the rows of a column contiguous)
@@ -416,36 +419,40 @@ bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& 
   }
   if (m != 1) return false;
   const double pi = 3.14159265358979323846;
-  // stage twiddles exp(-2 pi i q k / (M r)), k = 0..M-1, q = 1..r-1 (argument reduced exactly)
+  // stage twiddles exp(-2 pi i j1 q / L), j1 = 0..L/r-1, q = 1..r-1 (argument reduced exactly),
+  // sub-transform length L = N, N / r_1, ...
   b.tw_off = (long long)tw.size();
-  int M = 1;
+  int L = N;
   for (int s = 0; s < b.nst; ++s) {
-    const int r = b.rad[s], L = M * r;
-    for (int k = 0; k < M; ++k)
+    const int r = b.rad[s], M = L / r;
+    for (int j1 = 0; j1 < M; ++j1)
       for (int q = 1; q < r; ++q) {
-        const int e = (q * k) % L;
+        const int e = (j1 * q) % L;
         const double th = -2.0 * pi * e / L;
         tw.push_back(make_double2(std::cos(th), std::sin(th)));
       }
-    M = L;
+    L = M;
   }
   b.ntw = (int)(tw.size() - b.tw_off);
-  // rev[N]: digit-reversed position of y_j; gin[N]: column of input index j (1..n);
-  // src[n]: position holding the value of output column c
+  // pos[N]: where the FFT leaves Y_k (digits of k, radix r_1 first, weighted N / r_1, ...);
+  // gin[N]: column of input index j (1..n); src[n]: position holding output column c
   b.ioff = (long long)idx.size();
-  for (int j = 0; j < N; ++j) {
-    int jj = j, pos = 0;
-    int Ls[kDstMaxStages + 1];
-    Ls[0] = 1;
-    for (int s = 0; s < b.nst; ++s) Ls[s + 1] = Ls[s] * b.rad[s];
-    for (int s = b.nst - 1; s >= 0; --s) {
-      pos += (jj % b.rad[s]) * Ls[s];
-      jj /= b.rad[s];
+  std::vector<int> pos(N);
+  for (int k = 0; k < N; ++k) {
+    int kk = k, p = 0, Ls = N;
+    for (int s = 0; s < b.nst; ++s) {
+      Ls /= b.rad[s];
+      p += (kk % b.rad[s]) * Ls;
+      kk /= b.rad[s];
     }
-    idx.push_back(pos);
+    pos[k] = p;
   }
+  for (int k = 0; k < N; ++k) idx.push_back(pos[k]);
   for (int j = 0; j < N; ++j) idx.push_back(j == 0 ? 0 : (dir == 1 ? j - 1 : sym_col(j, n)));
-  for (int c = 0; c < n; ++c) idx.push_back(post_pos(dir == 1 ? sym_mode(c, n) : c + 1, N));
+  for (int c = 0; c < n; ++c) {
+    const int m = dir == 1 ? sym_mode(c, n) : c + 1;
+    idx.push_back(pos[m == 1 ? 0 : (m % 2 == 0 ? m / 2 : N - (m - 1) / 2)]);
+  }
   b.coff = (long long)coef.size();
   for (int j = 0; j <= N / 2; ++j) {
     const double sj = std::sin(pi * j / N);
@@ -464,29 +471,29 @@ bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out) {
   if (!dst_plan_block(n, 0, dir, S, blk, idx, coef, tw)) return false;
   const DstBlock& b = blk[0];
   const int N = n + 1;
-  const int* rev = idx.data() + b.ioff;
-  const int* gin = rev + N;
+  const int* pos = idx.data() + b.ioff;
+  const int* gin = pos + N;
   const int* src = gin + N;
   std::vector<double2> x(N);
-  x[rev[0]] = make_double2(0.0, 0.0);
+  x[0] = make_double2(0.0, 0.0);
   for (int j = 1; 2 * j <= N; ++j) {
     double2 yj, ym;
     pre_pair(in[gin[j]], in[gin[N - j]], coef[b.coff + 2 * j], coef[b.coff + 2 * j + 1], &yj, &ym);
-    x[rev[j]] = yj;
-    if (N - j != j) x[rev[N - j]] = ym;
+    x[j] = yj;
+    if (N - j != j) x[N - j] = ym;
   }
   // the kernel's per-lane code, the lanes of a row taken in turn
-  int M = 1, off = 0;
+  int L = N, off = 0;
   for (int st = 0; st < b.nst; ++st) {
-    for (int sub = 0; sub < kTPR; ++sub) fft_stage_any(x.data(), N, M, b.rad[st], tw.data() + b.tw_off + off, sub);
-    off += M * (b.rad[st] - 1);
-    M *= b.rad[st];
+    for (int sub = 0; sub < kTPR; ++sub) fft_stage_any(x.data(), N, L, b.rad[st], tw.data() + b.tw_off + off, sub);
+    off += (L / b.rad[st]) * (b.rad[st] - 1);
+    L /= b.rad[st];
   }
   double2 part[kTPR];
-  for (int sub = 0; sub < kTPR; ++sub) part[sub] = post_part_a(x.data(), N, sub);
+  for (int sub = 0; sub < kTPR; ++sub) part[sub] = post_part_a(x.data(), pos, N, sub);
   double2 excl = make_double2(0.0, 0.0);
   for (int sub = 0; sub < kTPR; ++sub) {
-    post_part_b(x.data(), N, sub, excl);
+    post_part_b(x.data(), pos, N, sub, excl);
     excl = cadd(excl, part[sub]);
   }
   for (int c = 0; c < n; ++c) out[c] = x[src[c]];

@@ -60,7 +60,7 @@ struct XTile {
 // symmetric-modes-first order; inverse: the transpose), i.e. a scaled DST-I.  It is
 // computed from one complex FFT of length N per row: y_j = p_j x_j + q_j x_{N-j}
 // (p_j, q_j = (S / 2) (sin(pi j / N) +- 1/2)), Y = FFT(y) by mixed-radix stages
-// (radices 2, 3, 4, 5; input in digit-reversed order, decimation in time), then
+// (radices 2, 3, 4, 5; decimation in frequency, output in digit-reversed order), then
 // X_{2k} = i (Y_k - Y_{N-k}) and X_{2k+1} = X_{2k-1} + Y_k + Y_{N-k}, X_1 = Y_0.
 constexpr int kDstMaxStages = 8;
 constexpr int kDstMaxN = 128;     // largest N = n + 1 handled by the fast transform
@@ -71,7 +71,7 @@ struct DstBlock {
   int rad[kDstMaxStages];         // radices in stage order
   int ntw;                        // twiddles of all stages (complex entries)
   long long tw_off;               // offset (complex) of the stage twiddles
-  long long ioff;                 // offset (ints) of rev[N], gin[N], src[n]
+  long long ioff;                 // offset (ints) of pos[N], gin[N], src[n]
   long long coff;                 // offset (doubles) of (p_j, q_j), j = 0..N/2
 };
 struct DstSet {
