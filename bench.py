@@ -428,37 +428,28 @@ def fp64_roofline(w, R, st, traffic_workload=None):
 
 
 def tc_roofline(w, R, st, refinements):
-    """Roofline of the mixed path's bulk transform kernels, HBM-bound.
+    """Roofline of the mixed path's bulk transform kernel (tensor cores, 3xTF32), HBM-bound.
 
     Algorithmic bytes per transformed value: forward x reads complex128 f and writes complex64
     (24 B), forward y and inverse y complex64 both ways (16 B), inverse x reads complex64 and
     writes complex128 u (24 B), or also reads u when it accumulates a correction (40 B);
-    averaged over the 4 (1 + refinements) launches of a step.  Uniform blocks run the FP32 fast
-    sine transform (dst_kernel<float2>), the others the tensor-core product
-    (xform_tc_kernel, 3xTF32), whose launches are also rated against the tensor pipe:
-    3 TF32 products of 8 real flops per complex multiply-add.
+    averaged over the 4 (1 + refinements) launches of a step.  The same launches against the
+    tensor pipe: 3 TF32 products of 8 real flops per complex multiply-add.  (The mixed path's
+    FP32 fast sine transform of uniform blocks is opt-in and not used here.)
     """
     hbm_peak, hbm_src = measured_peaks()
     t = launch_ms(st)
     b = tc_bytes_per_launch(w, R, refinements)
-    dense, fast, all_fast = fp64_transform_work(w, R)
-    if all_fast:
-        kernel, fname = "dst_kernel<float2> (FP32 fast sine transforms of the uniform blocks)", "hz_dst.cu"
-    elif fast == 0:
-        kernel, fname = "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)", "hz_xform_tc.cu"
-    else:
-        kernel, fname = "xform_tc_kernel + dst_kernel<float2> (bulk x/y transforms)", "hz_xform_tc.cu"
-    out = {"bound": "hbm", "kernel": kernel,
+    out = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
            "achieved": b / (t * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
            "frac": b / (t * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
            "bytes_per_launch": b, "launch_ms": t,
-           "traffic": profiled_traffic(kernel.split(" ")[0], w.name, fname)}
-    if not all_fast:
-        tc_flops = sum(bulk_macs(w, R)) / 4 * 8 * 3
-        tpk, tsrc = tf32_peak()
-        out["tensor"] = {"achieved": tc_flops / (t * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
-                         "frac": tc_flops / (t * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
-                         "flops_per_launch": tc_flops}
+           "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
+    tc_flops = sum(bulk_macs(w, R)) / 4 * 8 * 3
+    tpk, tsrc = tf32_peak()
+    out["tensor"] = {"achieved": tc_flops / (t * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                     "frac": tc_flops / (t * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
+                     "flops_per_launch": tc_flops}
     return out
 
 

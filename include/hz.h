@@ -126,8 +126,9 @@ typedef struct {
   int tensor_cores;          /* 1: the mixed path's bulk transforms run on the tensor
                                 cores (tcgen05, 3xTF32) with complex64 mode-space data;
                                 0: FP32 CUDA-core transforms on complex128 data          */
-  int fast_sine;             /* 1 when uniform blocks use the FFT-based sine transform
-                                (hz_plan_set_fast_sine), 0 otherwise                     */
+  int fast_sine;             /* uniform blocks on the FFT-based sine transform: 0 none,
+                                1 FP64 path, 2 both paths (hz_plan_set_fast_sine; 0 when
+                                the plan has no such block)                              */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's
@@ -180,11 +181,13 @@ hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
 
 /* Transform the uniform blocks (all steps equal and real, so that the block's eigenvectors
  * are the discrete sines and its tables a scaled DST-I) by the FFT-based sine transform, the
- * fast transform of the uniform core in the cost estimate of Sec. 2 (enable = 1, the
- * default: one complex FFT of length n + 1 per row, for blocks whose n + 1 <= 128 has no
- * prime factor above 5), or by the dense product (enable = 0: the folded FP64 product on the
- * FP64 path, the tensor cores on the mixed path).  The FP64 path computes it in FP64, the
- * mixed path's bulk transforms in FP32; the autotuner times both choices. */
+ * fast transform of the uniform core in the cost estimate of Sec. 2 (one complex FFT of
+ * length n + 1 per row, for blocks whose n + 1 <= 128 has no prime factor above 5), or by
+ * the dense product.  enable = 0: dense everywhere (the folded FP64 product on the FP64 path,
+ * the tensor cores on the mixed path); 1 (the default): the FP64 path in FP64 through the
+ * fast transform, the mixed path on the tensor cores; 2: also the mixed path's bulk
+ * transforms through the fast transform, in FP32.  The autotuner times both choices of the
+ * plan's path.  HZ_ERR_ARG for other values. */
 hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
 
 /* Host-only helper (no device memory is touched): the fast sine transform that the plan

@@ -94,6 +94,7 @@ struct hz_plan_s {
   bool use_tc = true;                // mixed path: bulk transforms on the tensor cores
   bool tc_ok = true;                 // the tensor-core tables have their TMA tensor maps
   bool fast_sine = true;             // FP64 path: uniform blocks through the FFT-based sine transform
+  bool fast_sine32 = false;          // mixed path: the same in FP32 instead of the tensor cores
   bool has_dst = false;              // some block has a fast sine transform
   int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
   // second stream for the y-side interface work (runs beside the x side)
@@ -821,7 +822,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
                   int rpp, int trans, int store_mode, int conj, const signed char* skip) {
     if (in32 || out32 || (lo && p->use_tc && !conj)) {
       // uniform blocks by the FP32 fast sine transform, the others on the tensor cores
-      const bool fs = p->fast_sine && xs.dst.nblk > 0 && (in32 || out32);
+      const bool fs = p->fast_sine32 && xs.dst.nblk > 0 && (in32 || out32);
       if (fs && !hz::dst_f32(xs.dst, in, in32, out, out32, rpp, planes, xs.ncols, trans, store_mode, skip, st))
         throw Fail{HZ_ERR_ARG};
       if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st,
@@ -1141,13 +1142,14 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   float best = 1e30f;
   int best_rb = p->zs_rb;
   bool best_tc = p->use_tc;
-  bool best_fs = p->fast_sine;
-  const int fs_lo = p->has_dst ? 0 : (p->fast_sine ? 1 : 0);
+  bool& fsref = mixed ? p->fast_sine32 : p->fast_sine;     // the fast-sine choice of this path
+  bool best_fs = fsref;
+  const int fs_lo = p->has_dst ? 0 : (fsref ? 1 : 0);
   const int fs_hi = p->has_dst ? 1 : fs_lo;
   for (int fs = fs_lo; fs <= fs_hi; ++fs)
   for (int rb = 1; rb <= 2; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
-      p->fast_sine = fs != 0;
+      fsref = fs != 0;
       p->zs_rb = rb;
       p->use_tc = tc != 0;
       solve_core(p, w, st, f, out, nrhs, mixed, hz::XS_STORE, 0);   // warm-up
@@ -1163,7 +1165,7 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   cudaEventDestroy(e1);
   p->zs_rb = best_rb;
   p->use_tc = best_tc;
-  p->fast_sine = best_fs;
+  fsref = best_fs;
   p->timing = timing;
   return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0);
 }
@@ -1529,8 +1531,9 @@ hz_status hz_tridiag_eig(int n, const hz_c128* kd, const hz_c128* ko, const hz_c
 }
 
 hz_status hz_plan_set_fast_sine(hz_plan_t p, int enable) {
-  if (!p) return HZ_ERR_ARG;
-  p->fast_sine = enable != 0;
+  if (!p || enable < 0 || enable > 2) return HZ_ERR_ARG;
+  p->fast_sine = enable >= 1;
+  p->fast_sine32 = enable == 2;
   return HZ_OK;
 }
 
@@ -1910,7 +1913,7 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   if (!p || !out) return HZ_ERR_ARG;
   p->info.device_bytes = p->bytes;
   p->info.tensor_cores = p->use_tc ? 1 : 0;
-  p->info.fast_sine = (p->fast_sine && p->has_dst) ? 1 : 0;
+  p->info.fast_sine = p->has_dst ? (p->fast_sine32 ? 2 : (p->fast_sine ? 1 : 0)) : 0;
   *out = p->info;
   return HZ_OK;
 }

@@ -139,8 +139,19 @@ template <int R, typename V>
 __host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int L, const V* tw, int sub) {
   const int M = L / R;
   const int nb = N / R;
-  for (int t = sub; t < nb; t += kTPR) {
-    const int blk = t / M, j1 = t - blk * M;
+  // FP32: lane sub takes the contiguous butterflies [t0, t1) (neighbouring lanes a chunk apart,
+  // spread over the shared-memory banks, indices stepped without division); FP64 (bound by
+  // the FP64 pipe, where this measured slower): butterflies sub, sub + kTPR, ...
+  constexpr bool CONTIG = sizeof(V) == 8;
+  const int chunk = CONTIG ? (nb + kTPR - 1) / kTPR : 1;
+  const int t0 = sub * chunk, t1 = CONTIG ? (t0 + chunk < nb ? t0 + chunk : nb) : nb;
+  const int step = CONTIG ? 1 : kTPR;
+  int blk = t0 / M, j1 = t0 - (t0 / M) * M;
+  for (int t = t0; t < t1; t += step) {
+    if (!CONTIG) {
+      blk = t / M;
+      j1 = t - blk * M;
+    }
     V a[R];
     V* p = x + blk * L + j1;
 #pragma unroll
@@ -155,6 +166,10 @@ __host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int L, const
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) p[q * M] = a[q];
+    if (CONTIG && ++j1 == M) {
+      j1 = 0;
+      ++blk;
+    }
   }
 }
 
@@ -281,14 +296,13 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
   const int* __restrict__ src = gin + N;
   const typename Scalar<V>::T* __restrict__ pq = coef + b.coff;
   // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} in natural order (rows
-  // that are skipped or past the end transform zeros and are not stored)
+  // that are skipped or past the end transform zeros and are not stored).  FP32: one warp per
+  // row at a time, lanes on consecutive j; FP64: all (row, j) pairs spread over the threads.
   const int np = N / 2;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < TM * np; e += NT) {
-    const int r = e / np, j = 1 + (e - r * np);
+  auto pre_one = [&](int r, int j, bool ok) {
+    const TI* rp = in + (row0 + r) * (long long)ncols + b.start;
     V xj = mk<V>(0, 0), xm = xj;
-    if (s_ok[r]) {
-      const TI* rp = in + (row0 + r) * (long long)ncols + b.start;
+    if (ok) {
       if constexpr (sizeof(V) == 16) {
         xj = to_c128(rp[gin[j]]);
         xm = to_c128(rp[gin[N - j]]);
@@ -302,6 +316,19 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     V* x = sm + r * stride;
     x[j] = yj;
     if (N - j != j) x[N - j] = ym;
+  };
+  if constexpr (sizeof(V) == 8) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < TM; r += NT / 32) {
+      const bool ok = s_ok[r] != 0;
+      for (int j = 1 + lane; j <= np; j += 32) pre_one(r, j, ok);
+    }
+  } else {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < TM * np; e += NT) {
+      const int r = e / np, j = 1 + (e - r * np);
+      pre_one(r, j, s_ok[r] != 0);
+    }
   }
   __syncthreads();
   // phase 2: FFT and post step, kTPR lanes per row
@@ -312,15 +339,22 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     post_row_par(x, pos, N, sub);
   }
   __syncthreads();
-  // phase 3: store (row-contiguous, or transposed with the rows of a column contiguous)
-  for (int e = threadIdx.x; e < TM * n; e += NT) {
+  // phase 3: store.  Transposed: a warp's lanes take consecutive rows of one column (contiguous
+  // in the output, conflict-free in shared memory).  Row-contiguous: lanes take G consecutive
+  // columns (64 bytes) of 32 / G rows, so that each row's segment is one or two sectors and the
+  // gathers from the scattered positions spread over rows.
+  constexpr int G = 64 / (int)sizeof(V);
+  const int ncg = (n + G - 1) / G;
+  for (int e = threadIdx.x; e < TM * (trans ? n : ncg * G); e += NT) {
     int r, c;
     if (trans) {
       c = e / TM;
       r = e - c * TM;
     } else {
-      r = e / n;
-      c = e - r * n;
+      const int cl = e % G, rest = e / G;
+      r = rest % TM;
+      c = (rest / TM) * G + cl;
+      if (c >= n) continue;
     }
     if (!s_ok[r]) continue;
     V v = sm[r * stride + src[c]];

@@ -219,10 +219,10 @@ class Plan:
         return {"rhs_per_thread": c.value % 10, "tensor_cores": (c.value // 10) % 10 == 1,
                 "fast_sine": c.value >= 100}
 
-    def set_fast_sine(self, enable: bool):
-        """FP64 path: uniform blocks by the FFT-based sine transform (True) or the folded
-        dense product (False) (hz_plan_set_fast_sine)."""
-        _check(_lib.hz_plan_set_fast_sine(self._h, int(bool(enable))), "hz_plan_set_fast_sine")
+    def set_fast_sine(self, enable: int):
+        """Uniform blocks by the FFT-based sine transform (hz_plan_set_fast_sine): 0 dense
+        everywhere, 1 (default) the FP64 path, 2 also the mixed path (in FP32)."""
+        _check(_lib.hz_plan_set_fast_sine(self._h, int(enable)), "hz_plan_set_fast_sine")
 
     def set_frequency(self, omega: float):
         _check(_lib.hz_plan_set_frequency(self._h, float(omega)), "hz_plan_set_frequency")

@@ -356,7 +356,7 @@ def _uniform_mix_workload(nrhs=2):
                       rng.standard_normal((nrhs, nz, ny, nx)) + 1j * rng.standard_normal((nrhs, nz, ny, nx)))
 
 
-@pytest.mark.parametrize("precision,fast", [("fp64", True), ("fp64", False), ("mixed", True), ("mixed", False)])
+@pytest.mark.parametrize("precision,fast", [("fp64", 1), ("fp64", 0), ("mixed", 2), ("mixed", 1)])
 def test_uniform_blocks_sine_path(hz, torch_cuda, precision, fast):
     # x blocks 17 (n + 1 = 18 = 2 x 3 x 3: fast sine transform), 18 (19 is prime: folded dense),
     # 17; y core block of 35 (36 = 4 x 3 x 3) between dense complex rim blocks
@@ -368,7 +368,7 @@ def test_uniform_blocks_sine_path(hz, torch_cuda, precision, fast):
     u = plan.solve(torch_cuda.from_numpy(w.f).cuda()).cpu().numpy()
     assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
     assert plan.info()["eig_max_residual"] < 1e-12
-    assert plan.info()["fast_sine"] == int(fast)
+    assert plan.info()["fast_sine"] == fast
 
 
 def test_fast_sine_many_tiles_against_lu_and_dense(hz, torch_cuda):
@@ -387,13 +387,13 @@ def test_fast_sine_many_tiles_against_lu_and_dense(hz, torch_cuda):
     fd = torch.from_numpy(w.f).cuda()
     u_fast = plan.solve(fd).cpu().numpy()
     assert plan.info()["fast_sine"] == 1
-    plan.set_fast_sine(False)
+    plan.set_fast_sine(0)
     u_dense = plan.solve(fd).cpu().numpy()
     assert rel(u_fast, ref) < TOL64
     assert rel(u_fast, u_dense) < 1e-12
     # the mixed path: bulk transforms of these all-uniform blocks by the FP32 fast sine kernel
     plan.set_options(precision="mixed", rtol=1e-10, max_refine=12)
-    plan.set_fast_sine(True)
+    plan.set_fast_sine(2)
     u_mix = plan.solve(fd).cpu().numpy()
     assert plan.info()["rel_residual"] <= 1e-10
     assert rel(u_mix, ref) < TOLMIX
