@@ -577,6 +577,24 @@ def run_extra(args):
     from paper_1909_01299_gb300 import hz, workloads as W
     out = {"workload": args.workload}
     if args.workload == "scaling":
+        def survey_split(n):
+            """Interfaces of the paper's split of a survey axis (rim | uniform core | rim, Sec. 2 cost
+            paragraph): the uniform nodes 17..n-18 of rim_axis(n - 32) carry core blocks of width s
+            (s + 1 with no prime factor above 5, s <= 127, so that they take the fast sine
+            transform), interface nodes between them, and the rest of the axis goes to the two
+            rim blocks."""
+            lo, hi = 17, n - 17                          # uniform nodes [lo, hi)
+            C = hi - lo
+            k = max(1, -(-(C + 1) // 128))
+            s = max(m for m in range(2, 128) if fast_sine_ok(m) and k * m + (k - 1) <= C)
+            used = k * s + (k - 1)
+            start = lo + (C - used) // 2
+            ifc = [start - 1]
+            for b in range(1, k):
+                ifc.append(start + b * (s + 1) - 1)
+            ifc.append(start + used)
+            return ifc, s, k
+
         # the two regimes of the cost estimate in Sec. 2, FP64 path: one block per axis (dense
         # N x N transforms, work per unknown ~ N) against the automatic ~sqrt(N) partition
         # (work per unknown ~ sqrt(N)); survey-type axes (uniform core + 16-node rim), nz = 64
@@ -588,13 +606,21 @@ def run_extra(args):
             f = torch.from_numpy(rng.standard_normal((2, 64, n, n)) + 1j * rng.standard_normal((2, 64, n, n))).cuda()
             u = torch.empty_like(f)
             row = {"n": n, "unknowns_x_rhs": n * n * 64 * 2}
-            for label, nb in (("one_block", 1), ("auto", 0)):
-                plan = hz.Plan(hx, hx, hzz, [0, 32, 64], [0.2 + 0.004j, 0.35 + 0.007j], nbx=nb, nby=nb,
-                               precision="fp64")
+            ifc, s_core, k_core = survey_split(n)
+            for label, nb in (("one_block", 1), ("auto", 0), ("survey_fast", None)):
+                if nb is None:       # rim | k uniform core blocks of width s (fast sine transform) | rim
+                    plan = hz.Plan(hx, hx, hzz, [0, 32, 64], [0.2 + 0.004j, 0.35 + 0.007j], x_iface=ifc,
+                                   y_iface=ifc, precision="fp64")
+                else:
+                    plan = hz.Plan(hx, hx, hzz, [0, 32, 64], [0.2 + 0.004j, 0.35 + 0.007j], nbx=nb, nby=nb,
+                                   precision="fp64")
                 ms, launches, st, clk = time_path(torch, hz, plan, f, u, args.steps, args.warmup, None, 1, 0)
                 row[label] = {"blocks": plan.info()["nbx"], "ms": ms, "value": n * n * 64 * 2 / (ms * 1e-3),
                               "ns_per_unknown": ms * 1e6 / (n * n * 64 * 2),
+                              "fast_sine": plan.info()["fast_sine"],
                               "rel_residual_max": float(np.max(plan.residual(f, u)))}
+                if nb is None:
+                    row[label]["core_blocks"] = f"{k_core} x {s_core}"
                 plan.close()
             rows.append(row)
         out.update({"path": "fp64", "sweep": rows, "unit": UNIT})

@@ -936,8 +936,18 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     zg.rhs = w.G; zg.out = w.V;                     // w~ (v~ in V is no longer needed)
     zg.P = p->Pg; zg.Q = p->Qg; zg.cm = p->cm_g;
     if (c64) zg.rhs32 = G32;
-    if (c64) hz::global_rhs(ga, G32, st);           // r~ (G is free until step 7)
-    else hz::global_rhs(ga, w.G, st);
+    if (c64) {
+      // complex64 copies of the interface transforms (cg, dg are free until the contractions)
+      float2* aX32 = reinterpret_cast<float2*>(w.cg);
+      float2* bY32 = reinterpret_cast<float2*>(w.dg);
+      hz::to_c64_copy(w.aX, aX32, (long long)nIx * ny * planes, st);
+      hz::to_c64_copy(w.bY, bY32, (long long)nIy * nx * planes, st);
+      ga.aX32 = aX32;
+      ga.bY32 = bY32;
+      hz::global_rhs(ga, G32, st);                  // r~ (G is free until step 7)
+    } else {
+      hz::global_rhs(ga, w.G, st);
+    }
     hz::zsolve(zg, st);
     fork(p, st);
     if (nIx) {
@@ -963,8 +973,18 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
     ba.cxl = p->dx.cl; ba.cxr = p->dx.cr; ba.cyl = p->dy.cl; ba.cyr = p->dy.cr;
     ba.real_x = p->dx.lr_real ? 1 : 0; ba.real_y = p->dy.lr_real ? 1 : 0;
     if (lo) { ba.cxl32 = p->dx.cl32; ba.cxr32 = p->dx.cr32; ba.cyl32 = p->dy.cl32; ba.cyr32 = p->dy.cr32; }
-    if (c64) hz::boundary_rhs(ba, FT32, st);        // f~ + g~ / M_z, in place
-    else hz::boundary_rhs(ba, w.FT, st);
+    if (c64) {
+      // complex64 copies of the boundary data (aX, bY are free after step 5); f~ + g~ in FP32
+      float2* alX32 = reinterpret_cast<float2*>(w.aX);
+      float2* alY32 = reinterpret_cast<float2*>(w.bY);
+      hz::to_c64_copy(w.alX, alX32, (long long)nIx * ny * planes, st);
+      hz::to_c64_copy(w.alY, alY32, (long long)nIy * nx * planes, st);
+      ba.alphaX32 = alX32;
+      ba.alphaY32 = alY32;
+      hz::boundary_rhs(ba, FT32, st);               // f~ + g~ / M_z, in place
+    } else {
+      hz::boundary_rhs(ba, w.FT, st);
+    }
     hz::zsolve(za, st);
   }
   // Step 7: u = W_x (x) W_y u~ in the blocks; u = w on the interfaces

@@ -64,6 +64,9 @@ __device__ __forceinline__ double2 to_c128(double2 v) { return v; }
 // Store a value computed in FP64 into either storage type (complex64: truncated).
 __device__ __forceinline__ void store_c(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void store_c(float2* p, double2 v) { *p = to_c64t(v); }
+// an FP32 value into a complex64 or complex128 element
+__device__ __forceinline__ void store_f32(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void store_f32(double2* p, float2 v) { *p = to_c128(v); }
 
 // acc + c * y in FP32
 __device__ __forceinline__ float2 cfma32(float2 c, float2 y, float2 acc) {

@@ -235,6 +235,9 @@ struct BoundaryArgs {
   const float2* cxl32 = nullptr; const float2* cxr32 = nullptr;
   const float2* cyl32 = nullptr; const float2* cyr32 = nullptr;
   int real_x = 0, real_y = 0;            // FP64: cxl/cxr (cyl/cyr) are real
+  // complex64 copies of alphaX / alphaY (mixed path with complex64 f~): read instead of the
+  // complex128 arrays, and the sum f~ + g~ is formed in FP32
+  const float2* alphaX32 = nullptr; const float2* alphaY32 = nullptr;
 };
 void boundary_rhs(const BoundaryArgs& a, double2* ft, cudaStream_t st);
 // complex64 f~ (mixed path, needs the FP32 coefficient copies): the sum is formed in FP64
@@ -251,7 +254,11 @@ struct GlobalRhsArgs {
   const float2* WgxI32 = nullptr;        // FP32 copies: when set, FP32 arithmetic (mixed path)
   const float2* WgyI32 = nullptr;
   int real_x = 0, real_y = 0;            // FP64: WgxI (WgyI) is real
+  const float2* aX32 = nullptr;          // complex64 copies of aX / bY (FP32 arithmetic only)
+  const float2* bY32 = nullptr;
 };
+// out[i] = complex64(in[i]) (truncating conversion), n values.
+void to_c64_copy(const double2* in, float2* out, long long n, cudaStream_t st);
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st);
 // complex64 output (mixed path, needs the FP32 coefficient copies)
 void global_rhs(const GlobalRhsArgs& a, float2* out, cudaStream_t st);

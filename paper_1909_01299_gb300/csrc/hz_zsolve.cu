@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
   const double2* __restrict__ ayp = a.alphaY + (long long)rk * a.nIy * a.nx;
   FT* __restrict__ ftp = ft + (long long)rk * plane;
   double2 val[REPT];
+  float2 val32[REPT];
   bool ok[REPT];
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
@@ -145,7 +146,20 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
     const double2* ax = axp + j;
     const double2* ay = ayp + i;
     double2 v = to_c128(ftp[pos]);
-    if (LO) {
+    if (LO && a.alphaX32) {
+      // complex64 interface data and f~: the whole sum in FP32 (one rounding to nearest)
+      const float2* ax32 = a.alphaX32 + (long long)rk * a.nIx * a.ny + j;
+      const float2* ay32 = a.alphaY32 + (long long)rk * a.nIy * a.nx + i;
+      float2 g = make_float2(0.f, 0.f);
+      if (pl >= 0) g = cfma32(a.cxl32[i], ax32[(long long)pl * a.ny], g);
+      if (pr >= 0) g = cfma32(a.cxr32[i], ax32[(long long)pr * a.ny], g);
+      if (ql >= 0) g = cfma32(a.cyl32[j], ay32[(long long)ql * a.nx], g);
+      if (qr >= 0) g = cfma32(a.cyr32[j], ay32[(long long)qr * a.nx], g);
+      const float2 f32 = to_c64t(ftp[pos]);
+      const float s32 = s == 1.0 ? 1.f : f64_to_f32_trunc(s);
+      val32[e] = make_float2(fmaf(s32, g.x, f32.x), fmaf(s32, g.y, f32.y));
+      continue;
+    } else if (LO) {
       float2 g = make_float2(0.f, 0.f);
       if (pl >= 0) g = cfma32(a.cxl32[i], to_c64t(ax[(long long)pl * a.ny]), g);
       if (pr >= 0) g = cfma32(a.cxr32[i], to_c64t(ax[(long long)pr * a.ny]), g);
@@ -180,6 +194,12 @@ __global__ void __launch_bounds__(RT) boundary_rhs_kernel(const BoundaryArgs a, 
     }
     val[e] = v;
   }
+  if (LO && a.alphaX32) {
+#pragma unroll
+    for (int e = 0; e < REPT; ++e)
+      if (ok[e]) store_f32(ftp + ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x, val32[e]);
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < REPT; ++e)
     if (ok[e]) store_c(ftp + ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x, val[e]);
@@ -197,6 +217,7 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, O
   const double2* __restrict__ byp = a.bY + (long long)rk * a.nIy * a.nx;
   OT* __restrict__ op = out + (long long)rk * plane;
   double2 val[REPT];
+  float2 val32[REPT];
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
     const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
@@ -204,7 +225,14 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, O
     const int i = pos / a.ny, j = pos - i * a.ny;
     const double2* ax = axp + j;
     const double2* by = byp + i;
-    if (LO) {
+    if (LO && a.aX32) {
+      const float2* ax32 = a.aX32 + (long long)rk * a.nIx * a.ny + j;
+      const float2* by32 = a.bY32 + (long long)rk * a.nIy * a.nx + i;
+      float2 g = make_float2(0.f, 0.f);
+      for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], ax32[(long long)p * a.ny], g);
+      for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], by32[(long long)q * a.nx], g);
+      val32[e] = g;
+    } else if (LO) {
       float2 g = make_float2(0.f, 0.f);
       for (int p = 0; p < a.nIx; ++p) g = cfma32(a.WgxI32[(long long)p * a.nx + i], to_c64t(ax[(long long)p * a.ny]), g);
       for (int q = 0; q < a.nIy; ++q) g = cfma32(a.WgyI32[(long long)q * a.ny + j], to_c64t(by[(long long)q * a.nx]), g);
@@ -222,11 +250,24 @@ __global__ void __launch_bounds__(RT) global_rhs_kernel(const GlobalRhsArgs a, O
       val[e] = b;
     }
   }
+  if (LO && a.aX32) {
+#pragma unroll
+    for (int e = 0; e < REPT; ++e) {
+      const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
+      if (pos < plane) store_f32(op + pos, val32[e]);
+    }
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < REPT; ++e) {
     const int pos = ((int)blockIdx.x * REPT + e) * RT + (int)threadIdx.x;
     if (pos < plane) store_c(op + pos, val[e]);
   }
+}
+
+__global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = to_c64t(in[t]);
 }
 
 __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
@@ -326,6 +367,12 @@ void global_rhs_t(const GlobalRhsArgs& a, OT* out, cudaStream_t st) {
 }
 void global_rhs(const GlobalRhsArgs& a, double2* out, cudaStream_t st) { global_rhs_t(a, out, st); }
 void global_rhs(const GlobalRhsArgs& a, float2* out, cudaStream_t st) { global_rhs_t(a, out, st); }
+
+void to_c64_copy(const double2* in, float2* out, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  to_c64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+  count_launch();
+}
 
 void zfactor(double2* P, double2* Q, const double2* lamx, const double2* lamy,
              const signed char* skip_i, const signed char* skip_j, const double2* tzd,
