@@ -15,9 +15,11 @@
 // One CTA (8 warps) computes a 128-row x Nt-column tile (Nt <= 160, a multiple of
 // 16) of one block; two CTAs share an SM (108-112 KB of shared memory and 256 TMEM
 // columns each).  The contraction runs in chunks of 16 real K (64 bytes per operand
-// row): all threads convert the data rows (complex128, or complex64 for the mixed
-// path's mode-space volumes, which carry FP32 accuracy only) to TF32 hi/lo and store
-// them in shared memory in the K-major 64-byte-swizzled layout; the tables' hi/lo rows
+// row): all threads load the data rows (complex128, or complex64 for the mixed path's
+// mode-space volumes, which carry FP32 accuracy only) into registers one chunk ahead,
+// convert them to TF32 hi/lo and store them in shared memory in the K-major
+// 64-byte-swizzled layout (the data never makes a shared-memory round trip before the
+// conversion, which spares the shared-memory bandwidth the MMAs need); the tables' hi/lo rows
 // arrive in the same layout by one TMA copy per chunk; one thread queues the 6 MMAs of
 // the chunk behind those of the previous chunk and commits them to the chunk's
 // mbarrier; two operand stages alternate, so the conversion of chunk c+1 overlaps the
@@ -153,24 +155,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  // 16-byte global -> shared copy; zero fill when !valid (src must still be a valid address)
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
-  // 8-byte copy (one complex64 value: a block may start at an odd column, so pairs of
-  // complex64 values are not 16-byte aligned in general)
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // Shared-memory plan of one CTA (offsets from a 1024-byte aligned base):
-//   raw[2]   : data chunks as loaded, 128 rows x 8 complex (16 KB each for complex128 data,
-//              8 KB for complex64)
+//   raw[2]   : unused by the chunk loop (the data goes to registers); with the pipeline
+//              buffers after it, room for the epilogue's FP32 staging tile
 //   aop[2]   : TF32 hi | lo operand planes of a chunk (2 x 8 KB each), 64B-swizzled
 //   bop[NB]  : TF32 hi | lo table planes of a chunk (2 x nt x 64 B each), 64B-swizzled; three
 //              stages for complex64 data, two for complex128 (whose raw buffers are larger)
@@ -180,8 +167,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // are queued behind them as soon as c is converted), the table rows of chunk c are in flight
 // (one TMA copy per chunk: a 16 x nt x 2 box of the tile's 3-D tensor map [plane][row][k]
 // with the 64-byte swizzle, which lands in exactly the operand layout above) and so are the
-// data rows of chunk c+1 (cp.async: a block may start at any column, so its rows have no
-// 16-byte alignment a TMA box would need).
+// data rows of chunk c+1 (plain loads into registers: a block may start at any column, so
+// its rows have no 16-byte alignment a TMA box would need).
 constexpr int RAW_ROWB = KCH * 8;        // FP64 bytes of a data row in a chunk (KCH / 2 complex)
 constexpr int RAW_BYTES = TC_M * RAW_ROWB;
 __host__ __device__ constexpr int nbstages(bool in32) { return in32 ? 3 : 2; }
@@ -207,7 +194,6 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
   const int nt = t.nt;
   const int B_BYTES = nt * ROWB;                           // one table plane of a chunk
   constexpr bool IN32 = sizeof(TI) == 8, OUT32 = sizeof(TO) == 8;
-  constexpr int RROWB = (int)sizeof(TI) * (KCH / 2);       // bytes of a data row in a chunk
   constexpr int RAWB = raw_bytes(IN32), NB = nbstages(IN32);
   const uint32_t s_base = smem_u32(smem);
   const uint32_t raw0 = s_base, aop0 = raw0 + 2 * RAWB, bop0 = aop0 + 2 * 2 * A_BYTES;
@@ -219,19 +205,26 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
   const int n = b.size;
   const int nk = b.kpad / KCH;
 
-  // issue the data rows of chunk c (8 complex per row) into raw[c & 1]
-  auto load_raw = [&](int c) {
-    const uint32_t dst = raw0 + (c & 1) * RAWB;
+  // the data values of chunk c that this thread converts: conversion task q (row r = task / 4,
+  // 16-byte TF32 unit u = task % 4) needs the complex columns 2u and 2u + 1 of the chunk;
+  // loaded straight into registers one chunk ahead (no shared-memory round trip)
+  constexpr int NTASK = TC_M * (ROWB / 16) / TC_THREADS;
+  TI dreg[NTASK][2];
+  auto load_regs = [&](int c) {
 #pragma unroll
-    for (int q = 0; q < TC_M * (KCH / 2) / TC_THREADS; ++q) {
-      const int task = tid + TC_THREADS * q;               // row = task / 8, complex = task % 8
-      const int r = task >> 3, cc = task & 7;
+    for (int q = 0; q < NTASK; ++q) {
+      const int task = tid + TC_THREADS * q;
+      const int r = task >> 2, u = task & 3;
       const long long grow = row0 + r;
-      const int col = c * (KCH / 2) + cc;
-      const bool ok = grow < nrows && col < n;
-      const TI* src = ok ? in + grow * (long long)ncols + b.start + col : in;
-      if constexpr (IN32) cp_async8(dst + r * RROWB + cc * 8, src, ok);
-      else cp_async16(dst + r * RROWB + cc * 16, src, ok);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = c * (KCH / 2) + 2 * u + h;
+        TI v;
+        if constexpr (IN32) v = make_float2(0.f, 0.f);
+        else v = make_double2(0.0, 0.0);
+        if (grow < nrows && col < n) v = __ldg(in + grow * (long long)ncols + b.start + col);
+        dreg[q][h] = v;
+      }
     }
   };
   // (thread 0) one TMA copy of the table rows (hi and lo planes) of chunk c into bop[c % NB]
@@ -253,11 +246,8 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     load_b(0);
   }
-  // prologue: cp.async groups {A0}, {A1}; table chunk 0 by TMA
-  load_raw(0);
-  cp_async_commit();
-  if (nk > 1) load_raw(1);
-  cp_async_commit();
+  // prologue: data of chunk 0 into registers; table chunk 0 by TMA
+  load_regs(0);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -266,41 +256,35 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
   bool ok = true;
   int issued = 0;
 
-  // Iteration kc: (1) wait for this thread's data rows of chunk kc and for the MMAs of kc-2,
-  // the last reader of operand stage kc & 1; (2) convert the rows into that stage (the MMAs
-  // of kc-1 run meanwhile); (3) thread 0 waits for the table rows of kc, (4) queues the MMAs
-  // of kc behind those of kc-1 and (5) issues the TMA copy of the table rows of kc+1 into
-  // stage (kc+1) % NB, last read by the MMAs of kc+1-NB (with two stages: kc-1, which thread
-  // 0 waits for first); (6) all threads start the data rows of kc+2 (their buffer was
-  // converted in (2)).  cp.async groups are committed in the order A0 A1 | A2 | A3 | ...,
-  // so at (1) all but the newest group A(kc+1) are complete.
+  // Iteration kc: (1) wait for the MMAs of kc-2, the last reader of operand stage kc & 1;
+  // (2) convert this thread's data values of chunk kc (in registers) into that stage (the
+  // MMAs of kc-1 run meanwhile) and start loading those of kc+1 into the same registers;
+  // (3) thread 0 waits for the table rows of kc, (4) queues the MMAs of kc behind those of
+  // kc-1 and (5) issues the TMA copy of the table rows of kc+1 into stage (kc+1) % NB, last
+  // read by the MMAs of kc+1-NB (with two stages: kc-1, which thread 0 waits for first).
   int tab_issued = (tid == 0) ? 1 : 0, tab_done = 0;        // (thread 0) table copies issued / arrived
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
-    cp_async_wait<1>();                                     // raw A(kc) has landed
     int w = 1;
     if (kc >= 2) w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
     if (!__syncthreads_and(w)) { ok = false; break; }       // every thread's rows in; stage s free
     {
-      const uint32_t rsrc = raw0 + s * RAWB;
       const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
 #pragma unroll
-      for (int q = 0; q < TC_M * (ROWB / 16) / TC_THREADS; ++q) {
+      for (int q = 0; q < NTASK; ++q) {
         const int task = tid + TC_THREADS * q;             // row = task / 4, 16-byte unit = task % 4
         const int r = task >> 2, c = task & 3;
         float f[4];
         if constexpr (IN32) {
-          asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                       : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3])
-                       : "r"(rsrc + r * RROWB + c * 16));
+          f[0] = dreg[q][0].x;
+          f[1] = dreg[q][0].y;
+          f[2] = dreg[q][1].x;
+          f[3] = dreg[q][1].y;
         } else {
-          double x0, x1, x2, x3;
-          asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(rsrc + r * RROWB + c * 32));
-          asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x2), "=d"(x3) : "r"(rsrc + r * RROWB + c * 32 + 16));
-          f[0] = f64_to_f32_trunc(x0);
-          f[1] = f64_to_f32_trunc(x1);
-          f[2] = f64_to_f32_trunc(x2);
-          f[3] = f64_to_f32_trunc(x3);
+          f[0] = f64_to_f32_trunc(dreg[q][0].x);
+          f[1] = f64_to_f32_trunc(dreg[q][0].y);
+          f[2] = f64_to_f32_trunc(dreg[q][1].x);
+          f[3] = f64_to_f32_trunc(dreg[q][1].y);
         }
         uint32_t h[4], l[4];
 #pragma unroll
@@ -313,6 +297,7 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
         if (NP == 3) st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
       }
     }
+    if (kc + 1 < nk) load_regs(kc + 1);                    // lands while chunk kc's MMAs run
     int w2 = 1;
     if (tid == 0) {
       if (tab_done < tab_issued && mbar_wait(&tbars[kc % NB], (kc / NB) & 1)) tab_done = kc + 1;
@@ -346,10 +331,7 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
       }
     }
     issued = kc + 1;
-    if (kc + 2 < nk) load_raw(kc + 2);
-    cp_async_commit();
   }
-  cp_async_wait<0>();                                       // no copy left in flight
   // (thread 0) a table copy that has not arrived (no later one was issued): wait for it once
   // more, bounded, before the shared memory is given up
   if (tid == 0 && tab_done < tab_issued) {

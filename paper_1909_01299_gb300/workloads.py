@@ -177,6 +177,23 @@ def uniform_320x320x200(nrhs: int = 8) -> Workload:
                     precision="mixed", extra={"centres_zyx": cen})
 
 
+def uniform_320x320x40(nrhs: int = 2) -> Workload:
+    """The 320 x 320 grid of the benchmark workload with 40 planes and 2 RHS (same blocks of
+    79 and 80 nodes, inputs of 131 MB, above the L2 size): a small case for kernel captures."""
+    rng = np.random.default_rng(SEED_BASE + 103)
+    nx = ny = 320
+    nz = 40
+    k2 = (np.array([0.10, 0.25, 0.15, 0.40]) * (1 + 0.05j)).astype(np.complex128)
+    cen = np.stack([rng.integers(8, nz - 8, nrhs), rng.integers(8, ny - 8, nrhs),
+                    rng.integers(8, nx - 8, nrhs)], axis=1)     # (z, y, x)
+    f = np.empty((nrhs, nz, ny, nx), dtype=np.complex128)
+    for r in range(nrhs):
+        f[r] = gaussian_source(nz, ny, nx, cen[r])
+    return Workload("uniform-320x320x40-4x4blocks-2rhs", uniform_steps(nx), uniform_steps(ny),
+                    uniform_steps(nz), np.array([0, 10, 20, 30, 40], dtype=np.int32), k2,
+                    default_ifaces(nx, 4), default_ifaces(ny, 4), f, precision="mixed")
+
+
 def adjoint_192x192x128(nsrc: int = 16) -> Workload:
     """192x192x128, PML rim in x/y, uniform z, 32 layers of 4 planes, 2x2 blocks.
 
@@ -258,5 +275,6 @@ NAMED = {
     "uniform32": single_block_32,
     "pml160": pml_160x160x128,
     "uniform320": uniform_320x320x200,
+    "uniform320x40": uniform_320x320x40,
     "adjoint192": adjoint_192x192x128,
 }
