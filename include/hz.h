@@ -129,6 +129,8 @@ typedef struct {
   int fast_sine;             /* uniform blocks on the FFT-based sine transform: 0 none,
                                 1 FP64 path, 2 both paths (hz_plan_set_fast_sine; 0 when
                                 the plan has no such block)                              */
+  int real_tables;           /* 1 when the mixed path's real block tables run the
+                                real-table tensor-core kernel (hz_plan_set_real_tables)  */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's
@@ -174,9 +176,10 @@ hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
 /* Autotuner: times one solve of nrhs right-hand sides (on zero data, in the plan's
  * workspace) for each kernel variant the plan can use -- one or two right-hand sides per
  * thread in the z sweeps ("pencil batch"), for mixed plans tensor-core or CUDA-core FP32
- * bulk transforms, for FP64 plans with uniform blocks the fast sine transform or the
- * folded dense product -- and keeps the fastest.  *choice_out (may be NULL) receives
- * rhs_per_thread + 10 * tensor_cores + 100 * fast_sine. */
+ * bulk transforms and the real-table or interleaved tensor-core kernel, for plans with
+ * uniform blocks the fast sine transform or the dense product -- and keeps the fastest.
+ * *choice_out (may be NULL) receives
+ * rhs_per_thread + 10 * tensor_cores + 100 * fast_sine + 1000 * real_tables. */
 hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
 
 /* Transform the uniform blocks (all steps equal and real, so that the block's eigenvectors
@@ -189,6 +192,13 @@ hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
  * transforms through the fast transform, in FP32.  The autotuner times both choices of the
  * plan's path.  HZ_ERR_ARG for other values. */
 hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
+
+/* Mixed path: blocks whose eigenvector tables are real (all their steps real) run the
+ * tensor-core transform as two real products, Re C = Re A B and Im C = Im A B, each with K = N =
+ * n (enable = 1, the default: 64 data rows per CTA, four CTAs per SM), or as one real GEMM of the
+ * interleaved complex matrices with K = N = 2 n (enable = 0).  Same result up to FP32 rounding;
+ * the autotuner times both.  Blocks with complex (PML) tables always use the interleaved form. */
+hz_status hz_plan_set_real_tables(hz_plan_t plan, int enable);
 
 /* Host-only helper (no device memory is touched): the fast sine transform that the plan
  * runs on the GPU, applied to one row: out[c] = scale sum_j in[g(j)] sin(pi j m / (n + 1)).

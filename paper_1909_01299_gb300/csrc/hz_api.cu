@@ -95,6 +95,8 @@ struct hz_plan_s {
   bool tc_ok = true;                 // the tensor-core tables have their TMA tensor maps
   bool fast_sine = true;             // FP64 path: uniform blocks through the FFT-based sine transform
   bool fast_sine32 = false;          // mixed path: the same in FP32 instead of the tensor cores
+  bool tc_real = true;               // mixed path: real tables through the real-table kernel
+  bool has_real_tc = false;          // some block has a real table
   bool has_dst = false;              // some block has a fast sine transform
   int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
   // second stream for the y-side interface work (runs beside the x side)
@@ -461,33 +463,42 @@ void make_tc(hz_plan_t p, hz::TCSet& ts, int ncols, const std::vector<int>& star
              const std::vector<int>& size, const std::vector<char>& fastb, Get get) {
   std::vector<float> tab;
   std::vector<hz::TCBlock> blocks(start.size());
-  std::vector<hz::TCTile> tiles;
+  std::vector<hz::TCTile> tiles, rtiles;
   for (size_t b = 0; b < start.size(); ++b) {
     const int n = size[b];
     std::vector<cd> B((size_t)n * n);
+    bool real = true;
     for (int a = 0; a < n; ++a)
-      for (int c = 0; c < n; ++c) B[(size_t)a * n + c] = get((int)b, a, c);
-    hz::tc_pack_block(B.data(), n, start[b], tab, blocks[b], tiles, (int)b);
+      for (int c = 0; c < n; ++c) {
+        B[(size_t)a * n + c] = get((int)b, a, c);
+        if (B[(size_t)a * n + c].imag() != 0.0) real = false;
+      }
+    hz::tc_pack_block(B.data(), n, start[b], tab, blocks[b], tiles, (int)b, real ? &rtiles : nullptr);
   }
   ts.ncols = ncols;
-  ts.ntiles = (int)tiles.size();
-  ts.nt_max = 16;
-  for (const auto& t : tiles) ts.nt_max = std::max(ts.nt_max, t.nt);
   ts.d_blocks = upload(p, blocks);
-  ts.d_tiles = upload(p, tiles);
   ts.d_tab = upload(p, tab);
-  std::vector<unsigned char> maps;
-  if (hz::tc_encode_tmaps(ts.d_tab, blocks, tiles, maps)) ts.d_tmaps = upload(p, maps);
-  else p->use_tc = p->tc_ok = false;   // no tensor maps: the mixed path runs the SIMT FP32 transforms
-  std::vector<hz::TCTile> nf;
-  for (const auto& t : tiles)
-    if (!fastb[t.blk]) nf.push_back(t);
-  ts.ntiles_nf = (int)nf.size();
-  if (!nf.empty() && p->tc_ok) {
-    std::vector<unsigned char> maps_nf;
-    ts.d_tiles_nf = upload(p, nf);
-    if (hz::tc_encode_tmaps(ts.d_tab, blocks, nf, maps_nf)) ts.d_tmaps_nf = upload(p, maps_nf);
-    else p->use_tc = p->tc_ok = false;
+  if (!rtiles.empty()) p->has_real_tc = true;
+  // tile lists per variant v = fast + 2 real (see TCSet)
+  for (int v = 0; v < 4; ++v) {
+    const bool fast = v & 1, real = v & 2;
+    std::vector<hz::TCTile> cl, rl;
+    for (const auto& t : tiles)
+      if (!(fast && fastb[t.blk]) && !(real && blocks[t.blk].npad_r > 0)) cl.push_back(t);
+    if (real)
+      for (const auto& t : rtiles)
+        if (!(fast && fastb[t.blk])) rl.push_back(t);
+    for (int k = 0; k < 2; ++k) {
+      const std::vector<hz::TCTile>& lt = k ? rl : cl;
+      hz::TCList& L = k ? ts.rl[v] : ts.cl[v];
+      L.ntiles = (int)lt.size();
+      if (lt.empty()) continue;
+      for (const auto& t : lt) L.nt_max = std::max(L.nt_max, t.nt);
+      L.d_tiles = upload(p, lt);
+      std::vector<unsigned char> maps;
+      if (p->tc_ok && hz::tc_encode_tmaps(ts.d_tab, blocks, lt, maps, k == 1)) L.d_tmaps = upload(p, maps);
+      else p->use_tc = p->tc_ok = false;   // no tensor maps: the mixed path runs the SIMT FP32 transforms
+    }
   }
 }
 
@@ -826,7 +837,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
       if (fs && !hz::dst_f32(xs.dst, in, in32, out, out32, rpp, planes, xs.ncols, trans, store_mode, skip, st))
         throw Fail{HZ_ERR_ARG};
       if (!hz::xform_tc(ts, in, in32, out, out32, rpp, planes, trans, store_mode, skip, p->status, st,
-                        p->opts.precision == HZ_MIXED_TF32 ? 1 : 3, fs))
+                        p->opts.precision == HZ_MIXED_TF32 ? 1 : 3, fs, p->tc_real))
         throw Fail{HZ_ERR_ARG};
     } else if (!lo) {
       hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
@@ -1164,11 +1175,16 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   bool best_tc = p->use_tc;
   bool& fsref = mixed ? p->fast_sine32 : p->fast_sine;     // the fast-sine choice of this path
   bool best_fs = fsref;
+  bool best_tr = p->tc_real;
+  const int tr_lo = (mixed && p->has_real_tc) ? 0 : (p->tc_real ? 1 : 0);
+  const int tr_hi = (mixed && p->has_real_tc) ? 1 : tr_lo;
   const int fs_lo = p->has_dst ? 0 : (fsref ? 1 : 0);
   const int fs_hi = p->has_dst ? 1 : fs_lo;
+  for (int tr = tr_lo; tr <= tr_hi; ++tr)
   for (int fs = fs_lo; fs <= fs_hi; ++fs)
   for (int rb = 1; rb <= 2; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
+      p->tc_real = tr != 0;
       fsref = fs != 0;
       p->zs_rb = rb;
       p->use_tc = tc != 0;
@@ -1179,15 +1195,16 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
       ck(cudaEventSynchronize(e1));
       float ms = 0.f;
       ck(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; best_fs = fs != 0; }
+      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; best_fs = fs != 0; best_tr = tr != 0; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->zs_rb = best_rb;
   p->use_tc = best_tc;
   fsref = best_fs;
+  p->tc_real = best_tr;
   p->timing = timing;
-  return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0);
+  return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0) + (best_tr ? 1000 : 0);
 }
 
 }  // namespace
@@ -1554,6 +1571,12 @@ hz_status hz_plan_set_fast_sine(hz_plan_t p, int enable) {
   if (!p || enable < 0 || enable > 2) return HZ_ERR_ARG;
   p->fast_sine = enable >= 1;
   p->fast_sine32 = enable == 2;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_real_tables(hz_plan_t p, int enable) {
+  if (!p) return HZ_ERR_ARG;
+  p->tc_real = enable != 0;
   return HZ_OK;
 }
 
@@ -1934,6 +1957,7 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   p->info.device_bytes = p->bytes;
   p->info.tensor_cores = p->use_tc ? 1 : 0;
   p->info.fast_sine = p->has_dst ? (p->fast_sine32 ? 2 : (p->fast_sine ? 1 : 0)) : 0;
+  p->info.real_tables = (p->tc_real && p->has_real_tc) ? 1 : 0;
   *out = p->info;
   return HZ_OK;
 }

@@ -126,53 +126,62 @@ enum XformStore { XS_STORE = 0, XS_ACCUM = 1 };
 
 // Tensor-core (tcgen05 kind::tf32, 3xTF32) version of the bulk transforms.  Per block the
 // complex table B (n x n) is stored as the real interleaved matrix B' (2n x 2n) transposed
-// to K-major, padded to npad (multiple of 16) rows and kpad (multiple of 32) columns, as
-// TF32 hi (npad x kpad floats at toff) followed by TF32 lo (same size).
+// to K-major, padded to npad (multiple of 16) rows and kpad (multiple of 16) columns, as
+// TF32 hi (npad x kpad floats at toff) followed by TF32 lo (same size).  A block whose table
+// is real also has the real table itself, K-major (npad_r x kpad_r at toff_r, hi then lo), for
+// the real-table kernel, which transforms the real and imaginary parts of the data as two
+// rows of one real GEMM (K = N = n instead of 2n).
 struct TCBlock {
   int start;            // first complex column of the block
   int size;             // complex width n
   int npad, kpad;
-  long long toff;       // float offset of the hi table
+  long long toff;       // float offset of the hi table (interleaved complex form)
+  int npad_r, kpad_r;   // real form (real tables only; npad_r = 0 otherwise)
+  long long toff_r;
 };
 struct TCTile {
   int blk;
-  int n0;               // first real output column (multiple of 16)
-  int nt;               // real output columns (multiple of 16, <= 256)
+  int n0;               // first output column (interleaved: real column, multiple of 16; real
+                        //   kernel: complex column, multiple of 16)
+  int nt;               // output columns (multiple of 16; <= 160 interleaved, <= 128 real)
   int pad;
+};
+// A list of output tiles with one 128-byte TMA tensor map per tile (its table rows).
+struct TCList {
+  int ntiles = 0;
+  int nt_max = 16;
+  TCTile* d_tiles = nullptr;
+  unsigned char* d_tmaps = nullptr;
 };
 struct TCSet {
   int ncols = 0;
-  int ntiles = 0;
-  int nt_max = 16;
   TCBlock* d_blocks = nullptr;
-  TCTile* d_tiles = nullptr;
   float* d_tab = nullptr;
-  unsigned char* d_tmaps = nullptr;   // one 128-byte TMA tensor map per tile (its table rows)
-  // the tiles of the blocks without a fast sine transform, with their tensor maps (mixed path
-  // with fast_sine: the other blocks go through dst_f32)
-  int ntiles_nf = 0;
-  TCTile* d_tiles_nf = nullptr;
-  unsigned char* d_tmaps_nf = nullptr;
+  // Tile lists per variant v = fast + 2 real: fast leaves the uniform blocks with a fast sine
+  // transform to dst_f32; real sends the blocks with real tables to the real-table kernel.
+  // cl[v]: tiles of the interleaved complex kernel, rl[v]: tiles of the real-table kernel.
+  TCList cl[4], rl[4];
 };
 // Encode the TMA tensor maps of the tiles (tables already on the device at d_tab) into
-// 128-byte records; false if the driver offers no encoder or rejects a map.
+// 128-byte records; real: the tiles index the real tables.  false if the driver offers no
+// encoder or rejects a map.
 bool tc_encode_tmaps(const float* d_tab, const std::vector<TCBlock>& blocks, const std::vector<TCTile>& tiles,
-                     std::vector<unsigned char>& bytes);
+                     std::vector<unsigned char>& bytes, bool real = false);
 size_t xform_tc_smem(int nt_max, bool in32);
-// Set the tensor-core kernel's shared-memory limit on the current device (before any capture).
+// Set the tensor-core kernels' shared-memory limits on the current device (before any capture).
 void xform_tc_prepare();
 // Host: append the TF32 hi/lo K-major tables of one block (complex table B, n x n row-major,
-// B[a][c]) and its output tiles.
+// B[a][c]) and its output tiles; with real_tiles (B real) also the real form and its tiles.
 void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
-                   std::vector<TCTile>& tiles, int blk_index);
+                   std::vector<TCTile>& tiles, int blk_index, std::vector<TCTile>* real_tiles = nullptr);
 // err: device status word (set to HZ_ERR_TIMEOUT if a bounded wait gives up).
 // in32 / out32: the input / output are complex64 (float2) instead of complex128 (double2).
 // Returns false (nothing launched) for XS_ACCUM with a complex64 output.
-// products: 3 (3xTF32) or 1 (plain TF32).  skip_fast: only the tiles of the blocks without a
-// fast sine transform.
+// products: 3 (3xTF32) or 1 (plain TF32).  skip_fast: leave out the blocks with a fast sine
+// transform; real_tables: blocks with real tables through the real-table kernel.
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st, int products = 3, bool skip_fast = false);
+              cudaStream_t st, int products = 3, bool skip_fast = false, bool real_tables = false);
 
 // FP64 transform (DFMA): rows_per_plane rows of length ncols per plane, nplanes planes.
 // trans = 1 writes out[plane][col][row] (plane of ncols x rows_per_plane); else out

@@ -458,6 +458,247 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Real-table kernel.  When a block's table B is real, C = A B for complex data A is two real
+// products, Re C = Re A B and Im C = Im A B.  The MMA rows are the data rows' parts
+// (MMA row m = 2 r + u: data row r, u = 0 real / 1 imaginary part), K = N = n (half of the
+// interleaved form's 2n each way, so a quarter of its MMA work per data row, half per
+// output value).  One CTA (4 warps) takes 64 data rows x nt <= 128 columns: 128 TMEM
+// columns and about 53 KB of shared memory, so four CTAs share an SM.  The chunk loop is the
+// interleaved kernel's (16 K per chunk, data in registers one chunk ahead, two operand stages,
+// one TMA copy of the table rows per chunk); in the epilogue each lane pair (2r, 2r+1) trades
+// half of its columns so that every lane writes whole complex values.
+// ---------------------------------------------------------------------------
+constexpr int TCR_THREADS = 128;
+constexpr int TCR_ROWS = TC_M / 2;                  // data rows per CTA
+constexpr int TCR_TMEM = 128;                       // TMEM columns (nt <= 128)
+constexpr int kTcrMaxN = 128;
+constexpr int TCR_CTAS_PER_SM = 4;
+
+template <typename TI, typename TO, int NP>
+__global__ void __launch_bounds__(TCR_THREADS, TCR_CTAS_PER_SM)
+xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* __restrict__ blocks,
+                 const TCTile* __restrict__ tiles, const unsigned char* __restrict__ tmaps, int ntiles,
+                 long long nrows, int rows_per_plane, int ncols, int trans, int store,
+                 const signed char* __restrict__ rowskip, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_dyn[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  const int tile = (int)(blockIdx.x % ntiles);
+  const TCTile t = tiles[tile];
+  const void* tmap = tmaps + (size_t)tile * 128;
+  const TCBlock b = blocks[t.blk];
+  const long long row0 = (long long)(blockIdx.x / ntiles) * TCR_ROWS;
+  const int nt = t.nt;
+  const int B_BYTES = nt * ROWB;
+  constexpr bool IN32 = sizeof(TI) == 8, OUT32 = sizeof(TO) == 8;
+  constexpr int NB = 2;
+  const uint32_t s_base = smem_u32(smem);
+  const uint32_t aop0 = s_base, bop0 = aop0 + 2 * 2 * A_BYTES;
+  const uint32_t BSTAGE = 2 * B_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * A_BYTES + NB * BSTAGE);
+  uint64_t* tbars = bars + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + NB);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = b.size;
+  const int nk = b.kpad_r / KCH;
+
+  // conversion task q: data row r = task / 4, complex columns 4 u .. 4 u + 3 of the chunk (u = task
+  // % 4) -> one 16-byte TF32 unit of MMA row 2 r (real parts) and of row 2 r + 1 (imaginary)
+  constexpr int NTASK = TCR_ROWS * (KCH / 4) / TCR_THREADS;
+  TI dreg[NTASK][4];
+  auto load_regs = [&](int c) {
+#pragma unroll
+    for (int q = 0; q < NTASK; ++q) {
+      const int task = tid + TCR_THREADS * q;
+      const int r = task >> 2, u = task & 3;
+      const long long grow = row0 + r;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int col = c * KCH + 4 * u + h;
+        TI v;
+        if constexpr (IN32) v = make_float2(0.f, 0.f);
+        else v = make_double2(0.0, 0.0);
+        if (grow < nrows && col < n) v = __ldg(in + grow * (long long)ncols + b.start + col);
+        dreg[q][h] = v;
+      }
+    }
+  };
+  auto load_b = [&](int c) {
+    uint64_t* tb = &tbars[c % NB];
+    mbar_expect_tx(tb, (uint32_t)(2 * B_BYTES));
+    tma_load_3d(bop0 + (c % NB) * BSTAGE, tmap, c * KCH, t.n0, 0, tb);
+  };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TCR_TMEM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    for (int q = 0; q < NB; ++q) mbar_init(&tbars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_b(0);
+  }
+  load_regs(0);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_tf32(nt);
+  bool ok = true;
+  int issued = 0;
+  int tab_issued = (tid == 0) ? 1 : 0, tab_done = 0;
+  // iteration kc as in the interleaved kernel: (1) MMAs of kc-2 done (stage kc & 1 free);
+  // (2) convert chunk kc from registers, start loading kc+1; (3) table rows of kc arrived;
+  // (4) queue the MMAs of kc; (5) table rows of kc+1 into the stage the MMAs of kc-1 read
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    int w = 1;
+    if (kc >= 2) w = mbar_wait(&bars[s], ((kc - 2) >> 1) & 1) ? 1 : 0;
+    if (!__syncthreads_and(w)) { ok = false; break; }
+    {
+      const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
+#pragma unroll
+      for (int q = 0; q < NTASK; ++q) {
+        const int task = tid + TCR_THREADS * q;
+        const int r = task >> 2, u = task & 3;
+        float fr[4], fi[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          if constexpr (IN32) {
+            fr[h] = dreg[q][h].x;
+            fi[h] = dreg[q][h].y;
+          } else {
+            fr[h] = f64_to_f32_trunc(dreg[q][h].x);
+            fi[h] = f64_to_f32_trunc(dreg[q][h].y);
+          }
+        }
+        uint32_t hr[4], lr[4], hi[4], li[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          hr[h] = to_tf32(fr[h]);
+          hi[h] = to_tf32(fi[h]);
+          if (NP == 3) {
+            lr[h] = to_tf32(fr[h] - __uint_as_float(hr[h]));
+            li[h] = to_tf32(fi[h] - __uint_as_float(hi[h]));
+          }
+        }
+        const uint32_t offr = swz64(2 * r, u), offi = swz64(2 * r + 1, u);
+        st_shared_v4(a_hi + offr, hr[0], hr[1], hr[2], hr[3]);
+        st_shared_v4(a_hi + offi, hi[0], hi[1], hi[2], hi[3]);
+        if (NP == 3) {
+          st_shared_v4(a_lo + offr, lr[0], lr[1], lr[2], lr[3]);
+          st_shared_v4(a_lo + offi, li[0], li[1], li[2], li[3]);
+        }
+      }
+    }
+    if (kc + 1 < nk) load_regs(kc + 1);
+    int w2 = 1;
+    if (tid == 0) {
+      if (tab_done < tab_issued && mbar_wait(&tbars[kc % NB], (kc / NB) & 1)) tab_done = kc + 1;
+      if (tab_done != kc + 1) w2 = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(w2)) { ok = false; break; }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_hi = aop0 + s * 2 * A_BYTES, a_lo = a_hi + A_BYTES;
+      const uint32_t b_hi = bop0 + (kc % NB) * BSTAGE, b_lo = b_hi + B_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < KCH / 8; ++ks) {
+        const uint32_t koff = ks * 32;
+        const uint64_t dah = smem_desc_sw64(a_hi + koff), dal = smem_desc_sw64(a_lo + koff);
+        const uint64_t dbh = smem_desc_sw64(b_hi + koff), dbl = smem_desc_sw64(b_lo + koff);
+        const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+        mma_tf32(tmem, dah, dbh, idesc, first);
+        if (NP == 3) {
+          mma_tf32(tmem, dah, dbl, idesc, 1u);
+          mma_tf32(tmem, dal, dbh, idesc, 1u);
+        }
+      }
+      mma_commit(&bars[s]);
+      if (kc + 1 < nk) {
+        bool free_stage = true;
+        if (kc >= 1) free_stage = mbar_wait(&bars[(kc - 1) & 1], ((kc - 1) >> 1) & 1);
+        if (free_stage) { load_b(kc + 1); tab_issued = kc + 2; }
+      }
+    }
+    issued = kc + 1;
+  }
+  if (tid == 0 && tab_done < tab_issued) {
+    const int c = tab_issued - 1;
+    mbar_wait(&tbars[c % NB], (c / NB) & 1);
+  }
+  if (issued > 0) {
+    const int last = issued - 1;
+    if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) ok = false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int all_ok = __syncthreads_and(ok ? 1 : 0);
+  if (all_ok) {
+    // TMEM lane m = 32 warp + lane holds MMA row m: data row r = m / 2, part = m % 2
+    const int m = warp * 32 + lane;
+    const int r = m >> 1;
+    const bool odd = (lane & 1) != 0;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const long long grow = row0 + r;
+    bool row_ok = grow < nrows;
+    long long plane = 0;
+    int rip = 0;
+    if (row_ok) {
+      plane = grow / rows_per_plane;
+      rip = (int)(grow - plane * rows_per_plane);
+      if (rowskip && rowskip[rip]) row_ok = false;
+    }
+    for (int c16 = 0; c16 < nt; c16 += 16) {
+      float v[16];
+      tmem_ld16(tl + c16, v);
+      // the even lane (real parts) keeps columns c16..c16+7, the odd lane (imaginary parts) the
+      // next eight: each sends the partner's half
+      float part[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float send = odd ? v[e] : v[8 + e];
+        part[e] = __shfl_xor_sync(0xffffffffu, send, 1);
+      }
+      if (!row_ok) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int ccol = t.n0 + c16 + (odd ? 8 : 0) + e;      // complex column within the block
+        if (ccol >= n) continue;
+        const float re = odd ? part[e] : v[e];
+        const float im = odd ? v[8 + e] : part[e];
+        TO* p = trans ? out + plane * (long long)ncols * rows_per_plane + (long long)(b.start + ccol) * rows_per_plane + rip
+                      : out + grow * (long long)ncols + b.start + ccol;
+        if constexpr (OUT32) {
+          *p = make_float2(re, im);
+        } else {
+          double2 val = make_double2(f32_to_f64(re), f32_to_f64(im));
+          if (store == XS_ACCUM) {
+            const double2 o = *p;
+            val.x += o.x;
+            val.y += o.y;
+          }
+          *p = val;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, (int)HZ_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCR_TMEM));
+}
+
+size_t xform_tcr_smem(int nt_max) {
+  // at least 46 KB, so that no more than four CTAs (TCR_TMEM columns each) share an SM
+  const size_t need = 1024 + 4 * (size_t)A_BYTES + 2 * 2 * (size_t)nt_max * ROWB + 64;
+  return std::max(need, (size_t)46 * 1024);
+}
+
 float tf32_round_host(double x) {
   // round an FP32 value to TF32 (10 explicit mantissa bits), nearest, ties away from zero
   float f = (float)x;
@@ -471,9 +712,11 @@ float tf32_round_host(double x) {
 }  // namespace
 
 void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlock& blk,
-                   std::vector<TCTile>& tiles, int blk_index) {
+                   std::vector<TCTile>& tiles, int blk_index, std::vector<TCTile>* real_tiles) {
   blk.start = start;
   blk.size = n;
+  blk.npad_r = blk.kpad_r = 0;
+  blk.toff_r = 0;
   blk.npad = ((2 * n + 15) / 16) * 16;
   blk.kpad = ((2 * n + KCH - 1) / KCH) * KCH;
   blk.toff = (long long)tab.size();
@@ -502,10 +745,35 @@ void tc_pack_block(const cd* B, int n, int start, std::vector<float>& tab, TCBlo
     tiles.push_back(TCTile{blk_index, n0, w, 0});
     n0 += w;
   }
+  if (!real_tiles) return;
+  // the real form: T[c][a] = B[a][c], K-major, hi then lo; tiles of at most kTcrMaxN columns
+  blk.npad_r = ((n + 15) / 16) * 16;
+  blk.kpad_r = ((n + KCH - 1) / KCH) * KCH;
+  blk.toff_r = (long long)tab.size();
+  const size_t rplane = (size_t)blk.npad_r * blk.kpad_r;
+  tab.resize(tab.size() + 2 * rplane, 0.0f);
+  float* rhi = tab.data() + blk.toff_r;
+  float* rlo = rhi + rplane;
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) {
+      const double v = B[(size_t)a * n + c].real();
+      const size_t o = (size_t)c * blk.kpad_r + a;
+      const float h = tf32_round_host(v);
+      rhi[o] = h;
+      rlo[o] = tf32_round_host(v - (double)h);
+    }
+  const int rtl = (blk.npad_r + kTcrMaxN - 1) / kTcrMaxN;
+  const int runits = blk.npad_r / 16;
+  int c0 = 0;
+  for (int q = 0; q < rtl; ++q) {
+    const int w = 16 * ((runits * (q + 1)) / rtl - (runits * q) / rtl);
+    real_tiles->push_back(TCTile{blk_index, c0, w, 0});
+    c0 += w;
+  }
 }
 
 bool tc_encode_tmaps(const float* d_tab, const std::vector<TCBlock>& blocks, const std::vector<TCTile>& tiles,
-                     std::vector<unsigned char>& bytes) {
+                     std::vector<unsigned char>& bytes, bool real) {
   using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -524,11 +792,14 @@ bool tc_encode_tmaps(const float* d_tab, const std::vector<TCBlock>& blocks, con
     const TCBlock& b = blocks[tiles[i].blk];
     // [plane][row][k] view of the block's hi | lo tables; box = one chunk of K x the tile's rows
     // x both planes, 64-byte swizzle (the K-major operand layout of the MMA descriptors)
-    const cuuint64_t dims[3] = {(cuuint64_t)b.kpad, (cuuint64_t)b.npad, 2};
-    const cuuint64_t strides[2] = {(cuuint64_t)b.kpad * 4, (cuuint64_t)b.npad * b.kpad * 4};
+    const int kp = real ? b.kpad_r : b.kpad, np = real ? b.npad_r : b.npad;
+    if (np == 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)np, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)kp * 4, (cuuint64_t)np * kp * 4};
     const cuuint32_t box[3] = {(cuuint32_t)KCH, (cuuint32_t)tiles[i].nt, 2};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d_tab + b.toff), dims, strides,
+    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d_tab + (real ? b.toff_r : b.toff)),
+               dims, strides,
                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
@@ -554,6 +825,10 @@ void set_smem_attr() {
                        (int)xform_tc_smem(kTcMaxN, sizeof(TI) == 8));
   cudaFuncSetAttribute(xform_tc_kernel<TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)xform_tc_smem(kTcMaxN, sizeof(TI) == 8));
+  cudaFuncSetAttribute(xform_tcr_kernel<TI, TO, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)xform_tcr_smem(kTcrMaxN));
+  cudaFuncSetAttribute(xform_tcr_kernel<TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)xform_tcr_smem(kTcrMaxN));
 }
 
 void xform_tc_prepare() {
@@ -572,34 +847,44 @@ void xform_tc_prepare() {
 
 bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, int rows_per_plane,
               long long nplanes, int trans, int store, const signed char* rowskip, int* err,
-              cudaStream_t st, int products, bool skip_fast) {
+              cudaStream_t st, int products, bool skip_fast, bool real_tables) {
   if (out32 && store != XS_STORE) return false;          // accumulation needs a complex128 output
-  const TCTile* tiles = skip_fast ? ts.d_tiles_nf : ts.d_tiles;
-  const unsigned char* tmaps = skip_fast ? ts.d_tmaps_nf : ts.d_tmaps;
-  const int ntiles = skip_fast ? ts.ntiles_nf : ts.ntiles;
+  const int v = (skip_fast ? 1 : 0) + (real_tables ? 2 : 0);
+  const TCList& cl = ts.cl[v];
+  const TCList& rl = ts.rl[v];
   const long long nrows = nplanes * (long long)rows_per_plane;
-  if (nrows <= 0 || ntiles == 0) return true;
-  if (!tmaps) return false;
+  if (nrows <= 0) return true;
+  if ((cl.ntiles && !cl.d_tmaps) || (rl.ntiles && !rl.d_tmaps)) return false;
   xform_tc_prepare();
-  const long long ctas = ((nrows + TC_M - 1) / TC_M) * ntiles;
-  const size_t smem = xform_tc_smem(ts.nt_max, in32 != 0);
-#define HZ_TC_LAUNCH(TI, TO, NP)                                                                      \
-  xform_tc_kernel<TI, TO, NP><<<(unsigned)ctas, TC_THREADS, smem, st>>>(                             \
-      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, tiles, tmaps, ntiles, nrows,          \
+#define HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, TI, TO, NP)                                            \
+  K<TI, TO, NP><<<(unsigned)(CTAS), THREADS, SMEM, st>>>(                                              \
+      static_cast<const TI*>(in), static_cast<TO*>(out), ts.d_blocks, L.d_tiles, L.d_tmaps, L.ntiles, nrows, \
       rows_per_plane, ts.ncols, trans, store, rowskip, err)
-  if (products == 1) {
-    if (in32 && out32) HZ_TC_LAUNCH(float2, float2, 1);
-    else if (in32) HZ_TC_LAUNCH(float2, double2, 1);
-    else if (out32) HZ_TC_LAUNCH(double2, float2, 1);
-    else HZ_TC_LAUNCH(double2, double2, 1);
-  } else {
-    if (in32 && out32) HZ_TC_LAUNCH(float2, float2, 3);
-    else if (in32) HZ_TC_LAUNCH(float2, double2, 3);
-    else if (out32) HZ_TC_LAUNCH(double2, float2, 3);
-    else HZ_TC_LAUNCH(double2, double2, 3);
+#define HZ_TC_TYPES(K, CTAS, THREADS, SMEM, L)                                                         \
+  do {                                                                                                 \
+    if (products == 1) {                                                                               \
+      if (in32 && out32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, float2, float2, 1);                  \
+      else if (in32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, float2, double2, 1);                     \
+      else if (out32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, double2, float2, 1);                    \
+      else HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, double2, double2, 1);                              \
+    } else {                                                                                           \
+      if (in32 && out32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, float2, float2, 3);                  \
+      else if (in32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, float2, double2, 3);                     \
+      else if (out32) HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, double2, float2, 3);                    \
+      else HZ_TC_LAUNCH(K, CTAS, THREADS, SMEM, L, double2, double2, 3);                              \
+    }                                                                                                  \
+    count_launch();                                                                                    \
+  } while (0)
+  if (cl.ntiles) {
+    const long long ctas = ((nrows + TC_M - 1) / TC_M) * cl.ntiles;
+    HZ_TC_TYPES(xform_tc_kernel, ctas, TC_THREADS, xform_tc_smem(cl.nt_max, in32 != 0), cl);
   }
+  if (rl.ntiles) {
+    const long long ctas = ((nrows + TCR_ROWS - 1) / TCR_ROWS) * rl.ntiles;
+    HZ_TC_TYPES(xform_tcr_kernel, ctas, TCR_THREADS, xform_tcr_smem(rl.nt_max), rl);
+  }
+#undef HZ_TC_TYPES
 #undef HZ_TC_LAUNCH
-  count_launch();
   return true;
 }
 

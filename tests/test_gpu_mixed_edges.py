@@ -77,3 +77,24 @@ def test_single_product_tf32_mixed_precision(hz, torch_cuda):
         assert rel(u, ref) < TOLMIX
         refinements[precision] = info["refinements"]
     assert refinements["mixed_tf32"] > refinements["mixed"]
+
+
+@pytest.mark.parametrize("real_tables", [True, False])
+def test_real_table_kernel(hz, torch_cuda, real_tables):
+    # real steps everywhere (real block tables): x one block of 130 (two real-table tiles of
+    # 64 and 80 columns), y blocks of 40 and 79; 3 RHS x 5 planes give ragged row tiles
+    torch = torch_cuda
+    rng = np.random.default_rng(23)
+    nx, ny, nz = 130, 120, 5
+    hy = W.rim_axis(ny - 8, rim_nodes=4, ratio=1.2, pml_nodes=0)        # real geometric rim
+    f = rng.standard_normal((3, nz, ny, nx)) + 1j * rng.standard_normal((3, nz, ny, nx))
+    w = W.Workload("real-tables", W.uniform_steps(nx, 0.9), hy, W.ramp_z(nz), np.array([0, 2, nz], np.int32),
+                   np.array([0.3 + 0.02j, 0.2 + 0.01j]), np.zeros(0, np.int32), np.array([40], np.int32), f)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan = hz.Plan.from_workload(w, precision="mixed", rtol=1e-10, max_refine=12)
+    plan.set_real_tables(real_tables)
+    u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+    info = plan.info()
+    assert info["tensor_cores"] == 1 and info["real_tables"] == int(real_tables)
+    assert info["rel_residual"] <= 1e-10
+    assert rel(u, ref) < TOLMIX
