@@ -86,7 +86,8 @@ def test_real_table_kernel(hz, torch_cuda, real_tables):
     torch = torch_cuda
     rng = np.random.default_rng(23)
     nx, ny, nz = 130, 120, 5
-    hy = W.rim_axis(ny - 8, rim_nodes=4, ratio=1.2, pml_nodes=0)        # real geometric rim
+    rim = 1.2 ** np.arange(1, 6)                                        # real geometric rim
+    hy = np.concatenate([rim[::-1], np.ones(ny - 9), rim]).astype(np.complex128)
     f = rng.standard_normal((3, nz, ny, nx)) + 1j * rng.standard_normal((3, nz, ny, nx))
     w = W.Workload("real-tables", W.uniform_steps(nx, 0.9), hy, W.ramp_z(nz), np.array([0, 2, nz], np.int32),
                    np.array([0.3 + 0.02j, 0.2 + 0.01j]), np.zeros(0, np.int32), np.array([40], np.int32), f)
