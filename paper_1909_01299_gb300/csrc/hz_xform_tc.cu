@@ -472,7 +472,9 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
 constexpr int TCR_THREADS = 128;
 constexpr int TCR_ROWS = TC_M / 2;                  // data rows per CTA
 constexpr int TCR_TMEM = 128;                       // TMEM columns (nt <= 128)
-constexpr int kTcrMaxN = 128;
+// widest real tile: the epilogue's staging tile (64 rows x (8 nt + 16) bytes) then fits in the
+// pipeline buffers below the mbarriers (32768 + 256 nt bytes) for every nt <= 112
+constexpr int kTcrMaxN = 112;
 constexpr int TCR_CTAS_PER_SM = 4;
 
 template <typename TI, typename TO, int NP>
@@ -652,7 +654,46 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
       rip = (int)(grow - plane * rows_per_plane);
       if (rowskip && rowskip[rip]) row_ok = false;
     }
-    for (int c16 = 0; c16 < nt; c16 += 16) {
+    if (!trans) {
+      // rows are contiguous in memory: stage the tile as complex64 (row stride 8 nt + 16 bytes)
+      // in the idle pipeline buffers, then each warp writes whole rows, consecutive lanes on
+      // consecutive columns
+      const int sstride = nt * 8 + 16;
+      for (int c16 = 0; c16 < nt; c16 += 16) {
+        float v[16];
+        tmem_ld16(tl + c16, v);
+        float* dst = reinterpret_cast<float*>(smem + (size_t)r * sstride) + 2 * c16 + (odd ? 1 : 0);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) dst[2 * e] = v[e];
+      }
+      __syncthreads();
+      const int ccount = min(nt, n - t.n0);
+      for (int rr = warp; rr < TCR_ROWS; rr += TCR_THREADS / 32) {
+        const long long g = row0 + rr;
+        if (g >= nrows) break;
+        if (rowskip) {
+          const long long pl = g / rows_per_plane;
+          if (rowskip[g - pl * rows_per_plane]) continue;
+        }
+        const float2* srow = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
+        TO* dg = out + g * (long long)ncols + b.start + t.n0;
+        for (int c = lane; c < ccount; c += 32) {
+          const float2 f = srow[c];
+          if constexpr (OUT32) {
+            dg[c] = f;
+          } else {
+            double2 val = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
+            if (store == XS_ACCUM) {
+              const double2 o = dg[c];
+              val.x += o.x;
+              val.y += o.y;
+            }
+            dg[c] = val;
+          }
+        }
+      }
+    }
+    for (int c16 = 0; trans && c16 < nt; c16 += 16) {
       float v[16];
       tmem_ld16(tl + c16, v);
       // the even lane (real parts) keeps columns c16..c16+7, the odd lane (imaginary parts) the
@@ -670,8 +711,7 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
         if (ccol >= n) continue;
         const float re = odd ? part[e] : v[e];
         const float im = odd ? v[8 + e] : part[e];
-        TO* p = trans ? out + plane * (long long)ncols * rows_per_plane + (long long)(b.start + ccol) * rows_per_plane + rip
-                      : out + grow * (long long)ncols + b.start + ccol;
+        TO* p = out + plane * (long long)ncols * rows_per_plane + (long long)(b.start + ccol) * rows_per_plane + rip;
         if constexpr (OUT32) {
           *p = make_float2(re, im);
         } else {
