@@ -51,7 +51,7 @@ def parse():
                     help="right-hand sides of an extra workload (default: the workload's own count)")
     ap.add_argument("--workload", default="uniform320",
                     choices=["uniform320", "pml160", "adjoint192", "uniform32", "batch48", "scaling", "perturbed160",
-                             "uniform320x40"],
+                             "uniform320x40", "longz"],
                     help="uniform320 is the benchmark line; the others are extra measurements")
     return ap.parse_args()
 
@@ -702,7 +702,7 @@ def run_extra(args):
     else:
         gen = {"uniform320": W.uniform_320x320x200, "adjoint192": W.adjoint_192x192x128,
                "uniform32": W.single_block_32, "pml160": W.pml_160x160x128,
-               "uniform320x40": W.uniform_320x320x40}[args.workload]
+               "uniform320x40": W.uniform_320x320x40, "longz": W.long_z}[args.workload]
         w = gen(args.nrhs) if args.nrhs else gen()
         f = torch.from_numpy(w.f).cuda()
         u = torch.empty_like(f)

@@ -194,6 +194,19 @@ def uniform_320x320x40(nrhs: int = 2) -> Workload:
                     default_ifaces(nx, 4), default_ifaces(ny, 4), f, precision="mixed")
 
 
+def long_z(nx: int = 32, ny: int = 32, nz: int = 4096, nrhs: int = 4, bx: int = 2, by: int = 2) -> Workload:
+    """Few modes, long z: a narrow column (nx x ny nodes, h = 1, bx x by blocks) of nz ramped
+    z steps with 64 layers, seeded complex noise.  The regime where one z sweep per mode leaves
+    most of the GPU idle (nx ny nrhs sweeps of length nz)."""
+    rng = np.random.default_rng(SEED_BASE + 6)
+    nl = 64
+    k2 = (rng.uniform(0.05, 0.5, nl) * (1 + 0.02j)).astype(np.complex128)
+    z_begin = np.array([(nz * L) // nl for L in range(nl + 1)], dtype=np.int32)
+    f = _cnoise(rng, (nrhs, nz, ny, nx))
+    return Workload(f"longz-{nx}x{ny}x{nz}-{bx}x{by}blocks-{nrhs}rhs", uniform_steps(nx), uniform_steps(ny),
+                    ramp_z(nz, 0.5, 1.0), z_begin, k2, default_ifaces(nx, bx), default_ifaces(ny, by), f)
+
+
 def adjoint_192x192x128(nsrc: int = 16) -> Workload:
     """192x192x128, PML rim in x/y, uniform z, 32 layers of 4 planes, 2x2 blocks.
 
@@ -276,5 +289,6 @@ NAMED = {
     "pml160": pml_160x160x128,
     "uniform320": uniform_320x320x200,
     "uniform320x40": uniform_320x320x40,
+    "longz": long_z,
     "adjoint192": adjoint_192x192x128,
 }

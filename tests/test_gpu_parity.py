@@ -436,3 +436,12 @@ def test_auto_partition_matches_lu(hz, torch_cuda):
         info = plan.info()
         assert (info["nbx"], info["nby"]) == counts
         assert rel(u, ref) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_long_z_few_modes(hz, torch_cuda, precision):
+    # few modes, long z: 13 x 11 nodes in 2 x 2 blocks, 1536 ramped z steps, 2 RHS
+    w = W.long_z(nx=13, ny=11, nz=1536, nrhs=2)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    _, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
