@@ -131,6 +131,7 @@ typedef struct {
                                 the plan has no such block)                              */
   int real_tables;           /* 1 when the mixed path's real block tables run the
                                 real-table tensor-core kernel (hz_plan_set_real_tables)  */
+  int z_sweep;               /* z sweep variant set (hz_plan_set_z_sweep; 0 automatic)  */
 } hz_info;
 
 /* Stage timers: when enabled, every solve records CUDA events on the plan's
@@ -174,12 +175,12 @@ hz_status hz_plan_set_frequency(hz_plan_t plan, double omega);
 hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
 
 /* Autotuner: times one solve of nrhs right-hand sides (on zero data, in the plan's
- * workspace) for each kernel variant the plan can use -- one or two right-hand sides per
- * thread in the z sweeps ("pencil batch"), for mixed plans tensor-core or CUDA-core FP32
+ * workspace) for each kernel variant the plan can use -- the three z sweep variants of
+ * hz_plan_set_z_sweep, for mixed plans tensor-core or CUDA-core FP32
  * bulk transforms and the real-table or interleaved tensor-core kernel, for plans with
  * uniform blocks the fast sine transform or the dense product -- and keeps the fastest.
  * *choice_out (may be NULL) receives
- * rhs_per_thread + 10 * tensor_cores + 100 * fast_sine + 1000 * real_tables. */
+ * z_sweep + 10 * tensor_cores + 100 * fast_sine + 1000 * real_tables. */
 hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
 
 /* Transform the uniform blocks (all steps equal and real, so that the block's eigenvectors
@@ -192,6 +193,15 @@ hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
  * transforms through the fast transform, in FP32.  The autotuner times both choices of the
  * plan's path.  HZ_ERR_ARG for other values. */
 hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
+
+/* The mode-wise z eliminations of Eq. (fdmtrprjfr) and Eq. (fdmtrprjfrerr) (Thomas sweeps, one
+ * thread per mode and right-hand side): variant 1 one right-hand side per thread, 2 two per
+ * thread sharing each factor load, 3 one per thread with z taken in register chunks of 16 steps
+ * (all loads of a chunk in flight together, one complex multiply-add on the dependency chain:
+ * for few modes and long z, where the sweeps cannot fill the GPU); 0 (the default): variant 3
+ * when a launch has fewer than 512 sweeps per SM, else 1.  Same elimination in FP64; variant 3
+ * rounds the forward step in another order.  HZ_ERR_ARG for other values. */
+hz_status hz_plan_set_z_sweep(hz_plan_t plan, int variant);
 
 /* Mixed path: blocks whose eigenvector tables are real (all their steps real) run the
  * tensor-core transform as two real products, Re C = Re A B and Im C = Im A B, each with K = N =

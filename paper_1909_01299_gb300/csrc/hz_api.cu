@@ -98,7 +98,8 @@ struct hz_plan_s {
   bool tc_real = true;               // mixed path: real tables through the real-table kernel
   bool has_real_tc = false;          // some block has a real table
   bool has_dst = false;              // some block has a fast sine transform
-  int zs_rb = 1;                     // right-hand sides per thread in the z sweeps (autotuned)
+  int zs_rb = 0;                     // z sweep variant (hz_plan_set_z_sweep; 0 automatic; autotuned)
+  int sms = 0;                       // SM count of the plan's device
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -903,6 +904,7 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   za.rhs = w.FT; za.out = w.V;
   za.P = p->Pb; za.Q = p->Qb; za.cm = p->cm_b;
   za.rhs_per_thread = p->zs_rb;
+  za.sms = p->sms;
   if (c64) { za.rhs32 = FT32; za.out32 = V32; za.scratch = w.V; }
   // Step 2: mode-wise z solves of every block (pass A)
   {
@@ -1182,7 +1184,7 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   const int fs_hi = p->has_dst ? 1 : fs_lo;
   for (int tr = tr_lo; tr <= tr_hi; ++tr)
   for (int fs = fs_lo; fs <= fs_hi; ++fs)
-  for (int rb = 1; rb <= 2; ++rb)
+  for (int rb = 1; rb <= 3; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
       p->tc_real = tr != 0;
       fsref = fs != 0;
@@ -1500,6 +1502,7 @@ hz_status hz_plan_create(const hz_grid* grid, const hz_layers* layers, const hz_
   if (s != HZ_OK) { delete p; return s; }
   try {
     ck(cudaGetDevice(&p->device));
+    ck(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
     hz::dst_prepare(hz::kDstMaxN);
     ck(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     ck(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
@@ -1577,6 +1580,12 @@ hz_status hz_plan_set_fast_sine(hz_plan_t p, int enable) {
 hz_status hz_plan_set_real_tables(hz_plan_t p, int enable) {
   if (!p) return HZ_ERR_ARG;
   p->tc_real = enable != 0;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_z_sweep(hz_plan_t p, int variant) {
+  if (!p || variant < 0 || variant > 3) return HZ_ERR_ARG;
+  p->zs_rb = variant;
   return HZ_OK;
 }
 
@@ -1958,6 +1967,7 @@ hz_status hz_get_info(hz_plan_t p, hz_info* out) {
   p->info.tensor_cores = p->use_tc ? 1 : 0;
   p->info.fast_sine = p->has_dst ? (p->fast_sine32 ? 2 : (p->fast_sine ? 1 : 0)) : 0;
   p->info.real_tables = (p->tc_real && p->has_real_tc) ? 1 : 0;
+  p->info.z_sweep = p->zs_rb;
   *out = p->info;
   return HZ_OK;
 }

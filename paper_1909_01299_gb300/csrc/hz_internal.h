@@ -217,7 +217,10 @@ struct ZSolveArgs {
   const signed char* skip_j = nullptr;
   int nx = 0, ny = 0, nz = 0, nrhs = 0;
   int real_cm = 0;
-  int rhs_per_thread = 0;                // 1 or 2; 0 = chosen from the launch size
+  // sweep variant: 1 or 2 right-hand sides per thread, 3 one per thread with z taken in
+  // register chunks (few sweeps, long z); 0 = chosen from the launch size and sms
+  int rhs_per_thread = 0;
+  int sms = 0;                           // SM count of the device (automatic choice)
   // complex64 storage (mixed path): when rhs32 is set, the right-hand side is read from
   // rhs32, the result written to out32 (truncated to FP32) and the FP64 forward-sweep
   // values kept in scratch (same layout); the elimination itself stays FP64

@@ -111,6 +111,82 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   }
 }
 
+// Few sweeps, long z.  With one thread per sweep and too few sweeps to fill the GPU, the plain
+// kernel waits a full memory latency for every z step (its next loads sit behind the current
+// step's store).  Here each thread takes z in chunks of ZD steps: all loads of a chunk (P_k,
+// the right-hand side, c_k; Q_k and the forward values on the way back) are issued together
+// into registers, then the chunk's steps run, with the plain kernel's arithmetic.  (With a
+// warp or two per SM sub-partition the step time is then the FP64 pipe's: one warp
+// instruction per 64 clocks per sub-partition, 6 of them per forward step with a real c_k,
+// 4 per back step.  A form with one multiply-add on the dependency chain,
+// y_k = (b_k P_k) - (c_k P_k) y_{k-1}, issues 10 and measured slower.)
+constexpr int ZD = 16;
+
+template <bool REALCM, bool C64>
+__global__ void __launch_bounds__(128) zsolve_chunk_kernel(const ZSolveArgs a) {
+  const long long plane = (long long)a.nx * a.ny;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= plane * a.nrhs) return;
+  const int r = (int)(tid / plane);
+  const long long pos = tid - (long long)r * plane;
+  const int i = (int)(pos / a.ny), j = (int)(pos - (long long)i * a.ny);
+  if (a.skip_i && (a.skip_i[i] | a.skip_j[j])) return;
+  const long long base = r * plane * a.nz + pos;
+  double2* __restrict__ fw = (C64 ? a.scratch : a.out) + base;
+  const double2* __restrict__ P = a.P + pos;
+  const double2* __restrict__ Q = a.Q + pos;
+  const double2* __restrict__ cm = a.cm;
+  const int nz = a.nz;
+
+  double2 y = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < nz; k0 += ZD) {
+    double2 pk[ZD], bk[ZD], ck[ZD];
+#pragma unroll
+    for (int d = 0; d < ZD; ++d) {
+      const int k = k0 + d;
+      if (k < nz) {
+        pk[d] = P[(long long)k * plane];
+        if constexpr (C64) bk[d] = to_c128(a.rhs32[base + (long long)k * plane]);
+        else bk[d] = a.rhs[base + (long long)k * plane];
+        ck[d] = cm[k];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ZD; ++d) {
+      const int k = k0 + d;
+      if (k < nz) {
+        const double2 c = ck[d];
+        const double2 t = REALCM ? make_double2(fma(-c.x, y.x, bk[d].x), fma(-c.x, y.y, bk[d].y))
+                                 : csub_mul(bk[d], c, y);
+        y = cmul(t, pk[d]);
+        fw[(long long)k * plane] = y;
+      }
+    }
+  }
+  if constexpr (C64) a.out32[base + (long long)(nz - 1) * plane] = to_c64t(y);
+  // back substitution over k = nz - 2 .. 0 in chunks of ZD (the last chunk may be short)
+  for (int k1 = nz - 2; k1 >= 0; k1 -= ZD) {
+    double2 qk[ZD], yk[ZD];
+#pragma unroll
+    for (int d = 0; d < ZD; ++d) {
+      const int k = k1 - d;
+      if (k >= 0) {
+        qk[d] = Q[(long long)k * plane];
+        yk[d] = fw[(long long)k * plane];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ZD; ++d) {
+      const int k = k1 - d;
+      if (k >= 0) {
+        y = csub_mul(yk[d], qk[d], y);
+        if constexpr (C64) a.out32[base + (long long)k * plane] = to_c64t(y);
+        else fw[(long long)k * plane] = y;
+      }
+    }
+  }
+}
+
 constexpr int RT = 256, REPT = 4;      // right-hand-side kernels: threads, positions per thread
 
 // The right-hand-side kernels below first compute all REPT values of a thread and only
@@ -321,9 +397,28 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
 void zsolve(const ZSolveArgs& a, cudaStream_t st) {
   if ((long long)a.nx * a.ny * a.nrhs == 0) return;
   const int T = 128;
-  // one right-hand side per thread unless asked otherwise (measured faster on GB300 for
-  // the benchmark sizes: more independent sweeps in flight beat shared factor loads)
-  const int rb = (a.rhs_per_thread == 2) ? 2 : 1;
+  int variant = a.rhs_per_thread;
+  if (variant < 1 || variant > 3) {
+    // automatic: the chunked sweep when the sweeps fill less than 512 threads per SM (the
+    // plain kernel then waits a memory latency per z step), else one right-hand side per
+    // thread (measured faster on GB300 at the benchmark sizes than two per thread: more
+    // independent sweeps in flight beat shared factor loads)
+    const long long sweeps = (long long)a.nx * a.ny * a.nrhs;
+    variant = (a.sms > 0 && sweeps < 512LL * a.sms) ? 3 : 1;
+  }
+  if (variant == 3) {
+    const unsigned grid = (unsigned)(((long long)a.nx * a.ny * a.nrhs + T - 1) / T);
+    const int v = (a.rhs32 ? 2 : 0) + (a.real_cm ? 1 : 0);
+    switch (v) {
+      case 0: zsolve_chunk_kernel<false, false><<<grid, T, 0, st>>>(a); break;
+      case 1: zsolve_chunk_kernel<true, false><<<grid, T, 0, st>>>(a); break;
+      case 2: zsolve_chunk_kernel<false, true><<<grid, T, 0, st>>>(a); break;
+      default: zsolve_chunk_kernel<true, true><<<grid, T, 0, st>>>(a); break;
+    }
+    count_launch();
+    return;
+  }
+  const int rb = variant;
   const long long n = (long long)a.nx * a.ny * ((a.nrhs + rb - 1) / rb);
   const unsigned grid = (unsigned)((n + T - 1) / T);
   const int v = (a.rhs32 ? 4 : 0) + (rb == 2 ? 2 : 0) + (a.real_cm ? 1 : 0);

@@ -49,7 +49,8 @@ class hz_info(ctypes.Structure):
                 ("min_abs_pivot", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("eig_max_residual", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("nbx", ctypes.c_int), ("nby", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int), ("fast_sine", ctypes.c_int), ("real_tables", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("fast_sine", ctypes.c_int), ("real_tables", ctypes.c_int),
+                ("z_sweep", ctypes.c_int)]
 
 
 # Every symbol declared in include/hz.h, with its ctypes signature.
@@ -63,6 +64,7 @@ SIGNATURES = {
     "hz_plan_set_options": (ctypes.c_int, [_P, ctypes.POINTER(hz_options)]),
     "hz_plan_set_fast_sine": (ctypes.c_int, [_P, ctypes.c_int]),
     "hz_plan_set_real_tables": (ctypes.c_int, [_P, ctypes.c_int]),
+    "hz_plan_set_z_sweep": (ctypes.c_int, [_P, ctypes.c_int]),
     "hz_sine_transform_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P]),
     "hz_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
@@ -217,13 +219,18 @@ class Plan:
         """hz_plan_autotune: pick the fastest kernel variants for nrhs right-hand sides."""
         c = ctypes.c_int()
         _check(_lib.hz_plan_autotune(self._h, int(nrhs), ctypes.byref(c)), "hz_plan_autotune")
-        return {"rhs_per_thread": c.value % 10, "tensor_cores": (c.value // 10) % 10 == 1,
+        return {"z_sweep": c.value % 10, "tensor_cores": (c.value // 10) % 10 == 1,
                 "fast_sine": (c.value // 100) % 10 == 1, "real_tables": c.value >= 1000}
 
     def set_real_tables(self, enable: bool):
         """Mixed path: real block tables through the real-table tensor-core kernel (True, the
         default) or the interleaved complex GEMM (False) (hz_plan_set_real_tables)."""
         _check(_lib.hz_plan_set_real_tables(self._h, int(bool(enable))), "hz_plan_set_real_tables")
+
+    def set_z_sweep(self, variant: int):
+        """z sweep variant (hz_plan_set_z_sweep): 1 or 2 right-hand sides per thread, 3 z in
+        register chunks (few modes, long z), 0 (default) chosen per launch."""
+        _check(_lib.hz_plan_set_z_sweep(self._h, int(variant)), "hz_plan_set_z_sweep")
 
     def set_fast_sine(self, enable: int):
         """Uniform blocks by the FFT-based sine transform (hz_plan_set_fast_sine): 0 dense

@@ -438,10 +438,40 @@ def test_auto_partition_matches_lu(hz, torch_cuda):
         assert rel(u, ref) < tol
 
 
+_REFS = {}
+
+
+def _oracle_ref(key, make):
+    """The oracle's sparse-LU solution of a seeded workload, computed once per module."""
+    if key not in _REFS:
+        w = make()
+        _REFS[key] = (w, O.solve(O.Problem.from_workload(w), w.f))
+    return _REFS[key]
+
+
+@pytest.mark.parametrize("z_sweep", [0, 1, 3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_long_z_few_modes(hz, torch_cuda, precision):
-    # few modes, long z: 13 x 11 nodes in 2 x 2 blocks, 1536 ramped z steps, 2 RHS
-    w = W.long_z(nx=13, ny=11, nz=1536, nrhs=2)
-    ref = O.solve(O.Problem.from_workload(w), w.f)
-    _, u = gpu_solve(hz, torch_cuda, w, precision=precision)
+def test_long_z_few_modes(hz, torch_cuda, precision, z_sweep):
+    # few modes, long z: 13 x 11 nodes in 2 x 2 blocks, 1536 ramped z steps, 2 RHS (the
+    # automatic choice takes the chunked sweep here)
+    w, ref = _oracle_ref("long_z", lambda: W.long_z(nx=13, ny=11, nz=1536, nrhs=2))
+    plan = hz.Plan.from_workload(w, precision=precision)
+    plan.set_z_sweep(z_sweep)
+    u = plan.solve(torch_cuda.from_numpy(w.f).cuda()).cpu().numpy()
+    assert plan.info()["z_sweep"] == z_sweep
+    assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+@pytest.mark.parametrize("z_sweep", [1, 2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kw", [dict(nx=70, ny=45, nz=33, bx=3, by=2, rim=6, pml=3, nrhs=3),   # ragged z chunk
+                                dict(nx=23, ny=19, nz=1, bx=2, by=3, rim=4, pml=2, nrhs=2),
+                                dict(nx=23, ny=19, nz=17, bx=2, by=3, rim=4, pml=2, nrhs=1, sigma=True)])
+def test_z_sweep_variants(hz, torch_cuda, kw, precision, z_sweep):
+    # every z sweep variant on the same input: one or two RHS per thread, z in register
+    # chunks of 16 (33 and 17 planes leave a short last chunk, 1 plane no back substitution)
+    w, ref = _oracle_ref(repr(sorted(kw.items())), lambda: W.tiny_pml(**kw))
+    plan = hz.Plan.from_workload(w, precision=precision)
+    plan.set_z_sweep(z_sweep)
+    u = plan.solve(torch_cuda.from_numpy(w.f).cuda()).cpu().numpy()
     assert rel(u, ref) < (TOL64 if precision == "fp64" else TOLMIX)
