@@ -169,6 +169,30 @@ def bulk_macs(w, nrhs):
     return [per * rows_x * sx, per * rows_y * sy, per * rows_y * sy, per * rows_x * sx]
 
 
+def real_block_flags(h, ifaces):
+    """Per block of one axis: True when all its steps are real (a real eigenvector table)."""
+    import numpy as np
+    edges = [-1] + [int(p) for p in ifaces] + [len(h)]
+    return [bool(np.all(np.imag(h[edges[b] + 1:edges[b + 1]]) == 0)) for b in range(len(edges) - 1)]
+
+
+def tc_mma_flops(w, nrhs, real_tables):
+    """Tensor-pipe flops of the four bulk transform launches of one solve (3 TF32 products).
+
+    Interleaved complex GEMM (K = N = 2 n): 8 real flops per complex multiply-add; the
+    real-table kernel (real blocks, when enabled): Re and Im parts times the real table, 4.
+    """
+    rx = real_block_flags(w.hx, w.x_iface) if real_tables else None
+    ry = real_block_flags(w.hy, w.y_iface) if real_tables else None
+    bx = [int(n) for n in block_sizes(w.nx, w.x_iface)]
+    by = [int(n) for n in block_sizes(w.ny, w.y_iface)]
+    fx = sum(n * n * (4 if rx and rx[b] else 8) for b, n in enumerate(bx))
+    fy = sum(n * n * (4 if ry and ry[b] else 8) for b, n in enumerate(by))
+    per = nrhs * w.nz
+    rows_x, rows_y = w.ny - len(w.y_iface), w.nx - len(w.x_iface)
+    return 3 * per * (2 * rows_x * fx + 2 * rows_y * fy)
+
+
 def tc_bytes_per_launch(w, nrhs, nref):
     """Algorithmic HBM bytes of a tensor-core transform launch, averaged over a mixed step.
 
@@ -428,25 +452,34 @@ def fp64_roofline(w, R, st, traffic_workload=None):
             "share_of_step": (st["fwd"][0] + st["inv"][0]) / max(total_ms, 1e-9)}
 
 
-def tc_roofline(w, R, st, refinements):
+def tc_roofline(w, R, st, refinements, real_tables=False):
     """Roofline of the mixed path's bulk transform kernel (tensor cores, 3xTF32), HBM-bound.
 
     Algorithmic bytes per transformed value: forward x reads complex128 f and writes complex64
     (24 B), forward y and inverse y complex64 both ways (16 B), inverse x reads complex64 and
     writes complex128 u (24 B), or also reads u when it accumulates a correction (40 B);
     averaged over the 4 (1 + refinements) launches of a step.  The same launches against the
-    tensor pipe: 3 TF32 products of 8 real flops per complex multiply-add.  (The mixed path's
-    FP32 fast sine transform of uniform blocks is opt-in and not used here.)
+    tensor pipe: the MMA flops of tc_mma_flops (3 TF32 products; the real-table kernel issues
+    half the interleaved form's per complex multiply-add).  (The mixed path's FP32 fast sine
+    transform of uniform blocks is opt-in and not used here.)
     """
     hbm_peak, hbm_src = measured_peaks()
     t = launch_ms(st)
     b = tc_bytes_per_launch(w, R, refinements)
-    out = {"bound": "hbm", "kernel": "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)",
+    nreal = sum(real_block_flags(w.hx, w.x_iface)) + sum(real_block_flags(w.hy, w.y_iface)) if real_tables else 0
+    nblk = len(w.x_iface) + len(w.y_iface) + 2
+    if nreal == nblk:
+        kernel, fname = "xform_tcr_kernel (tcgen05 3xTF32 bulk x/y transforms, real tables)", "hz_xform_tc.cu"
+    elif nreal:
+        kernel, fname = "xform_tc_kernel + xform_tcr_kernel (tcgen05 3xTF32 bulk x/y transforms)", "hz_xform_tc.cu"
+    else:
+        kernel, fname = "xform_tc_kernel (tcgen05 3xTF32 bulk x/y transforms)", "hz_xform_tc.cu"
+    out = {"bound": "hbm", "kernel": kernel,
            "achieved": b / (t * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
            "frac": b / (t * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src,
            "bytes_per_launch": b, "launch_ms": t,
-           "traffic": profiled_traffic("xform_tc_kernel", w.name, "hz_xform_tc.cu")}
-    tc_flops = sum(bulk_macs(w, R)) / 4 * 8 * 3
+           "traffic": profiled_traffic(kernel.split(" ")[0], w.name, fname)}
+    tc_flops = tc_mma_flops(w, R, real_tables) / 4
     tpk, tsrc = tf32_peak()
     out["tensor"] = {"achieved": tc_flops / (t * 1e-3) / 1e12, "peak": tpk, "unit": "TFLOP/s",
                      "frac": tc_flops / (t * 1e-3) / 1e12 / tpk, "peak_source": tsrc,
@@ -476,7 +509,8 @@ def measure_both(torch, hz, w, args, dist, world, device):
                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in st64.items() if v[1]},
                  "clocks": clk64},
         "mixed": {"value": job_throughput(unknowns, world, msmx * 1e-3), "ms_per_step": msmx,
-                  "roofline": tc_roofline(w, R, stmx, int(infomx.get("refinements", 0))),
+                  "roofline": tc_roofline(w, R, stmx, int(infomx.get("refinements", 0)),
+                                          bool(infomx.get("real_tables", 0))),
                   "speedup_vs_fp64": ms64 / msmx, "refinements": infomx["refinements"],
                   "rel_residual_max": resmx, "gpu_launches": lmx, "dtype": "c64 transforms + f64",
                   "stages_ms_per_step": {k: v[0] / args.steps for k, v in stmx.items() if v[1]},

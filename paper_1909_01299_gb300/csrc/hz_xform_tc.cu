@@ -408,45 +408,53 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
       __syncthreads();
       const int cbase = t.n0 / 2;                           // first complex column of the tile in the block
       const int ccount = min(nt / 2, n - cbase);
-      for (int rr = warp; rr < TC_M; rr += TC_THREADS / 32) {
-        const long long g = row0 + rr;
-        if (g >= nrows) break;
-        if (rowskip) {
-          const long long pl = g / rows_per_plane;
-          if (rowskip[g - pl * rows_per_plane]) continue;
-        }
-        const float2* src = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
-        TO* dg = out + g * (long long)ncols + b.start + cbase;
-        constexpr int CPL = kTcMaxN / 2 / 32 + 1;           // complex columns per lane (<= 3)
-        TO val[CPL];
+      // warp w writes rows w, w + 8, ..., RB rows at a time; with accumulation the old values of
+      // the RB rows are all loaded before the first store
+      constexpr int NW = TC_THREADS / 32;
+      constexpr int CPL = kTcMaxN / 2 / 32 + 1;             // complex columns per lane (<= 3)
+      constexpr int RB = 2;
+      for (int m0 = 0; m0 < TC_M / NW; m0 += RB) {
+        TO* dg[RB];
+        const float2* src[RB];
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const int c = lane + 32 * q;
-          if (c < ccount) {
-            const float2 f = src[c];
-            if constexpr (OUT32) val[q] = f;
-            else val[q] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
+        for (int i = 0; i < RB; ++i) {
+          const int rr = warp + NW * (m0 + i);
+          const long long g = row0 + rr;
+          bool rok = g < nrows;
+          if (rok && rowskip) {
+            const long long pl = g / rows_per_plane;
+            rok = rowskip[g - pl * rows_per_plane] == 0;
           }
+          dg[i] = rok ? out + g * (long long)ncols + b.start + cbase : nullptr;
+          src[i] = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
         }
-        if constexpr (!OUT32) {
-          if (store == XS_ACCUM) {                         // every old value in flight at once
-            double2 o[CPL];
+        if constexpr (OUT32) {
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               const int c = lane + 32 * q;
-              if (c < ccount) o[q] = dg[c];
+              if (dg[i] && c < ccount) dg[i][c] = src[i][c];
             }
+        } else {
+          double2 o[RB][CPL];
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               const int c = lane + 32 * q;
-              if (c < ccount) { val[q].x += o[q].x; val[q].y += o[q].y; }
+              o[i][q] = (store == XS_ACCUM && dg[i] && c < ccount) ? dg[i][c] : make_double2(0.0, 0.0);
             }
-          }
-        }
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const int c = lane + 32 * q;
-          if (c < ccount) dg[c] = val[q];
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (dg[i] && c < ccount) {
+                const float2 f = src[i][c];
+                dg[i][c] = make_double2(f32_to_f64(f.x) + o[i][q].x, f32_to_f64(f.y) + o[i][q].y);
+              }
+            }
         }
       }
     }
@@ -462,8 +470,8 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
 // Real-table kernel.  When a block's table B is real, C = A B for complex data A is two real
 // products, Re C = Re A B and Im C = Im A B.  The MMA rows are the data rows' parts
 // (MMA row m = 2 r + u: data row r, u = 0 real / 1 imaginary part), K = N = n (half of the
-// interleaved form's 2n each way, so a quarter of its MMA work per data row, half per
-// output value).  One CTA (4 warps) takes 64 data rows x nt <= 128 columns: 128 TMEM
+// interleaved form's 2n each way: a quarter of its MMA work per MMA row, half per data
+// row).  One CTA (4 warps) takes 64 data rows x nt <= 128 columns: 128 TMEM
 // columns and about 53 KB of shared memory, so four CTAs share an SM.  The chunk loop is the
 // interleaved kernel's (16 K per chunk, data in registers one chunk ahead, two operand stages,
 // one TMA copy of the table rows per chunk); in the epilogue each lane pair (2r, 2r+1) trades
@@ -668,28 +676,55 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
       }
       __syncthreads();
       const int ccount = min(nt, n - t.n0);
-      for (int rr = warp; rr < TCR_ROWS; rr += TCR_THREADS / 32) {
-        const long long g = row0 + rr;
-        if (g >= nrows) break;
-        if (rowskip) {
-          const long long pl = g / rows_per_plane;
-          if (rowskip[g - pl * rows_per_plane]) continue;
-        }
-        const float2* srow = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
-        TO* dg = out + g * (long long)ncols + b.start + t.n0;
-        for (int c = lane; c < ccount; c += 32) {
-          const float2 f = srow[c];
-          if constexpr (OUT32) {
-            dg[c] = f;
-          } else {
-            double2 val = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
-            if (store == XS_ACCUM) {
-              const double2 o = dg[c];
-              val.x += o.x;
-              val.y += o.y;
-            }
-            dg[c] = val;
+      // warp w writes rows w, w + 4, ..., RB rows at a time: with accumulation the old values of
+      // the RB rows are all loaded before the first store (a store may alias a later load, so
+      // the compiler keeps them in program order: row by row, each old value would cost a
+      // full memory latency)
+      constexpr int NW = TCR_THREADS / 32;
+      constexpr int CPL = kTcrMaxN / 32 + 1;              // complex columns per lane (<= 4)
+      constexpr int RB = 4;
+      for (int m0 = 0; m0 < TCR_ROWS / NW; m0 += RB) {
+        TO* dg[RB];
+        const float2* srow[RB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          const int rr = warp + NW * (m0 + i);
+          const long long g = row0 + rr;
+          bool rok = g < nrows;
+          if (rok && rowskip) {
+            const long long pl = g / rows_per_plane;
+            rok = rowskip[g - pl * rows_per_plane] == 0;
           }
+          dg[i] = rok ? out + g * (long long)ncols + b.start + t.n0 : nullptr;
+          srow[i] = reinterpret_cast<const float2*>(smem + (size_t)rr * sstride);
+        }
+        if constexpr (OUT32) {
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (dg[i] && c < ccount) dg[i][c] = srow[i][c];
+            }
+        } else {
+          double2 o[RB][CPL];
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              o[i][q] = (store == XS_ACCUM && dg[i] && c < ccount) ? dg[i][c] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (dg[i] && c < ccount) {
+                const float2 f = srow[i][c];
+                dg[i][c] = make_double2(f32_to_f64(f.x) + o[i][q].x, f32_to_f64(f.y) + o[i][q].y);
+              }
+            }
         }
       }
     }
@@ -705,23 +740,26 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
         part[e] = __shfl_xor_sync(0xffffffffu, send, 1);
       }
       if (!row_ok) continue;
+      TO* p[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int ccol = t.n0 + c16 + (odd ? 8 : 0) + e;      // complex column within the block
-        if (ccol >= n) continue;
-        const float re = odd ? part[e] : v[e];
-        const float im = odd ? v[8 + e] : part[e];
-        TO* p = out + plane * (long long)ncols * rows_per_plane + (long long)(b.start + ccol) * rows_per_plane + rip;
-        if constexpr (OUT32) {
-          *p = make_float2(re, im);
-        } else {
-          double2 val = make_double2(f32_to_f64(re), f32_to_f64(im));
-          if (store == XS_ACCUM) {
-            const double2 o = *p;
-            val.x += o.x;
-            val.y += o.y;
-          }
-          *p = val;
+        p[e] = ccol < n ? out + plane * (long long)ncols * rows_per_plane + (long long)(b.start + ccol) * rows_per_plane + rip
+                        : nullptr;
+      }
+      if constexpr (OUT32) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (p[e]) *p[e] = odd ? make_float2(part[e], v[8 + e]) : make_float2(v[e], part[e]);
+      } else {
+        double2 o[8];                                         // all old values in flight at once
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = (store == XS_ACCUM && p[e]) ? *p[e] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float re = odd ? part[e] : v[e];
+          const float im = odd ? v[8 + e] : part[e];
+          if (p[e]) *p[e] = make_double2(f32_to_f64(re) + o[e].x, f32_to_f64(im) + o[e].y);
         }
       }
     }
