@@ -955,9 +955,18 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
       float2* bY32 = reinterpret_cast<float2*>(w.dg);
       hz::to_c64_copy(w.aX, aX32, (long long)nIx * ny * planes, st);
       hz::to_c64_copy(w.bY, bY32, (long long)nIy * nx * planes, st);
-      ga.aX32 = aX32;
-      ga.bY32 = bY32;
-      hz::global_rhs(ga, G32, st);                  // r~ (G is free until step 7)
+      // r~ formed inside the sweep where the sweep can (FP32, from the complex64 interface
+      // transforms), else by global_rhs into G
+      zg.gen.kind = 1;
+      zg.gen.nIx = nIx; zg.gen.nIy = nIy;
+      zg.gen.aX32 = aX32; zg.gen.bY32 = bY32;
+      zg.gen.wx32 = p->dx.gcoef32; zg.gen.wy32 = p->dy.gcoef32;
+      if (!hz::zsolve_forms_rhs(zg)) {
+        zg.gen.kind = 0;
+        ga.aX32 = aX32;
+        ga.bY32 = bY32;
+        hz::global_rhs(ga, G32, st);
+      }
     } else {
       hz::global_rhs(ga, w.G, st);
     }
@@ -992,13 +1001,26 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
       float2* alY32 = reinterpret_cast<float2*>(w.bY);
       hz::to_c64_copy(w.alX, alX32, (long long)nIx * ny * planes, st);
       hz::to_c64_copy(w.alY, alY32, (long long)nIy * nx * planes, st);
-      ba.alphaX32 = alX32;
-      ba.alphaY32 = alY32;
-      hz::boundary_rhs(ba, FT32, st);               // f~ + g~ / M_z, in place
+      // f~ + g~ / M_z formed inside the sweep where the sweep can (FP32; f~ itself is left as
+      // it is), else by boundary_rhs into f~
+      hz::ZSolveArgs zb = za;
+      zb.gen.kind = 2;
+      zb.gen.nIx = nIx; zb.gen.nIy = nIy;
+      zb.gen.aX32 = alX32; zb.gen.bY32 = alY32;
+      zb.gen.gxl = p->dx.gl; zb.gen.gxr = p->dx.gr; zb.gen.gyl = p->dy.gl; zb.gen.gyr = p->dy.gr;
+      zb.gen.cxl32 = p->dx.cl32; zb.gen.cxr32 = p->dx.cr32; zb.gen.cyl32 = p->dy.cl32; zb.gen.cyr32 = p->dy.cr32;
+      zb.gen.sig = p->sig;
+      if (!hz::zsolve_forms_rhs(zb)) {
+        zb.gen.kind = 0;
+        ba.alphaX32 = alX32;
+        ba.alphaY32 = alY32;
+        hz::boundary_rhs(ba, FT32, st);             // f~ + g~ / M_z, in place
+      }
+      hz::zsolve(zb, st);
     } else {
       hz::boundary_rhs(ba, w.FT, st);
+      hz::zsolve(za, st);
     }
-    hz::zsolve(za, st);
   }
   // Step 7: u = W_x (x) W_y u~ in the blocks; u = w on the interfaces
   {

@@ -207,6 +207,28 @@ struct ZFactors {
   double2* cm = nullptr;          // [k]: forward multiplier c_k (/ mz_k when folded)
 };
 
+// Right-hand side formed inside the sweep (mixed path, complex64 storage), in FP32 with the
+// arithmetic of global_rhs / boundary_rhs (so that the separate kernel and its complex64 volume
+// round trip are not needed): kind 1, the step-5 global right-hand side
+//   sum_p wx32[p][i] aX32[r][k][p][j] + sum_q wy32[q][j] bY32[r][k][q][i];
+// kind 2, rhs32 plus the step-6 boundary term
+//   sigma_k (cxl32[i] aX32[r][k][gxl[i]][j] + cxr32[i] aX32[..gxr[i]..] + cyl32[j] bY32[r][k][gyl[j]][i]
+//            + cyr32[j] bY32[..gyr[j]..]).
+constexpr int kGenMaxIface = 4;         // kind 1: interfaces per axis held in registers
+struct ZRhsGen {
+  int kind = 0;                          // 0: read rhs32
+  int nIx = 0, nIy = 0;
+  const float2* aX32 = nullptr;          // [r][k][nIx][ny]: aX (kind 1) or alphaX (kind 2)
+  const float2* bY32 = nullptr;          // [r][k][nIy][nx]: bY (kind 1) or alphaY (kind 2)
+  const float2* wx32 = nullptr;          // kind 1: [nIx][nx]
+  const float2* wy32 = nullptr;          // kind 1: [nIy][ny]
+  const int* gxl = nullptr; const int* gxr = nullptr;     // kind 2: per i, interface index or -1
+  const int* gyl = nullptr; const int* gyr = nullptr;     // kind 2: per j
+  const float2* cxl32 = nullptr; const float2* cxr32 = nullptr;   // kind 2: per i
+  const float2* cyl32 = nullptr; const float2* cyr32 = nullptr;   // kind 2: per j
+  const double* sig = nullptr;           // kind 2: [k] or NULL
+};
+
 struct ZSolveArgs {
   const double2* rhs = nullptr;   // mode-layout right-hand side [r][k][i][j]
   double2* out = nullptr;         // mode-layout result [r][k][i][j]
@@ -227,8 +249,13 @@ struct ZSolveArgs {
   const float2* rhs32 = nullptr;
   float2* out32 = nullptr;
   double2* scratch = nullptr;
+  ZRhsGen gen;                           // complex64 storage only: right-hand side formed in the sweep
 };
 void zsolve(const ZSolveArgs& a, cudaStream_t st);
+// Whether zsolve forms a.gen's right-hand side itself (the plain sweep kernels; kind 1 with at
+// most kGenMaxIface interfaces per axis).  The chunked sweep reads rhs32: the caller then
+// launches global_rhs / boundary_rhs first.
+bool zsolve_forms_rhs(const ZSolveArgs& a);
 
 // Step 6 boundary term g~ / M_z added in place to the block right-hand side f~:
 // sigma_k (cxl aX[pl] + cxr aX[pr] + cyl aY[ql] + cyr aY[qr]).

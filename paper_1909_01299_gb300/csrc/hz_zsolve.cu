@@ -22,6 +22,7 @@
 // accuracy of the tensor-core transforms that produce and consume them) and the
 // forward values go to an FP64 scratch array instead.
 #include <algorithm>
+#include <type_traits>
 
 #include "hz_convert.cuh"
 #include "hz_internal.h"
@@ -45,10 +46,77 @@ __device__ __forceinline__ double2 rfma(double c, double2 y, double2 acc) {
   return make_double2(fma(c, y.x, acc.x), fma(c, y.y, acc.y));
 }
 
+// Per-thread constants of a generated right-hand side: kind 1, the thread's coefficients
+// wx32[p][i] and wy32[q][j]; kind 2, the interface indices and coefficients of its block edges.
+struct GenThread {
+  float2 wx[kGenMaxIface], wy[kGenMaxIface];
+  int pl = -1, pr = -1, ql = -1, qr = -1;
+  float2 cl, cr, dl, dr;
+};
+template <int GEN>
+__device__ __forceinline__ GenThread gen_thread(const ZSolveArgs& a, int i, int j) {
+  GenThread t;
+  const ZRhsGen& g = a.gen;
+  if constexpr (GEN == 1) {
+#pragma unroll
+    for (int p = 0; p < kGenMaxIface; ++p) {
+      t.wx[p] = p < g.nIx ? g.wx32[(long long)p * a.nx + i] : make_float2(0.f, 0.f);
+      t.wy[p] = p < g.nIy ? g.wy32[(long long)p * a.ny + j] : make_float2(0.f, 0.f);
+    }
+  } else if constexpr (GEN == 2) {
+    t.pl = g.gxl[i]; t.pr = g.gxr[i]; t.ql = g.gyl[j]; t.qr = g.gyr[j];
+    t.cl = g.cxl32[i]; t.cr = g.cxr32[i]; t.dl = g.cyl32[j]; t.dr = g.cyr32[j];
+  }
+  return t;
+}
+
+// Complex64 right-hand side of plane k of RHS r at mode (i, j), element idx of rhs32, as FP64:
+// GEN 0 read, 1 the global right-hand side, 2 rhs32 plus the boundary term (the FP32 sums of
+// global_rhs_kernel and boundary_rhs_kernel, term by term in the same order).
+template <int GEN>
+__device__ __forceinline__ double2 c64_rhs(const ZSolveArgs& a, const GenThread& gt, long long idx, int r, int k,
+                                           int i, int j) {
+  if constexpr (GEN == 0) {
+    return to_c128(a.rhs32[idx]);
+  } else {
+    const ZRhsGen& g = a.gen;
+    const long long rk = (long long)r * a.nz + k;
+    float2 s = make_float2(0.f, 0.f);
+    if constexpr (GEN == 1) {
+      const float2* ax = g.aX32 + rk * g.nIx * a.ny + j;
+      const float2* by = g.bY32 + rk * g.nIy * a.nx + i;
+      float2 vx[kGenMaxIface], vy[kGenMaxIface];
+#pragma unroll
+      for (int p = 0; p < kGenMaxIface; ++p) {
+        if (p < g.nIx) vx[p] = ax[(long long)p * a.ny];
+        if (p < g.nIy) vy[p] = by[(long long)p * a.nx];
+      }
+#pragma unroll
+      for (int p = 0; p < kGenMaxIface; ++p)
+        if (p < g.nIx) s = cfma32(gt.wx[p], vx[p], s);
+#pragma unroll
+      for (int p = 0; p < kGenMaxIface; ++p)
+        if (p < g.nIy) s = cfma32(gt.wy[p], vy[p], s);
+      return to_c128(s);
+    } else {
+      const float2* ax = g.aX32 + rk * g.nIx * a.ny + j;
+      const float2* ay = g.bY32 + rk * g.nIy * a.nx + i;
+      if (gt.pl >= 0) s = cfma32(gt.cl, ax[(long long)gt.pl * a.ny], s);
+      if (gt.pr >= 0) s = cfma32(gt.cr, ax[(long long)gt.pr * a.ny], s);
+      if (gt.ql >= 0) s = cfma32(gt.dl, ay[(long long)gt.ql * a.nx], s);
+      if (gt.qr >= 0) s = cfma32(gt.dr, ay[(long long)gt.qr * a.nx], s);
+      const float2 f32 = a.rhs32[idx];
+      const double sg = g.sig ? g.sig[k] : 1.0;
+      const float s32 = sg == 1.0 ? 1.f : f64_to_f32_trunc(sg);
+      return to_c128(make_float2(fmaf(s32, s.x, f32.x), fmaf(s32, s.y, f32.y)));
+    }
+  }
+}
+
 // RB right-hand sides per thread share each factor load and give the sweep RB independent
 // dependency chains.  C64: complex64 right-hand side and result (mixed path); the forward
 // values y_k are kept in FP64 in the scratch array, so only the stored result is rounded.
-template <bool REALCM, int RB, bool C64>
+template <bool REALCM, int RB, bool C64, int GEN>
 __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const long long plane = (long long)a.nx * a.ny;
   const int ngrp = (a.nrhs + RB - 1) / RB;
@@ -67,6 +135,7 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
   const double2* __restrict__ P = a.P + pos;
   const double2* __restrict__ Q = a.Q + pos;
   const double2* __restrict__ cm = a.cm;
+  const GenThread gt = gen_thread<GEN>(a, i, j);
 
   double2 y[RB];
 #pragma unroll
@@ -79,7 +148,7 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
     for (int q = 0; q < RB; ++q) {
       if (q < nr) {
         double2 b;
-        if constexpr (C64) b = to_c128(a.rhs32[base + q * rs + k * plane]);
+        if constexpr (C64) b = c64_rhs<GEN>(a, gt, base + q * rs + k * plane, r0 + q, k, i, j);
         else b = a.rhs[base + q * rs + k * plane];
         double2 t;
         if (REALCM)
@@ -113,14 +182,14 @@ __global__ void __launch_bounds__(128) zsolve_kernel(const ZSolveArgs a) {
 
 // Few sweeps, long z.  With one thread per sweep and too few sweeps to fill the GPU, the plain
 // kernel waits a full memory latency for every z step (its next loads sit behind the current
-// step's store).  Here each thread takes z in chunks of ZD steps: all loads of a chunk (P_k,
+// step's store).  Here each thread takes z in chunks of 16 steps: all loads of a chunk (P_k,
 // the right-hand side, c_k; Q_k and the forward values on the way back) are issued together
 // into registers, then the chunk's steps run, with the plain kernel's arithmetic.  (With a
 // warp or two per SM sub-partition the step time is then the FP64 pipe's: one warp
 // instruction per 64 clocks per sub-partition, 6 of them per forward step with a real c_k,
 // 4 per back step.  A form with one multiply-add on the dependency chain,
 // y_k = (b_k P_k) - (c_k P_k) y_{k-1}, issues 10 and measured slower.)
-constexpr int ZD = 16;
+constexpr int kZD = 16;
 
 template <bool REALCM, bool C64>
 __global__ void __launch_bounds__(128) zsolve_chunk_kernel(const ZSolveArgs a) {
@@ -137,17 +206,22 @@ __global__ void __launch_bounds__(128) zsolve_chunk_kernel(const ZSolveArgs a) {
   const double2* __restrict__ Q = a.Q + pos;
   const double2* __restrict__ cm = a.cm;
   const int nz = a.nz;
+  constexpr int ZD = kZD;
+  using RV = typename std::conditional<C64, float2, double2>::type;
+  const RV* __restrict__ rhs = C64 ? (const RV*)a.rhs32 : (const RV*)a.rhs;
 
   double2 y = make_double2(0.0, 0.0);
   for (int k0 = 0; k0 < nz; k0 += ZD) {
-    double2 pk[ZD], bk[ZD], ck[ZD];
+    // the loads only (a complex64 value is converted where it is used, so that no conversion
+    // waits on a load before the next load is issued)
+    double2 pk[ZD], ck[ZD];
+    RV bk[ZD];
 #pragma unroll
     for (int d = 0; d < ZD; ++d) {
       const int k = k0 + d;
       if (k < nz) {
         pk[d] = P[(long long)k * plane];
-        if constexpr (C64) bk[d] = to_c128(a.rhs32[base + (long long)k * plane]);
-        else bk[d] = a.rhs[base + (long long)k * plane];
+        bk[d] = rhs[base + (long long)k * plane];
         ck[d] = cm[k];
       }
     }
@@ -156,8 +230,8 @@ __global__ void __launch_bounds__(128) zsolve_chunk_kernel(const ZSolveArgs a) {
       const int k = k0 + d;
       if (k < nz) {
         const double2 c = ck[d];
-        const double2 t = REALCM ? make_double2(fma(-c.x, y.x, bk[d].x), fma(-c.x, y.y, bk[d].y))
-                                 : csub_mul(bk[d], c, y);
+        const double2 b = to_c128(bk[d]);
+        const double2 t = REALCM ? make_double2(fma(-c.x, y.x, b.x), fma(-c.x, y.y, b.y)) : csub_mul(b, c, y);
         y = cmul(t, pk[d]);
         fw[(long long)k * plane] = y;
       }
@@ -394,45 +468,49 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
 
 }  // namespace
 
+template <bool REALCM, bool C64, int GEN>
+void launch_sweep(const ZSolveArgs& a, int variant, unsigned grid, cudaStream_t st) {
+  const int T = 128;
+  if (variant == 3 && GEN == 0) zsolve_chunk_kernel<REALCM, C64><<<grid, T, 0, st>>>(a);
+  else if (variant == 2) zsolve_kernel<REALCM, 2, C64, GEN><<<grid, T, 0, st>>>(a);
+  else zsolve_kernel<REALCM, 1, C64, GEN><<<grid, T, 0, st>>>(a);
+}
+
+int sweep_variant(const ZSolveArgs& a) {
+  const int variant = a.rhs_per_thread;
+  if (variant >= 1 && variant <= 3) return variant;
+  // automatic: the chunked sweep when the sweeps fill less than 512 threads per SM (the plain
+  // kernel then waits a memory latency per z step), else one right-hand side per thread
+  // (measured faster on GB300 at the benchmark sizes than two per thread: more independent
+  // sweeps in flight beat shared factor loads)
+  const long long sweeps = (long long)a.nx * a.ny * a.nrhs;
+  return (a.sms > 0 && sweeps < 512LL * a.sms) ? 3 : 1;
+}
+
+template <bool REALCM>
+void launch_sweep_c(const ZSolveArgs& a, int variant, unsigned grid, cudaStream_t st) {
+  if (!a.rhs32) launch_sweep<REALCM, false, 0>(a, variant, grid, st);
+  else if (a.gen.kind == 1) launch_sweep<REALCM, true, 1>(a, variant, grid, st);
+  else if (a.gen.kind == 2) launch_sweep<REALCM, true, 2>(a, variant, grid, st);
+  else launch_sweep<REALCM, true, 0>(a, variant, grid, st);
+}
+
 void zsolve(const ZSolveArgs& a, cudaStream_t st) {
   if ((long long)a.nx * a.ny * a.nrhs == 0) return;
   const int T = 128;
-  int variant = a.rhs_per_thread;
-  if (variant < 1 || variant > 3) {
-    // automatic: the chunked sweep when the sweeps fill less than 512 threads per SM (the
-    // plain kernel then waits a memory latency per z step), else one right-hand side per
-    // thread (measured faster on GB300 at the benchmark sizes than two per thread: more
-    // independent sweeps in flight beat shared factor loads)
-    const long long sweeps = (long long)a.nx * a.ny * a.nrhs;
-    variant = (a.sms > 0 && sweeps < 512LL * a.sms) ? 3 : 1;
-  }
-  if (variant == 3) {
-    const unsigned grid = (unsigned)(((long long)a.nx * a.ny * a.nrhs + T - 1) / T);
-    const int v = (a.rhs32 ? 2 : 0) + (a.real_cm ? 1 : 0);
-    switch (v) {
-      case 0: zsolve_chunk_kernel<false, false><<<grid, T, 0, st>>>(a); break;
-      case 1: zsolve_chunk_kernel<true, false><<<grid, T, 0, st>>>(a); break;
-      case 2: zsolve_chunk_kernel<false, true><<<grid, T, 0, st>>>(a); break;
-      default: zsolve_chunk_kernel<true, true><<<grid, T, 0, st>>>(a); break;
-    }
-    count_launch();
-    return;
-  }
-  const int rb = variant;
+  const int variant = sweep_variant(a);
+  const int rb = variant == 2 ? 2 : 1;
   const long long n = (long long)a.nx * a.ny * ((a.nrhs + rb - 1) / rb);
   const unsigned grid = (unsigned)((n + T - 1) / T);
-  const int v = (a.rhs32 ? 4 : 0) + (rb == 2 ? 2 : 0) + (a.real_cm ? 1 : 0);
-  switch (v) {
-    case 0: zsolve_kernel<false, 1, false><<<grid, T, 0, st>>>(a); break;
-    case 1: zsolve_kernel<true, 1, false><<<grid, T, 0, st>>>(a); break;
-    case 2: zsolve_kernel<false, 2, false><<<grid, T, 0, st>>>(a); break;
-    case 3: zsolve_kernel<true, 2, false><<<grid, T, 0, st>>>(a); break;
-    case 4: zsolve_kernel<false, 1, true><<<grid, T, 0, st>>>(a); break;
-    case 5: zsolve_kernel<true, 1, true><<<grid, T, 0, st>>>(a); break;
-    case 6: zsolve_kernel<false, 2, true><<<grid, T, 0, st>>>(a); break;
-    default: zsolve_kernel<true, 2, true><<<grid, T, 0, st>>>(a); break;
-  }
+  if (a.real_cm) launch_sweep_c<true>(a, variant, grid, st);
+  else launch_sweep_c<false>(a, variant, grid, st);
   count_launch();
+}
+
+bool zsolve_forms_rhs(const ZSolveArgs& a) {
+  if (sweep_variant(a) == 3) return false;
+  if (a.gen.kind == 1) return a.gen.nIx <= kGenMaxIface && a.gen.nIy <= kGenMaxIface;
+  return a.gen.kind == 2;
 }
 
 template <typename FT>
