@@ -110,6 +110,45 @@ __global__ void contract_cols_kernel(const TV* __restrict__ V, double2* __restri
   }
 }
 
+// FP32 contraction within rows (mixed path): one warp per (plane, row) takes every slot of the
+// row (a slot range is contiguous in the row: consecutive lanes read consecutive columns), so the
+// index arithmetic and the row start are shared by the slots; the per-slot sums are reduced
+// across the warp at the end.  out[(plane * nslots + s) * nrows + i].
+constexpr int kColSlotsMax = 8;
+template <typename TV>
+__global__ void __launch_bounds__(256) contract_cols_row_kernel(const TV* __restrict__ V, double2* __restrict__ out,
+                                                                const float2* __restrict__ coef,
+                                                                const int2* __restrict__ range, int nrows,
+                                                                int ncols, int nslots, long long nplanes) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = (int)(threadIdx.x & 31);
+  if (w >= nplanes * nrows) return;                         // warp-uniform
+  const int i = (int)(w % nrows);
+  const long long plane = w / nrows;
+  const TV* __restrict__ v = V + (plane * nrows + i) * (long long)ncols;
+  float2 acc[kColSlotsMax];
+#pragma unroll
+  for (int s = 0; s < kColSlotsMax; ++s) {
+    acc[s] = make_float2(0.f, 0.f);
+    if (s < nslots) {
+      const int2 rg = range[s];
+      const float2* __restrict__ c = coef + (long long)s * ncols;
+      for (int j = rg.x + lane; j < rg.y; j += 32) acc[s] = cfma32(c[j], to_c64t(v[j]), acc[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kColSlotsMax; ++s) {
+    if (s < nslots) {
+      float2 a32 = acc[s];
+      for (int o = 16; o > 0; o >>= 1) {
+        a32.x += __shfl_down_sync(0xffffffffu, a32.x, o);
+        a32.y += __shfl_down_sync(0xffffffffu, a32.y, o);
+      }
+      if (lane == 0) out[(plane * nslots + s) * nrows + i] = to_c128(a32);
+    }
+  }
+}
+
 // Step 5 on the mixed path with several interfaces per axis: every slot contracts the
 // whole row or column (the whole-axis eigenvector rows), so one pass over V accumulates all
 // nslots sums (2 <= nslots <= 8, a compile-time count) in FP32 instead of reading V once
@@ -471,6 +510,14 @@ void contract_cols_t(const TV* V, double2* out, const C* coef, const int2* range
                      int nslots, long long nplanes, cudaStream_t st, int real_coef = 0) {
   const long long n = nplanes * nslots * (long long)nrows;
   if (n == 0) return;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (nslots <= kColSlotsMax) {                            // FP32: one warp per row, all slots
+      contract_cols_row_kernel<TV><<<blocks_for(nplanes * nrows * 32, 256), 256, 0, st>>>(
+          V, out, coef, range, nrows, ncols, nslots, nplanes);
+      count_launch();
+      return;
+    }
+  }
   const long long threads = sizeof(C) == sizeof(double2) ? n : n * 32;   // FP32: one warp per output
   contract_cols_kernel<C, TV><<<blocks_for(threads, 256), 256, 0, st>>>(V, out, coef, range, nrows, ncols,
                                                                        nslots, nplanes, real_coef);

@@ -436,14 +436,14 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
               const int c = lane + 32 * q;
               if (dg[i] && c < ccount) dg[i][c] = src[i][c];
             }
-        } else {
+        } else if (store == XS_ACCUM) {
           double2 o[RB][CPL];
 #pragma unroll
           for (int i = 0; i < RB; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               const int c = lane + 32 * q;
-              o[i][q] = (store == XS_ACCUM && dg[i] && c < ccount) ? dg[i][c] : make_double2(0.0, 0.0);
+              if (dg[i] && c < ccount) o[i][q] = dg[i][c];
             }
 #pragma unroll
           for (int i = 0; i < RB; ++i)
@@ -453,6 +453,17 @@ xform_tc_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock* 
               if (dg[i] && c < ccount) {
                 const float2 f = src[i][c];
                 dg[i][c] = make_double2(f32_to_f64(f.x) + o[i][q].x, f32_to_f64(f.y) + o[i][q].y);
+              }
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (dg[i] && c < ccount) {
+                const float2 f = src[i][c];
+                dg[i][c] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
               }
             }
         }
@@ -706,14 +717,14 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
               const int c = lane + 32 * q;
               if (dg[i] && c < ccount) dg[i][c] = srow[i][c];
             }
-        } else {
+        } else if (store == XS_ACCUM) {
           double2 o[RB][CPL];
 #pragma unroll
           for (int i = 0; i < RB; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               const int c = lane + 32 * q;
-              o[i][q] = (store == XS_ACCUM && dg[i] && c < ccount) ? dg[i][c] : make_double2(0.0, 0.0);
+              if (dg[i] && c < ccount) o[i][q] = dg[i][c];
             }
 #pragma unroll
           for (int i = 0; i < RB; ++i)
@@ -723,6 +734,19 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
               if (dg[i] && c < ccount) {
                 const float2 f = srow[i][c];
                 dg[i][c] = make_double2(f32_to_f64(f.x) + o[i][q].x, f32_to_f64(f.y) + o[i][q].y);
+              }
+            }
+        } else {
+          // no FP64 arithmetic here: the FP64 pipe is 64x slower than FP32 (an add of zero would
+          // cost as much as the accumulation)
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+              const int c = lane + 32 * q;
+              if (dg[i] && c < ccount) {
+                const float2 f = srow[i][c];
+                dg[i][c] = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
               }
             }
         }
@@ -751,15 +775,22 @@ xform_tcr_kernel(const TI* __restrict__ in, TO* __restrict__ out, const TCBlock*
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           if (p[e]) *p[e] = odd ? make_float2(part[e], v[8 + e]) : make_float2(v[e], part[e]);
-      } else {
+      } else if (store == XS_ACCUM) {
         double2 o[8];                                         // all old values in flight at once
 #pragma unroll
-        for (int e = 0; e < 8; ++e) o[e] = (store == XS_ACCUM && p[e]) ? *p[e] : make_double2(0.0, 0.0);
+        for (int e = 0; e < 8; ++e) o[e] = p[e] ? *p[e] : make_double2(0.0, 0.0);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const float re = odd ? part[e] : v[e];
           const float im = odd ? v[8 + e] : part[e];
           if (p[e]) *p[e] = make_double2(f32_to_f64(re) + o[e].x, f32_to_f64(im) + o[e].y);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float re = odd ? part[e] : v[e];
+          const float im = odd ? v[8 + e] : part[e];
+          if (p[e]) *p[e] = make_double2(f32_to_f64(re), f32_to_f64(im));
         }
       }
     }
