@@ -160,7 +160,7 @@ __host__ __device__ __forceinline__ void fft_stage_par(V* x, int N, int L, const
     else if (R == 3) dft3(a);
     else if (R == 4) dft4(a);
     else dft5(a);
-    if (j1 > 0) {
+    if (tw && j1 > 0) {                              // no table: a prime-factor stage
 #pragma unroll
       for (int q = 1; q < R; ++q) a[q] = cmulw(a[q], tw[j1 * (R - 1) + q - 1]);
     }
@@ -226,9 +226,10 @@ __device__ __forceinline__ void fft_row_par(V* x, const DstBlock& b, const V* tw
   int L = N, off = 0;
   for (int s = 0; s < b.nst; ++s) {
     const int r = b.rad[s];
-    fft_stage_any(x, N, L, r, tw + off, sub);
+    const bool twiddled = !(b.pfa && s == 0);
+    fft_stage_any(x, N, L, r, twiddled ? tw + off : static_cast<const V*>(nullptr), sub);
     __syncwarp();
-    off += (L / r) * (r - 1);
+    if (twiddled) off += (L / r) * (r - 1);
     L /= r;
   }
 }
@@ -294,6 +295,7 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
   const int* __restrict__ pos = idx + b.ioff;
   const int* __restrict__ gin = pos + N;
   const int* __restrict__ src = gin + N;
+  const int* __restrict__ pin = src + n;
   const typename Scalar<V>::T* __restrict__ pq = coef + b.coff;
   // phase 1: load the row pairs (x_j, x_{N-j}) and write y_j, y_{N-j} in natural order (rows
   // that are skipped or past the end transform zeros and are not stored).  FP32: one warp per
@@ -314,8 +316,8 @@ dst_kernel(const TI* __restrict__ in, TO* __restrict__ out, const DstBlock* __re
     V yj, ym;
     pre_pair(xj, xm, pq[2 * j], pq[2 * j + 1], &yj, &ym);
     V* x = sm + r * stride;
-    x[j] = yj;
-    if (N - j != j) x[N - j] = ym;
+    x[pin[j]] = yj;
+    if (N - j != j) x[pin[N - j]] = ym;
   };
   if constexpr (sizeof(V) == 8) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -443,7 +445,19 @@ bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& 
   DstBlock b{};
   b.start = start;
   b.n = n;
-  int m = N;
+  // prime-factor split N = m N1 (m = 3 or 5, N1 = 2^a >= 4): the radix-m stage first, without
+  // twiddles, then the radix-4/2 stages of the length-N1 transforms
+  int N1 = N, pm = 1;
+  while (N1 % 2 == 0) N1 /= 2;
+  if ((N1 == 3 || N1 == 5) && N / N1 >= 4) {
+    pm = N1;
+    N1 = N / pm;
+    b.pfa = 1;
+    b.rad[b.nst++] = pm;
+  } else {
+    N1 = N;
+  }
+  int m = N1;
   for (int r : {4, 3, 5, 2}) {
     while (m % r == 0) {
       if (b.nst == kDstMaxStages) return false;
@@ -454,39 +468,48 @@ bool dst_plan_block(int n, int start, int dir, double S, std::vector<DstBlock>& 
   if (m != 1) return false;
   const double pi = 3.14159265358979323846;
   // stage twiddles exp(-2 pi i j1 q / L), j1 = 0..L/r-1, q = 1..r-1 (argument reduced exactly),
-  // sub-transform length L = N, N / r_1, ...
+  // sub-transform length L = N, N / r_1, ... (a prime-factor first stage has none)
   b.tw_off = (long long)tw.size();
   int L = N;
   for (int s = 0; s < b.nst; ++s) {
     const int r = b.rad[s], M = L / r;
-    for (int j1 = 0; j1 < M; ++j1)
-      for (int q = 1; q < r; ++q) {
-        const int e = (j1 * q) % L;
-        const double th = -2.0 * pi * e / L;
-        tw.push_back(make_double2(std::cos(th), std::sin(th)));
-      }
+    if (!(b.pfa && s == 0))
+      for (int j1 = 0; j1 < M; ++j1)
+        for (int q = 1; q < r; ++q) {
+          const int e = (j1 * q) % L;
+          const double th = -2.0 * pi * e / L;
+          tw.push_back(make_double2(std::cos(th), std::sin(th)));
+        }
     L = M;
   }
   b.ntw = (int)(tw.size() - b.tw_off);
-  // pos[N]: where the FFT leaves Y_k (digits of k, radix r_1 first, weighted N / r_1, ...);
-  // gin[N]: column of input index j (1..n); src[n]: position holding output column c
+  // pos[N]: where the FFT leaves Y_k: the digits of k (radix r_1 first, weighted N / r_1, ...)
+  // of the mixed-radix transform, or with the prime-factor split N1 (k mod m) + the digits of
+  // k mod N1 within the length-N1 transform; gin[N]: column of input index j (1..n); src[n]:
+  // position holding output column c; pin[N]: position of y_j (the identity without the split)
   b.ioff = (long long)idx.size();
-  std::vector<int> pos(N);
+  std::vector<int> pos(N), pin(N);
+  const int s0 = b.pfa ? 1 : 0;
   for (int k = 0; k < N; ++k) {
-    int kk = k, p = 0, Ls = N;
-    for (int s = 0; s < b.nst; ++s) {
+    int kk = b.pfa ? k % N1 : k, p = 0, Ls = N1;
+    for (int s = s0; s < b.nst; ++s) {
       Ls /= b.rad[s];
       p += (kk % b.rad[s]) * Ls;
       kk /= b.rad[s];
     }
-    pos[k] = p;
+    pos[k] = b.pfa ? N1 * (k % pm) + p : p;
   }
+  for (int j = 0; j < N; ++j) pin[j] = j;
+  if (b.pfa)
+    for (int n1 = 0; n1 < N1; ++n1)
+      for (int n2 = 0; n2 < pm; ++n2) pin[(pm * n1 + N1 * n2) % N] = n1 + N1 * n2;
   for (int k = 0; k < N; ++k) idx.push_back(pos[k]);
   for (int j = 0; j < N; ++j) idx.push_back(j == 0 ? 0 : (dir == 1 ? j - 1 : sym_col(j, n)));
   for (int c = 0; c < n; ++c) {
     const int m = dir == 1 ? sym_mode(c, n) : c + 1;
     idx.push_back(pos[m == 1 ? 0 : (m % 2 == 0 ? m / 2 : N - (m - 1) / 2)]);
   }
+  for (int j = 0; j < N; ++j) idx.push_back(pin[j]);
   b.coff = (long long)coef.size();
   for (int j = 0; j <= N / 2; ++j) {
     const double sj = std::sin(pi * j / N);
@@ -508,19 +531,22 @@ bool dst_apply_host(int n, int dir, double S, const double2* in, double2* out) {
   const int* pos = idx.data() + b.ioff;
   const int* gin = pos + N;
   const int* src = gin + N;
+  const int* pin = src + n;
   std::vector<double2> x(N);
   x[0] = make_double2(0.0, 0.0);
   for (int j = 1; 2 * j <= N; ++j) {
     double2 yj, ym;
     pre_pair(in[gin[j]], in[gin[N - j]], coef[b.coff + 2 * j], coef[b.coff + 2 * j + 1], &yj, &ym);
-    x[j] = yj;
-    if (N - j != j) x[N - j] = ym;
+    x[pin[j]] = yj;
+    if (N - j != j) x[pin[N - j]] = ym;
   }
   // the kernel's per-lane code, the lanes of a row taken in turn
   int L = N, off = 0;
   for (int st = 0; st < b.nst; ++st) {
-    for (int sub = 0; sub < kTPR; ++sub) fft_stage_any(x.data(), N, L, b.rad[st], tw.data() + b.tw_off + off, sub);
-    off += (L / b.rad[st]) * (b.rad[st] - 1);
+    const bool twiddled = !(b.pfa && st == 0);
+    for (int sub = 0; sub < kTPR; ++sub)
+      fft_stage_any(x.data(), N, L, b.rad[st], twiddled ? tw.data() + b.tw_off + off : nullptr, sub);
+    if (twiddled) off += (L / b.rad[st]) * (b.rad[st] - 1);
     L /= b.rad[st];
   }
   double2 part[kTPR];

@@ -62,6 +62,9 @@ struct XTile {
 // (p_j, q_j = (S / 2) (sin(pi j / N) +- 1/2)), Y = FFT(y) by mixed-radix stages
 // (radices 2, 3, 4, 5; decimation in frequency, output in digit-reversed order), then
 // X_{2k} = i (Y_k - Y_{N-k}) and X_{2k+1} = X_{2k-1} + Y_k + Y_{N-k}, X_1 = Y_0.
+// For N = m 2^a (m = 3 or 5, a >= 2) the FFT is split by the prime-factor map (Good and
+// Thomas): y_j is placed at n1 + 2^a n2 for j = (m n1 + 2^a n2) mod N, the radix-m stage
+// needs no twiddles, and Y_k lands at 2^a (k mod m) + (digit-reversed k mod 2^a).
 constexpr int kDstMaxStages = 8;
 constexpr int kDstMaxN = 128;     // largest N = n + 1 handled by the fast transform
 struct DstBlock {
@@ -70,8 +73,11 @@ struct DstBlock {
   int nst;                        // radix stages
   int rad[kDstMaxStages];         // radices in stage order
   int ntw;                        // twiddles of all stages (complex entries)
-  long long tw_off;               // offset (complex) of the stage twiddles
-  long long ioff;                 // offset (ints) of pos[N], gin[N], src[n]
+  int pfa;                        // 1: N = m 2^a (m = 3 or 5, a >= 2) split by the prime-factor
+                                  //   (Good-Thomas) map: the radix-m first stage has no twiddles
+  long long tw_off;               // offset (complex) of the stage twiddles (from the first
+                                  //   twiddled stage)
+  long long ioff;                 // offset (ints) of pos[N], gin[N], src[n], pin[N]
   long long coff;                 // offset (doubles) of (p_j, q_j), j = 0..N/2
 };
 struct DstSet {

@@ -103,7 +103,7 @@ class _NoStream:
     cuda_stream = 0
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 7, 8, 9, 11, 14, 15, 19, 23, 24, 29, 31, 35, 39, 47, 63, 79, 80, 99, 119, 127])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 9, 11, 14, 15, 19, 23, 24, 29, 31, 35, 39, 47, 63, 79, 80, 95, 99, 119, 127])
 def test_fast_sine_transform_matches_the_definition(hz, n):
     # the plan's FFT-based sine transform (host twin of the GPU kernel) against the DST-I sum
     # out = S sum_j x_j sin(pi j m / (n + 1)) with the symmetric-modes-first column order

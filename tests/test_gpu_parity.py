@@ -372,8 +372,9 @@ def test_uniform_blocks_sine_path(hz, torch_cuda, precision, fast):
 
 
 def test_fast_sine_many_tiles_against_lu_and_dense(hz, torch_cuda):
-    # uniform 160 x 99 x 7 grid: x blocks of 79 and 80 nodes (n + 1 = 80 = 4 x 4 x 5 and
-    # 81 = 3^4, as in the 320-node benchmark grid), y one block of 99 (100 = 4 x 5 x 5);
+    # uniform 160 x 99 x 7 grid: x blocks of 79 and 80 nodes (n + 1 = 80 = 16 x 5, split by
+    # the prime-factor map, and 81 = 3^4, as in the 320-node benchmark grid), y one block of 99
+    # (100 = 4 x 5 x 5, mixed radix with twiddles);
     # 3 RHS give 2079 and 3339 rows per transform launch (ragged last row tile)
     torch = torch_cuda
     rng = np.random.default_rng(17)
