@@ -103,8 +103,9 @@ struct hz_plan_s {
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaStream_t cst = nullptr;                  // host <-> device copies overlapped with solves
-  cudaEvent_t ev_in = nullptr;
+  cudaStream_t cst = nullptr;                  // host -> device copies overlapped with solves
+  cudaStream_t cst2 = nullptr;                 // device -> host copies overlapped with solves
+  cudaEvent_t ev_in[4] = {};                   // upload of chunk c done
   int real_cm = 1;
   AxisDev dx, dy;
   // z tables
@@ -1170,11 +1171,14 @@ void release(hz_plan_t p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->cst) cudaStreamDestroy(p->cst);
-  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->cst2) cudaStreamDestroy(p->cst2);
+  for (cudaEvent_t& e : p->ev_in) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   p->side = nullptr;
   p->ev_fork = p->ev_join = nullptr;
-  p->cst = nullptr;
-  p->ev_in = nullptr;
+  p->cst = p->cst2 = nullptr;
 }
 
 }  // namespace
@@ -1653,31 +1657,40 @@ hz_status hz_solve_host(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
       ck(cudaMemcpyAsync(uh, ud, sizeof(double2) * per * nrhs, cudaMemcpyDeviceToHost, p->st));
       ck(cudaStreamSynchronize(p->st));
     } else {
-      // two halves: the second half's input arrives and the first half's result leaves on a
-      // copy stream while the other half is solved
+      // up to four chunks of RHS: every upload is queued at once on one copy stream (chunk c's
+      // solve waits for its own upload only), each chunk's download starts on a second copy
+      // stream as soon as its solve is done, so both directions overlap the later solves
       if (!p->cst) {
         ck(cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
-        ck(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+        ck(cudaStreamCreateWithFlags(&p->cst2, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : p->ev_in) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       }
-      const int R0 = (nrhs + 1) / 2, R1 = nrhs - R0;
-      const size_t b0 = sizeof(double2) * per * R0, b1 = sizeof(double2) * per * R1;
-      ck(cudaMemcpyAsync(fd, fh, b0, cudaMemcpyHostToDevice, p->st));
-      ck(cudaMemcpyAsync(fd + per * R0, fh + per * R0, b1, cudaMemcpyHostToDevice, p->cst));
-      ck(cudaEventRecord(p->ev_in, p->cst));
-      solve_full(p, fd, ud, R0, 0);                               // returns with the solve done
-      const int ref0 = p->info.refinements;
-      const double rel0 = p->info.rel_residual;
-      ck(cudaMemcpyAsync(uh, ud, b0, cudaMemcpyDeviceToHost, p->cst));
-      ck(cudaStreamWaitEvent(p->st, p->ev_in, 0));
-      solve_full(p, fd + per * R0, ud + per * R0, R1, 0);
-      ck(cudaMemcpyAsync(uh + per * R0, ud + per * R0, b1, cudaMemcpyDeviceToHost, p->st));
+      const int K = std::min(nrhs, 4);
+      int r0[5];
+      for (int c = 0; c <= K; ++c) r0[c] = (int)((long long)nrhs * c / K);
+      for (int c = 0; c < K; ++c) {
+        const size_t off = per * r0[c], bytes = sizeof(double2) * per * (r0[c + 1] - r0[c]);
+        ck(cudaMemcpyAsync(fd + off, fh + off, bytes, cudaMemcpyHostToDevice, p->cst));
+        ck(cudaEventRecord(p->ev_in[c], p->cst));
+      }
+      int refs = 0;
+      double rel = -1.0;
+      for (int c = 0; c < K; ++c) {
+        const size_t off = per * r0[c], bytes = sizeof(double2) * per * (r0[c + 1] - r0[c]);
+        ck(cudaStreamWaitEvent(p->st, p->ev_in[c], 0));
+        solve_full(p, fd + off, ud + off, r0[c + 1] - r0[c], 0);   // returns with the solve done
+        refs = std::max(refs, p->info.refinements);
+        rel = std::max(rel, p->info.rel_residual);
+        ck(cudaMemcpyAsync(uh + off, ud + off, bytes, cudaMemcpyDeviceToHost, p->cst2));
+      }
       ck(cudaStreamSynchronize(p->st));
-      ck(cudaStreamSynchronize(p->cst));
-      p->info.refinements = std::max(ref0, p->info.refinements);
-      p->info.rel_residual = std::max(rel0, p->info.rel_residual);
+      ck(cudaStreamSynchronize(p->cst2));
+      p->info.refinements = refs;
+      p->info.rel_residual = rel;
     }
   } catch (const Fail& e) {
     if (p->cst) cudaStreamSynchronize(p->cst);             // no copy may touch the caller's buffers later
+    if (p->cst2) cudaStreamSynchronize(p->cst2);
     return e.s;
   }
   return HZ_OK;

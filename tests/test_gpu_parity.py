@@ -143,6 +143,23 @@ def test_in_place_and_host_entry_points(hz, torch_cuda):
     assert rel(fd3.cpu().numpy(), u) < TOLMIX
 
 
+@pytest.mark.parametrize("nrhs", [1, 3, 5, 9])
+def test_host_entry_point_chunks(hz, torch_cuda, nrhs):
+    # host buffers: 1 RHS in one piece; 3, 5 and 9 RHS in up to four uneven chunks whose
+    # uploads, solves and downloads overlap; every RHS against the device-buffer solve
+    torch = torch_cuda
+    w = W.tiny_pml(30, 28, 17, 2, 2, rim=4, pml=2, nrhs=nrhs)
+    plan = hz.Plan.from_workload(w, precision="fp64")
+    u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+    for precision, tol in (("fp64", 1e-14), ("mixed", TOLMIX)):
+        plan.set_options(precision=precision)
+        uh = plan.solve_host(w.f)
+        for r in range(nrhs):
+            assert rel(uh[r], u[r]) < tol, (precision, r)
+        if precision == "mixed":
+            assert plan.info()["rel_residual"] <= 1e-8
+
+
 def test_ragged_rhs_counts(hz, torch_cuda):
     torch = torch_cuda
     w = W.tiny_pml(33, 29, 19, 2, 3, rim=4, pml=2, nrhs=5)
