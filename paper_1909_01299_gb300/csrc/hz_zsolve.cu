@@ -53,13 +53,20 @@ struct GenThread {
   int pl = -1, pr = -1, ql = -1, qr = -1;
   float2 cl, cr, dl, dr;
 };
+
+// GEN: 0 read rhs32; 2 rhs32 plus the boundary term (kind 2); 10 + NI the global right-hand
+// side (kind 1) with NI = max(nIx, nIy) <= kGenMaxIface terms per axis, unrolled at compile
+// time (terms past nIx or nIy are skipped by a uniform test).
+template <int GEN> __host__ __device__ constexpr int gen_terms() { return GEN > 10 ? GEN - 10 : 0; }
+
 template <int GEN>
 __device__ __forceinline__ GenThread gen_thread(const ZSolveArgs& a, int i, int j) {
   GenThread t;
   const ZRhsGen& g = a.gen;
-  if constexpr (GEN == 1) {
+  constexpr int NI = gen_terms<GEN>();
+  if constexpr (NI > 0) {
 #pragma unroll
-    for (int p = 0; p < kGenMaxIface; ++p) {
+    for (int p = 0; p < NI; ++p) {
       t.wx[p] = p < g.nIx ? g.wx32[(long long)p * a.nx + i] : make_float2(0.f, 0.f);
       t.wy[p] = p < g.nIy ? g.wy32[(long long)p * a.ny + j] : make_float2(0.f, 0.f);
     }
@@ -71,31 +78,31 @@ __device__ __forceinline__ GenThread gen_thread(const ZSolveArgs& a, int i, int 
 }
 
 // Complex64 right-hand side of plane k of RHS r at mode (i, j), element idx of rhs32, as FP64:
-// GEN 0 read, 1 the global right-hand side, 2 rhs32 plus the boundary term (the FP32 sums of
-// global_rhs_kernel and boundary_rhs_kernel, term by term in the same order).
+// the FP32 sums of global_rhs_kernel and boundary_rhs_kernel, term by term in the same order.
 template <int GEN>
 __device__ __forceinline__ double2 c64_rhs(const ZSolveArgs& a, const GenThread& gt, long long idx, int r, int k,
                                            int i, int j) {
+  constexpr int NI = gen_terms<GEN>();
   if constexpr (GEN == 0) {
     return to_c128(a.rhs32[idx]);
   } else {
     const ZRhsGen& g = a.gen;
     const long long rk = (long long)r * a.nz + k;
     float2 s = make_float2(0.f, 0.f);
-    if constexpr (GEN == 1) {
+    if constexpr (NI > 0) {
       const float2* ax = g.aX32 + rk * g.nIx * a.ny + j;
       const float2* by = g.bY32 + rk * g.nIy * a.nx + i;
-      float2 vx[kGenMaxIface], vy[kGenMaxIface];
+      float2 vx[NI], vy[NI];
 #pragma unroll
-      for (int p = 0; p < kGenMaxIface; ++p) {
+      for (int p = 0; p < NI; ++p) {
         if (p < g.nIx) vx[p] = ax[(long long)p * a.ny];
         if (p < g.nIy) vy[p] = by[(long long)p * a.nx];
       }
 #pragma unroll
-      for (int p = 0; p < kGenMaxIface; ++p)
+      for (int p = 0; p < NI; ++p)
         if (p < g.nIx) s = cfma32(gt.wx[p], vx[p], s);
 #pragma unroll
-      for (int p = 0; p < kGenMaxIface; ++p)
+      for (int p = 0; p < NI; ++p)
         if (p < g.nIy) s = cfma32(gt.wy[p], vy[p], s);
       return to_c128(s);
     } else {
@@ -471,9 +478,14 @@ __global__ void zfactor_kernel(double2* __restrict__ P, double2* __restrict__ Q,
 template <bool REALCM, bool C64, int GEN>
 void launch_sweep(const ZSolveArgs& a, int variant, unsigned grid, cudaStream_t st) {
   const int T = 128;
-  if (variant == 3 && GEN == 0) zsolve_chunk_kernel<REALCM, C64><<<grid, T, 0, st>>>(a);
-  else if (variant == 2) zsolve_kernel<REALCM, 2, C64, GEN><<<grid, T, 0, st>>>(a);
-  else zsolve_kernel<REALCM, 1, C64, GEN><<<grid, T, 0, st>>>(a);
+  if constexpr (GEN == 0) {
+    if (variant == 3) zsolve_chunk_kernel<REALCM, C64><<<grid, T, 0, st>>>(a);
+    else if (variant == 2) zsolve_kernel<REALCM, 2, C64, 0><<<grid, T, 0, st>>>(a);
+    else zsolve_kernel<REALCM, 1, C64, 0><<<grid, T, 0, st>>>(a);
+  } else {
+    // a sweep that forms its right-hand side takes one RHS per thread
+    zsolve_kernel<REALCM, 1, C64, GEN><<<grid, T, 0, st>>>(a);
+  }
 }
 
 int sweep_variant(const ZSolveArgs& a) {
@@ -489,17 +501,27 @@ int sweep_variant(const ZSolveArgs& a) {
 
 template <bool REALCM>
 void launch_sweep_c(const ZSolveArgs& a, int variant, unsigned grid, cudaStream_t st) {
-  if (!a.rhs32) launch_sweep<REALCM, false, 0>(a, variant, grid, st);
-  else if (a.gen.kind == 1) launch_sweep<REALCM, true, 1>(a, variant, grid, st);
-  else if (a.gen.kind == 2) launch_sweep<REALCM, true, 2>(a, variant, grid, st);
-  else launch_sweep<REALCM, true, 0>(a, variant, grid, st);
+  if (!a.rhs32) {
+    launch_sweep<REALCM, false, 0>(a, variant, grid, st);
+  } else if (a.gen.kind == 1) {
+    switch (std::max(a.gen.nIx, a.gen.nIy)) {
+      case 1: launch_sweep<REALCM, true, 11>(a, variant, grid, st); break;
+      case 2: launch_sweep<REALCM, true, 12>(a, variant, grid, st); break;
+      case 3: launch_sweep<REALCM, true, 13>(a, variant, grid, st); break;
+      default: launch_sweep<REALCM, true, 14>(a, variant, grid, st); break;
+    }
+  } else if (a.gen.kind == 2) {
+    launch_sweep<REALCM, true, 2>(a, variant, grid, st);
+  } else {
+    launch_sweep<REALCM, true, 0>(a, variant, grid, st);
+  }
 }
 
 void zsolve(const ZSolveArgs& a, cudaStream_t st) {
   if ((long long)a.nx * a.ny * a.nrhs == 0) return;
   const int T = 128;
   const int variant = sweep_variant(a);
-  const int rb = variant == 2 ? 2 : 1;
+  const int rb = (variant == 2 && a.gen.kind == 0) ? 2 : 1;
   const long long n = (long long)a.nx * a.ny * ((a.nrhs + rb - 1) / rb);
   const unsigned grid = (unsigned)((n + T - 1) / T);
   if (a.real_cm) launch_sweep_c<true>(a, variant, grid, st);
@@ -509,7 +531,7 @@ void zsolve(const ZSolveArgs& a, cudaStream_t st) {
 
 bool zsolve_forms_rhs(const ZSolveArgs& a) {
   if (sweep_variant(a) == 3) return false;
-  if (a.gen.kind == 1) return a.gen.nIx <= kGenMaxIface && a.gen.nIy <= kGenMaxIface;
+  if (a.gen.kind == 1) return std::max(a.gen.nIx, a.gen.nIy) >= 1 && std::max(a.gen.nIx, a.gen.nIy) <= kGenMaxIface;
   return a.gen.kind == 2;
 }
 
