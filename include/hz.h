@@ -196,7 +196,8 @@ hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
 
 /* The mode-wise z eliminations of Eq. (fdmtrprjfr) and Eq. (fdmtrprjfrerr) (Thomas sweeps, one
  * thread per mode and right-hand side): variant 1 one right-hand side per thread, 2 two per
- * thread sharing each factor load, 3 one per thread with z taken in register chunks of 16 steps
+ * thread sharing each factor load (the mixed path's step-5/6 sweeps, which form their
+ * right-hand side themselves, keep one), 3 one per thread with z taken in register chunks of 16 steps
  * (all loads of a chunk in flight together, one complex multiply-add on the dependency chain:
  * for few modes and long z, where the sweeps cannot fill the GPU); 0 (the default): variant 3
  * when a launch has fewer than 512 sweeps per SM, else 1.  Same elimination in FP64; variant 3
