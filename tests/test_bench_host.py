@@ -92,3 +92,27 @@ def test_pml_workload_uses_the_dense_count():
     dense, fast, all_fast = bench.fp64_transform_work(w, 4)
     assert fast == 0 and not all_fast
     assert dense == 4 * 128 * 159 * (79 * 79 + 80 * 80) * 8
+
+
+def test_tensor_core_mma_work_and_kernel_names():
+    # the MMA flops of a step's transforms: interleaved complex GEMM 8 flops per complex
+    # multiply-add, the real-table kernel 4 (its two real products of K = N = n); 3 TF32 products
+    import bench
+    w = bench.bench_workload()
+    per = 8 * 200
+    sq = 3 * 79 * 79 + 80 * 80
+    inter = 3 * per * (2 * 317 * sq * 8 + 2 * 317 * sq * 8)
+    assert bench.tc_mma_flops(w, 8, False) == inter
+    assert bench.tc_mma_flops(w, 8, True) == inter // 2
+    assert bench.real_block_flags(w.hx, w.x_iface) == [True] * 4
+    st = {k: (0.0, 0) for k in ("fwd", "pass_a", "edges", "iface_residual", "global", "pass_b", "inv",
+                                "iface_out", "residual")}
+    st["fwd"] = (1.0, 2)
+    st["inv"] = (1.0, 2)
+    assert bench.tc_roofline(w, 8, st, 0, True)["kernel"].startswith("xform_tcr_kernel")
+    assert bench.tc_roofline(w, 8, st, 0, False)["kernel"].startswith("xform_tc_kernel ")
+    # pml-160: the blocks reach into the complex rim steps, so no table is real
+    p = W.pml_160x160x128()
+    assert bench.real_block_flags(p.hx, p.x_iface) == [False, False]
+    assert bench.tc_mma_flops(p, 4, True) == bench.tc_mma_flops(p, 4, False)
+    assert bench.tc_roofline(p, 4, st, 1, True)["kernel"].startswith("xform_tc_kernel ")
