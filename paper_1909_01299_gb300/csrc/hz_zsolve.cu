@@ -9,11 +9,12 @@
 // z step is a coalesced access of the [k][i][j] mode layout.
 //
 // The right-hand sides of the global pass (r~ of step 5) and the boundary term of
-// pass B (g~ of step 6) are rank-|I| outer products of interface data; they are
-// formed by fully parallel kernels (global_rhs, boundary_rhs) so that every sweep
-// is the same plain kernel.  The elimination factors depend only on the mode and
-// the frequency, so they are computed once per plan/frequency (zfactor) and the
-// per-solve sweep is
+// pass B (g~ of step 6) are rank-|I| outer products of interface data.  On the FP64 path
+// they are formed by fully parallel kernels (global_rhs, boundary_rhs); on the mixed path
+// (FP32 sums of complex64 interface data) the sweep forms them itself, term by term in the
+// same order, so that no complex64 volume is written and read back.  The elimination factors
+// depend only on the mode and the frequency, so they are computed once per plan/frequency
+// (zfactor) and the per-solve sweep is
 //   forward  y_k = (rhs_k - cm_k y_{k-1}) P_k,   back  x_k = y_k - Q_k x_{k+1},
 // with P_k = fold_k / d_k, Q_k = c_{k+1} / d_k, cm_k = c_k / fold_k, d_k the
 // pivots.  The forward results are kept in the output array and overwritten by
