@@ -1188,9 +1188,11 @@ void release(hz_plan_t p) {
 // ---------------------------------------------------------------------------
 namespace {
 
-// Time the plan's kernel variants (z-sweep RHS per thread 1 or 2; on the mixed path tensor-core
-// or CUDA-core bulk transforms) with three solves each on workspace w and stream st, keep the
-// fastest; returns rb + 10 * tc of the choice.  f and out are device buffers of nrhs RHS.
+// Time the plan's kernel variants (z-sweep variant 1, 2 or 3; on the mixed path tensor-core or
+// CUDA-core bulk transforms and the real-table or interleaved tensor-core kernel; with uniform
+// blocks the fast sine transform or the dense product) with three solves each on workspace w and
+// stream st, keep the fastest; returns z_sweep + 10 tc + 100 fast_sine + 1000 real_tables of the
+// choice.  f and out are device buffers of nrhs RHS.
 int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* out, int nrhs) {
   const bool mixed = p->opts.precision != HZ_FP64;
   const bool timing = p->timing;
