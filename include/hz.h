@@ -176,11 +176,13 @@ hz_status hz_plan_set_k2(hz_plan_t plan, const hz_c128 *k2);
 
 /* Autotuner: times one solve of nrhs right-hand sides (on zero data, in the plan's
  * workspace) for each kernel variant the plan can use -- the three z sweep variants of
- * hz_plan_set_z_sweep, for mixed plans tensor-core or CUDA-core FP32
+ * hz_plan_set_z_sweep, two row tiles of the dense CUDA-core transforms, for mixed plans tensor-core or CUDA-core FP32
  * bulk transforms and the real-table or interleaved tensor-core kernel, for plans with
  * uniform blocks the fast sine transform or the dense product -- and keeps the fastest.
  * *choice_out (may be NULL) receives
- * z_sweep + 10 * tensor_cores + 100 * fast_sine + 1000 * real_tables. */
+ * z_sweep + 10 * tensor_cores + 100 * fast_sine + 1000 * real_tables + 10000 * tile, with tile the
+ * data rows per CTA of the dense CUDA-core transforms (FP64, and FP32 interface rows): 1 for 16,
+ * 2 for 64 (untuned plans choose by launch size). */
 hz_status hz_plan_autotune(hz_plan_t plan, int nrhs, int *choice_out);
 
 /* Transform the uniform blocks (all steps equal and real, so that the block's eigenvectors
@@ -203,6 +205,12 @@ hz_status hz_plan_set_fast_sine(hz_plan_t plan, int enable);
  * when a launch has fewer than 512 sweeps per SM, else 1.  Same elimination in FP64; variant 3
  * rounds the forward step in another order.  HZ_ERR_ARG for other values. */
 hz_status hz_plan_set_z_sweep(hz_plan_t plan, int variant);
+
+/* Data rows per CTA of the dense CUDA-core transforms (the FP64 block and whole-axis products of
+ * Eq. (fdmtrprjfr) and step 5, and the mixed path's FP32 interface-row transforms): 16 or 64; 0
+ * (the default) chooses 64 when a launch has at least two CTAs per SM, else 16.  The autotuner
+ * times both.  Same result.  HZ_ERR_ARG for other values. */
+hz_status hz_plan_set_dense_tile_rows(hz_plan_t plan, int rows);
 
 /* Mixed path: blocks whose eigenvector tables are real (all their steps real) run the
  * tensor-core transform as two real products, Re C = Re A B and Im C = Im A B, each with K = N =

@@ -99,6 +99,7 @@ struct hz_plan_s {
   bool has_real_tc = false;          // some block has a real table
   bool has_dst = false;              // some block has a fast sine transform
   int zs_rb = 0;                     // z sweep variant (hz_plan_set_z_sweep; 0 automatic; autotuned)
+  int xf_tile = 0;                   // data rows per CTA of the dense transforms: 16, 64, 0 by launch size (autotuned)
   int sms = 0;                       // SM count of the plan's device
   // second stream for the y-side interface work (runs beside the x side)
   cudaStream_t side = nullptr;
@@ -843,10 +844,10 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
         throw Fail{HZ_ERR_ARG};
     } else if (!lo) {
       hz::xform_f64(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
-                    store_mode, conj, skip, st, p->fast_sine);
+                    store_mode, conj, skip, st, p->fast_sine, p->xf_tile);
     } else {
       hz::xform_f32(xs, static_cast<const double2*>(in), static_cast<double2*>(out), rpp, planes, trans,
-                    store_mode, conj, skip, st);
+                    store_mode, conj, skip, st, p->xf_tile);
     }
   };
   // The interface-row transforms below are non-transposed, so their rows are
@@ -856,8 +857,8 @@ void solve_core(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, do
   // like the bulk transforms; the z eliminations, the interface residual and the
   // refinement residual stay FP64.
   auto rowx = [&](const hz::XformSet& xs, const double2* in, double2* out, long long rows, cudaStream_t s) {
-    if (lo) hz::xform_f32(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s);
-    else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s, p->fast_sine);
+    if (lo) hz::xform_f32(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s, p->xf_tile);
+    else hz::xform_f64(xs, in, out, (int)rows, 1, 0, hz::XS_STORE, 0, nullptr, s, p->fast_sine, p->xf_tile);
   };
   // contractions of the current z-sweep result (complex64 in V32, or complex128 in V)
   auto crows = [&](const AxisDev& d, double2* out, bool edge, int nslots, cudaStream_t s) {
@@ -1190,9 +1191,10 @@ namespace {
 
 // Time the plan's kernel variants (z-sweep variant 1, 2 or 3; on the mixed path tensor-core or
 // CUDA-core bulk transforms and the real-table or interleaved tensor-core kernel; with uniform
-// blocks the fast sine transform or the dense product) with three solves each on workspace w and
-// stream st, keep the fastest; returns z_sweep + 10 tc + 100 fast_sine + 1000 real_tables of the
-// choice.  f and out are device buffers of nrhs RHS.
+// blocks the fast sine transform or the dense product; 16 or 64 data rows per CTA of the dense
+// CUDA-core transforms) with three solves each on workspace w and stream st, keep the fastest;
+// returns z_sweep + 10 tc + 100 fast_sine + 1000 real_tables + 10000 tile (1: 16 rows, 2: 64)
+// of the choice.  f and out are device buffers of nrhs RHS.
 int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, double2* out, int nrhs) {
   const bool mixed = p->opts.precision != HZ_FP64;
   const bool timing = p->timing;
@@ -1202,6 +1204,7 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   ck(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_rb = p->zs_rb;
+  int best_tile = p->xf_tile;
   bool best_tc = p->use_tc;
   bool& fsref = mixed ? p->fast_sine32 : p->fast_sine;     // the fast-sine choice of this path
   bool best_fs = fsref;
@@ -1210,10 +1213,12 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
   const int tr_hi = (mixed && p->has_real_tc) ? 1 : tr_lo;
   const int fs_lo = p->has_dst ? 0 : (fsref ? 1 : 0);
   const int fs_hi = p->has_dst ? 1 : fs_lo;
+  for (int tile : {64, 16})
   for (int tr = tr_lo; tr <= tr_hi; ++tr)
   for (int fs = fs_lo; fs <= fs_hi; ++fs)
   for (int rb = 1; rb <= 3; ++rb)
     for (int tc = (mixed || !p->tc_ok) ? 0 : 1; tc <= (p->tc_ok ? 1 : 0); ++tc) {
+      p->xf_tile = tile;
       p->tc_real = tr != 0;
       fsref = fs != 0;
       p->zs_rb = rb;
@@ -1225,16 +1230,17 @@ int tune_plan(hz_plan_t p, Workspace& w, cudaStream_t st, const double2* f, doub
       ck(cudaEventSynchronize(e1));
       float ms = 0.f;
       ck(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; best_fs = fs != 0; best_tr = tr != 0; }
+      if (ms < best) { best = ms; best_rb = rb; best_tc = tc != 0; best_fs = fs != 0; best_tr = tr != 0; best_tile = tile; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->zs_rb = best_rb;
+  p->xf_tile = best_tile;
   p->use_tc = best_tc;
   fsref = best_fs;
   p->tc_real = best_tr;
   p->timing = timing;
-  return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0) + (best_tr ? 1000 : 0);
+  return best_rb + (best_tc ? 10 : 0) + (best_fs ? 100 : 0) + (best_tr ? 1000 : 0) + (best_tile == 16 ? 10000 : 20000);
 }
 
 }  // namespace
@@ -1608,6 +1614,12 @@ hz_status hz_plan_set_fast_sine(hz_plan_t p, int enable) {
 hz_status hz_plan_set_real_tables(hz_plan_t p, int enable) {
   if (!p) return HZ_ERR_ARG;
   p->tc_real = enable != 0;
+  return HZ_OK;
+}
+
+hz_status hz_plan_set_dense_tile_rows(hz_plan_t p, int rows) {
+  if (!p || (rows != 0 && rows != 16 && rows != 64)) return HZ_ERR_ARG;
+  p->xf_tile = rows;
   return HZ_OK;
 }
 

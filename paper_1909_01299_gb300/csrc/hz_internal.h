@@ -195,14 +195,15 @@ bool xform_tc(const TCSet& ts, const void* in, int in32, void* out, int out32, i
 // conjugates the result before it is stored.
 // rowskip (may be NULL) flags rows (index within the plane) that are neither computed nor
 // written: the interface rows, which belong to no block.
-// fast_sine: uniform blocks with a fast-transform descriptor use dst_f64.
+// fast_sine: uniform blocks with a fast-transform descriptor use dst_f64.  tile_rows: data rows
+// per CTA of the dense kernel, 16 or 64 (0: 64 when the launch has at least two CTAs per SM).
 void xform_f64(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
-               cudaStream_t st, bool fast_sine = false);
+               cudaStream_t st, bool fast_sine = false, int tile_rows = 0);
 // Same contraction with FP32 arithmetic on FP64 data (SIMT FFMA), for the mixed path.
 void xform_f32(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
-               cudaStream_t st);
+               cudaStream_t st, int tile_rows = 0);
 
 // ---------------------------------------------------------------------------
 // z solves per mode (Eq. (fdmtrprjfr), Eq. (fdmtrprjfrerr))

@@ -375,10 +375,11 @@ xform_kernel(const double2* __restrict__ in, double2* __restrict__ out, const Ac
 template <typename Acc>
 void launch(const XformSet& xs, const XTile* tiles, int ntiles, const Acc* tab, const double2* in, double2* out,
             int rows_per_plane, long long nplanes, int trans, int store, int conj_out,
-            const signed char* rowskip, cudaStream_t st) {
+            const signed char* rowskip, cudaStream_t st, int tile_rows) {
   const long long nrows = nplanes * (long long)rows_per_plane;
   if (nrows <= 0 || ntiles == 0) return;
-  if (((nrows + 63) / 64) * ntiles >= 2 * 152) {
+  const bool big = tile_rows == 64 || (tile_rows != 16 && ((nrows + 63) / 64) * ntiles >= 2 * 152);
+  if (big) {
     const long long ctas = ((nrows + 63) / 64) * ntiles;
     xform_kernel<Acc, 64><<<(unsigned)ctas, NT, 0, st>>>(in, out, tab, xs.d_blocks, tiles, ntiles, nrows,
                                                           rows_per_plane, xs.ncols, trans, store, conj_out,
@@ -396,23 +397,23 @@ void launch(const XformSet& xs, const XTile* tiles, int ntiles, const Acc* tab, 
 
 void xform_f64(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
-               cudaStream_t st, bool fast_sine) {
+               cudaStream_t st, bool fast_sine, int tile_rows) {
   if (fast_sine && xs.dst.nblk > 0) {
     // the two launches write disjoint columns of the output
     launch<double>(xs, xs.d_tiles64, xs.ntiles64, xs.d_tab, in, out, rows_per_plane, nplanes, trans, store,
-                   conj_out, rowskip, st);
+                   conj_out, rowskip, st, tile_rows);
     dst_f64(xs.dst, in, out, rows_per_plane, nplanes, xs.ncols, trans, store, conj_out, rowskip, st);
     return;
   }
   launch<double>(xs, xs.d_tiles, xs.ntiles, xs.d_tab, in, out, rows_per_plane, nplanes, trans, store, conj_out,
-                 rowskip, st);
+                 rowskip, st, tile_rows);
 }
 
 void xform_f32(const XformSet& xs, const double2* in, double2* out, int rows_per_plane,
                long long nplanes, int trans, int store, int conj_out, const signed char* rowskip,
-               cudaStream_t st) {
+               cudaStream_t st, int tile_rows) {
   launch<float>(xs, xs.d_tiles, xs.ntiles, xs.d_tab32, in, out, rows_per_plane, nplanes, trans, store, conj_out,
-                rowskip, st);
+                rowskip, st, tile_rows);
 }
 
 }  // namespace hz

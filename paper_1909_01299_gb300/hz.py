@@ -65,6 +65,7 @@ SIGNATURES = {
     "hz_plan_set_fast_sine": (ctypes.c_int, [_P, ctypes.c_int]),
     "hz_plan_set_real_tables": (ctypes.c_int, [_P, ctypes.c_int]),
     "hz_plan_set_z_sweep": (ctypes.c_int, [_P, ctypes.c_int]),
+    "hz_plan_set_dense_tile_rows": (ctypes.c_int, [_P, ctypes.c_int]),
     "hz_sine_transform_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P]),
     "hz_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
@@ -220,7 +221,8 @@ class Plan:
         c = ctypes.c_int()
         _check(_lib.hz_plan_autotune(self._h, int(nrhs), ctypes.byref(c)), "hz_plan_autotune")
         return {"z_sweep": c.value % 10, "tensor_cores": (c.value // 10) % 10 == 1,
-                "fast_sine": (c.value // 100) % 10 == 1, "real_tables": c.value >= 1000}
+                "fast_sine": (c.value // 100) % 10 == 1, "real_tables": (c.value // 1000) % 10 == 1,
+                "dense_tile_rows": {1: 16, 2: 64}.get(c.value // 10000, 0)}
 
     def set_real_tables(self, enable: bool):
         """Mixed path: real block tables through the real-table tensor-core kernel (True, the
@@ -231,6 +233,11 @@ class Plan:
         """z sweep variant (hz_plan_set_z_sweep): 1 or 2 right-hand sides per thread, 3 z in
         register chunks (few modes, long z), 0 (default) chosen per launch."""
         _check(_lib.hz_plan_set_z_sweep(self._h, int(variant)), "hz_plan_set_z_sweep")
+
+    def set_dense_tile_rows(self, rows: int):
+        """Data rows per CTA of the dense CUDA-core transforms (hz_plan_set_dense_tile_rows):
+        16, 64, or 0 (default) chosen by launch size."""
+        _check(_lib.hz_plan_set_dense_tile_rows(self._h, int(rows)), "hz_plan_set_dense_tile_rows")
 
     def set_fast_sine(self, enable: int):
         """Uniform blocks by the FFT-based sine transform (hz_plan_set_fast_sine): 0 dense

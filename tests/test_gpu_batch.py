@@ -90,10 +90,27 @@ def test_plan_autotune_keeps_results(env, precision):
     plan = hz.Plan.from_workload(w, precision=precision)
     choice = plan.autotune(w.nrhs)
     assert choice["z_sweep"] in (1, 2, 3)
+    assert choice["dense_tile_rows"] in (16, 64)
     assert precision == "mixed" or choice["tensor_cores"]
     u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
     tol = 1e-10 if precision == "fp64" else 1e-8
     assert rel(u, ref) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dense_transform_row_tiles(env, precision):
+    # both row tiles of the dense CUDA-core transforms give the oracle's solution: 16 rows per
+    # CTA (the small-launch tile) forced on every launch through the autotuner's state, and 64
+    torch, hz = env
+    w = W.tiny_pml(70, 45, 33, 3, 2, rim=6, pml=3, nrhs=3)
+    ref = O.solve(O.Problem.from_workload(w), w.f)
+    plan = hz.Plan.from_workload(w, precision=precision)
+    plan.set_options(precision=precision)
+    for tile in (16, 64):
+        plan.set_dense_tile_rows(tile)
+        u = plan.solve(torch.from_numpy(w.f).cuda()).cpu().numpy()
+        for r in range(w.nrhs):
+            assert rel(u[r], ref[r]) < (1e-10 if precision == "fp64" else 1e-8), (tile, r)
 
 
 def test_batch48_subset_at_full_model_size(env):
