@@ -132,3 +132,12 @@ def test_fast_sine_transform_rejects_unsupported_lengths(hz, n):
     with pytest.raises(hz.HzError) as e:
         hz.sine_transform_host(np.ones(n, complex), 1, 1.0)
     assert e.value.code == 1
+
+
+def test_plan_setters_reject_a_null_plan(hz):
+    # every per-plan kernel choice returns HZ_ERR_ARG (1) for a NULL plan, without a device
+    lib = hz._lib
+    assert lib.hz_plan_set_z_sweep(None, 1) == 1
+    assert lib.hz_plan_set_dense_tile_rows(None, 16) == 1
+    assert lib.hz_plan_set_fast_sine(None, 1) == 1
+    assert lib.hz_plan_set_real_tables(None, 1) == 1
