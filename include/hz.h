@@ -237,7 +237,7 @@ hz_status hz_solve(hz_plan_t plan, const hz_c128 *f_dev, hz_c128 *u_dev, int nrh
 
 /* The same solve with HOST arrays f_host, u_host (pageable or pinned): the call
  * copies f to the device, solves and copies u back.  With nrhs >= 2 the RHS are solved in
- * up to four chunks: all uploads are queued at once on one copy stream, each chunk's
+ * up to eight chunks: all uploads are queued at once on one copy stream, each chunk's
  * download starts on a second copy stream when its solve is done, so both overlap the
  * later chunks' solves (pinned buffers make the copies asynchronous).  info.refinements and
  * info.rel_residual are the maxima over the chunks. */

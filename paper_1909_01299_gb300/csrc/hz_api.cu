@@ -106,7 +106,7 @@ struct hz_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t cst = nullptr;                  // host -> device copies overlapped with solves
   cudaStream_t cst2 = nullptr;                 // device -> host copies overlapped with solves
-  cudaEvent_t ev_in[4] = {};                   // upload of chunk c done
+  cudaEvent_t ev_in[8] = {};                   // upload of chunk c done
   int real_cm = 1;
   AxisDev dx, dy;
   // z tables
@@ -1671,7 +1671,7 @@ hz_status hz_solve_host(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
       ck(cudaMemcpyAsync(uh, ud, sizeof(double2) * per * nrhs, cudaMemcpyDeviceToHost, p->st));
       ck(cudaStreamSynchronize(p->st));
     } else {
-      // up to four chunks of RHS: every upload is queued at once on one copy stream (chunk c's
+      // up to eight chunks of RHS: every upload is queued at once on one copy stream (chunk c's
       // solve waits for its own upload only), each chunk's download starts on a second copy
       // stream as soon as its solve is done, so both directions overlap the later solves
       if (!p->cst) {
@@ -1679,8 +1679,8 @@ hz_status hz_solve_host(hz_plan_t p, const hz_c128* f, hz_c128* u, int nrhs) {
         ck(cudaStreamCreateWithFlags(&p->cst2, cudaStreamNonBlocking));
         for (cudaEvent_t& e : p->ev_in) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       }
-      const int K = std::min(nrhs, 4);
-      int r0[5];
+      const int K = std::min(nrhs, 8);
+      int r0[9];
       for (int c = 0; c <= K; ++c) r0[c] = (int)((long long)nrhs * c / K);
       for (int c = 0; c < K; ++c) {
         const size_t off = per * r0[c], bytes = sizeof(double2) * per * (r0[c + 1] - r0[c]);

@@ -145,7 +145,7 @@ def test_in_place_and_host_entry_points(hz, torch_cuda):
 
 @pytest.mark.parametrize("nrhs", [1, 3, 5, 9])
 def test_host_entry_point_chunks(hz, torch_cuda, nrhs):
-    # host buffers: 1 RHS in one piece; 3, 5 and 9 RHS in up to four uneven chunks whose
+    # host buffers: 1 RHS in one piece; 3, 5 and 9 RHS in up to eight uneven chunks whose
     # uploads, solves and downloads overlap; every RHS against the device-buffer solve
     torch = torch_cuda
     w = W.tiny_pml(30, 28, 17, 2, 2, rim=4, pml=2, nrhs=nrhs)
